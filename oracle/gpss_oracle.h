@@ -1,0 +1,132 @@
+/*
+ * gpss_oracle.h -- FP64 CPU oracle for the GPSS macrofacet medium.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  The product library
+ * (the CUDA path) never includes, links or calls it, and the two share no
+ * source: this header and its .c files are written independently from the
+ * paper ("Macrofacet Theory for Gaussian Process Statistical Surfaces").
+ *
+ * Everything is computed in double precision.  Input grids are FP32 (that is
+ * the scene definition); they are widened on read.
+ *
+ * Reading of the paper used throughout (the paper's own notation in brackets):
+ *  - A scene object is a GPSS f ~ GP(mu(x), kappa) with squared-exponential
+ *    kernel (Eq. se_kernel).  mu and sigma^2 are node-centred grids, trilinearly
+ *    interpolated; grad mu is the analytic gradient of that interpolant.
+ *  - Under the independence assumption (Sec. 4.2.1) the gradient at a point is
+ *    g ~ N(grad mu, (sigma/l)^2 I) independent of f ~ N(mu, sigma^2).
+ *  - Extinction for a ray marching along d (omega_o in Eq. generalized_sigma_t):
+ *      sigma_t(x,d) = rho(x) * sigma(d),
+ *      rho   = phi(mu;0,sigma^2) / Phi(mu;0,sigma^2)      (Eq. macro_sigma_t)
+ *      sigma(d) = Lambda(d) cos(theta)                    (Eq. generalized_lambda)
+ *    with the mean gradient (0,0,1) of the paper generalised to grad mu.
+ *  - NDF by its definition D(m) = int_0^inf t^3 P(t m) dt  (Eq. gdf_to_ndf).
+ *  - Conductor phase function p = F D_d(m) / (4 |d.m|)      (Eq. phase, vndf),
+ *    F = albedo (no angular Fresnel term is given in the paper).
+ */
+#ifndef GPSS_ORACLE_H
+#define GPSS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int nx, ny, nz;            /* nodes per axis (>= 2), x fastest            */
+  double bmin[3], bmax[3];   /* object bounding box = node-grid extent       */
+  const float* mean;         /* nx*ny*nz signed-distance mean mu             */
+  const float* var;          /* nx*ny*nz variance sigma^2 (> 0)              */
+  const float* albedo;       /* channels planes of nx*ny*nz, F in [0,1]      */
+  int channels;              /* 1 or 3                                       */
+  double length_scale;       /* isotropic SE correlation l (> 0)             */
+} orc_object;
+
+enum { ORC_LIGHT_DIRECTIONAL = 0, ORC_LIGHT_SKY = 1, ORC_LIGHT_UNIFORM = 2 };
+
+typedef struct {
+  int type;
+  double dir[3];             /* directional: unit vector pointing to the light */
+  double radiance[3];        /* irradiance (directional) or radiance scale    */
+} orc_light;
+
+enum { ORC_CAMERA_ORTHO = 0, ORC_CAMERA_PERSPECTIVE = 1 };
+
+typedef struct {
+  int type;
+  double eye[3], look_at[3], up[3];
+  double fov_y_deg, ortho_w, ortho_h;
+  int width, height;
+} orc_camera;
+
+typedef struct {
+  const orc_object* objs;
+  int n_objs;
+  orc_light light;
+} orc_scene;
+
+typedef struct {
+  int spp, max_bounces;
+  uint64_t seed;
+  double mix_R;              /* probability of the Beckmann vNDF component    */
+  int row_begin, row_end, row_step;
+  int col_begin, col_end;
+  int threads;               /* <= 0: all hardware threads                    */
+} orc_render_opts;
+
+typedef struct {
+  uint64_t paths, vertices, truncated;
+} orc_stats;
+
+/* ---- special functions (Sec. 3 notation: phi, Phi) ---------------------- */
+double orc_erfcx(double x);           /* exp(x^2) erfc(x)                        */
+double orc_log_ndtr(double u);        /* ln Phi(u), standard normal              */
+double orc_inv_mills(double u);       /* lambda(u) = phi(u)/Phi(u)               */
+
+/* ---- Philox4x32-10 (Salmon et al. 2011), used for seeded sampling -------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* ---- fields and medium -------------------------------------------------- */
+/* Returns 1 and fills the outputs if x lies in the object's box, else 0. */
+int orc_field(const orc_object* o, const double x[3], double* mu, double grad[3],
+              double* var, double albedo[3]);
+/* Projected area sigma(w) in the paper's local frame: mean gradient (0,0,G),
+ * roughness alpha_x, alpha_y, alpha_z (Eq. generalized_lambda times cos). */
+double orc_projected_area_local(const double w[3], double G, double ax, double ay, double az);
+/* NDF by quadrature of its definition, local frame (Eq. gdf_to_ndf, gdf). */
+double orc_ndf_local(const double m[3], double G, double ax, double ay, double az);
+/* Extinction of one object / the whole scene (extinctions of objects add). */
+double orc_sigma_t_object(const orc_object* o, const double x[3], const double d[3]);
+double orc_sigma_t(const orc_scene* s, const double x[3], const double d[3]);
+/* Phase function of object k at x: p (per channel, includes F) and the pdf
+ * of the sampling mixture over outgoing directions (Sec. 4.2.2, end).     */
+int orc_phase_eval(const orc_scene* s, int k, const double x[3], const double d[3],
+                   const double d2[3], double R, double p_out[3], double* pdf_out);
+/* Samples d2 with three uniforms; returns weight p/pdf (per channel) and pdf. */
+int orc_phase_sample(const orc_scene* s, int k, const double x[3], const double d[3],
+                     double R, const double u[3], double d2[3], double w_out[3],
+                     double* pdf_out);
+/* Optical depth and transmittance along o + t d, t in [0, tmax]. */
+double orc_optical_depth(const orc_scene* s, const double o[3], const double d[3], double tmax);
+double orc_transmittance(const orc_scene* s, const double o[3], const double d[3], double tmax);
+
+/* ---- rendering ------------------------------------------------------------ */
+/* Path tracer by regular tracking.  sum/sumsq are width*height*3 doubles
+ * (accumulated over samples of the selected pixels; others untouched).    */
+int orc_render(const orc_scene* s, const orc_camera* cam, const orc_render_opts* o,
+               double* sum, double* sumsq, orc_stats* st);
+/* Same paths rendered in scene a and scene b with identical random numbers;
+ * accumulates the per-path difference L_a - L_b (common random numbers). */
+int orc_render_diff(const orc_scene* a, const orc_scene* b, const orc_camera* cam,
+                    const orc_render_opts* o, double* sum, double* sumsq, orc_stats* st);
+
+/* Camera ray through pixel (px,py) at sub-pixel jitter (jx,jy) in [0,1). */
+void orc_camera_ray(const orc_camera* c, int px, int py, double jx, double jy,
+                    double org[3], double dir[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

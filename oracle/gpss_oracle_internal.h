@@ -1,0 +1,38 @@
+/* gpss_oracle_internal.h -- private declarations shared by the oracle's .c
+ * files.  TEST INFRASTRUCTURE ONLY (see gpss_oracle.h). */
+#ifndef GPSS_ORACLE_INTERNAL_H
+#define GPSS_ORACLE_INTERNAL_H
+
+#include <stdint.h>
+#include "gpss_oracle.h"
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_SQRT2 1.41421356237309504880
+#define ORC_SQRTPI 1.77245385090551602730
+
+typedef double (*orc_fn)(double, void*);
+
+/* Field values of one object at one point, with derived quantities. */
+typedef struct {
+  double mu, g[3], var, F[3];
+  double sigma;   /* sqrt(var)                         */
+  double alpha;   /* sqrt(2) sigma / l  (Eq. roughness) */
+  double G;       /* |grad mu|                          */
+  double nhat[3]; /* grad mu / G (0 when G == 0)        */
+} orc_fpt;
+
+int orc_point(const orc_object* o, const double x[3], orc_fpt* p);
+double orc_projected_area_world(const double d[3], const orc_fpt* p);
+double orc_ndf_world(const double m[3], const orc_fpt* p);
+double orc_sigma_t_point(const orc_fpt* p, const double d[3]);
+int orc_phase_eval_point(const orc_fpt* p, const double d[3], const double d2[3], double R,
+                         double p_out[3], double* pdf_out);
+int orc_phase_sample_point(const orc_fpt* p, const double d[3], double R, const double u[3],
+                           double d2[3], double w_out[3], double* pdf_out);
+double orc_integrate(orc_fn f, void* ctx, double a, double b, double abs_tol);
+double orc_integrate_rough(orc_fn f, void* ctx, double a, double b);
+double orc_erfinv(double v);
+void orc_uniform4(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t bounce,
+                  uint32_t purpose, uint32_t draw, double u[4]);
+
+#endif

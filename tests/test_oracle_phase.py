@@ -1,0 +1,110 @@
+"""Pins of the oracle's phase function and its sampling mixture (Eq. phase,
+Eq. microfacet_vndf and the mixture at the end of Sec. 4.2.2)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import chisquare
+
+import oracle
+from paper_2603_00280_gb300 import workloads as W
+from tests import helpers as H
+
+
+@pytest.fixture(scope="module")
+def hetero():
+    wl = W.heterogeneous(n=16)
+    return oracle.Scene(wl["scene"])
+
+
+@pytest.fixture(scope="module")
+def moderate():
+    """Roughness 0.3..3 (l = 0.05), where a product rule resolves the Beckmann vNDF."""
+    wl = W.heterogeneous(n=16, length_scale=0.05)
+    return oracle.Scene(wl["scene"])
+
+
+def _points(seed, n):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-0.4, 0.4, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d2 = rng.normal(size=(n, 3))
+    d2 /= np.linalg.norm(d2, axis=1, keepdims=True)
+    return x, d, d2
+
+
+def test_reciprocity(hetero):
+    """sigma_t(x,d) p(d,d2) = sigma_t(x,-d2) p(-d2,-d): the medium's scattering
+    kernel is symmetric (the paper states reciprocity for Eq. phase)."""
+    x, d, d2 = _points(1, 40)
+    p1, _ = oracle.phase_eval(hetero, 0, x, d, d2)
+    p2, _ = oracle.phase_eval(hetero, 0, x, -d2, -d)
+    s1 = oracle.sigma_t(hetero, x, d)
+    s2 = oracle.sigma_t(hetero, x, -d2)
+    np.testing.assert_allclose(s1[:, None] * p1, s2[:, None] * p2, rtol=1e-11, atol=1e-300)
+
+
+def _reflect(d, m):
+    return d - 2.0 * (d @ m) * m
+
+
+@pytest.mark.parametrize("seed", [2, 3, 4])
+def test_energy_and_pdf_normalisation(moderate, seed):
+    """int p(d,d2) dd2 = F and int pdf(d2) dd2 = 1, integrated over half-vectors
+    m on the hemisphere facing -d with the Jacobian dd2 = 4|d.m| dm."""
+    hetero = moderate
+    x, d, _ = _points(seed, 1)
+    x, d = x[0], d[0]
+    F = oracle.field(hetero, 0, x)["albedo"][0]
+    ms, wts = H.sphere_points(-d, 96, 96, cos_range=(0.0, 1.0))
+    d2 = np.array([_reflect(d, m) for m in ms])
+    p, pdf = oracle.phase_eval(hetero, 0, np.repeat(x[None], len(ms), 0), np.repeat(d[None], len(ms), 0), d2)
+    jac = 4.0 * np.abs(ms @ d)
+    assert np.sum(wts * p[:, 0] * jac) == pytest.approx(F, rel=2e-4)
+    assert np.sum(wts * pdf * jac) == pytest.approx(1.0, rel=2e-4)
+
+
+def test_sampler_histogram_matches_pdf(hetero):
+    """chi^2 of sampled half-vectors against the mixture pdf integrated over bins,
+    and the returned weight equals p/pdf at the sampled direction."""
+    x, d, _ = _points(5, 1)
+    x, d = x[0], d[0]
+    n = 20000
+    rng = np.random.default_rng(6)
+    u = rng.random((n, 3))
+    d2, w, pdf, ok = oracle.phase_sample(hetero, 0, np.repeat(x[None], n, 0), np.repeat(d[None], n, 0), u)
+    assert ok.all()
+    m = d2 - d
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    fx, fy, fz = H.frame(-d)
+    c = m @ fz
+    ph = np.mod(np.arctan2(m @ fy, m @ fx), 2 * math.pi)
+    nc, nphi = 8, 8
+    obs, _, _ = np.histogram2d(c, ph, bins=[np.linspace(0, 1, nc + 1), np.linspace(0, 2 * math.pi, nphi + 1)])
+    # expected bin probabilities by 8x8 Gauss-Legendre inside each bin
+    gx, gw = np.polynomial.legendre.leggauss(8)
+    exp_p = np.zeros((nc, nphi))
+    for i in range(nc):
+        cc = (i + 0.5 + 0.5 * gx) / nc
+        cw = 0.5 * gw / nc
+        for j in range(nphi):
+            pp = (j + 0.5 + 0.5 * gx) * 2 * math.pi / nphi
+            pw = 0.5 * gw * 2 * math.pi / nphi
+            CC, PP = np.meshgrid(cc, pp, indexing="ij")
+            WW = np.outer(cw, pw)
+            s = np.sqrt(1 - CC ** 2)
+            mm = (s * np.cos(PP))[..., None] * fx + (s * np.sin(PP))[..., None] * fy + CC[..., None] * fz
+            mm = mm.reshape(-1, 3)
+            dd2 = np.array([_reflect(d, q) for q in mm])
+            _, pdf_b = oracle.phase_eval(hetero, 0, np.repeat(x[None], len(mm), 0), np.repeat(d[None], len(mm), 0), dd2)
+            exp_p[i, j] = np.sum(WW.reshape(-1) * pdf_b * 4 * np.abs(mm @ d))
+    assert exp_p.sum() == pytest.approx(1.0, rel=1e-3)
+    stat, pval = chisquare(obs.ravel(), exp_p.ravel() / exp_p.sum() * n)
+    assert pval > 1e-4, (stat, pval)
+    # weight consistency and unbiasedness of E[weight] = F
+    pe, pdfe = oracle.phase_eval(hetero, 0, np.repeat(x[None], 50, 0), np.repeat(d[None], 50, 0), d2[:50])
+    np.testing.assert_allclose(pdf[:50], pdfe, rtol=1e-9)
+    np.testing.assert_allclose(w[:50, 0], pe[:, 0] / pdfe, rtol=1e-9)
+    F = oracle.field(hetero, 0, x)["albedo"][0]
+    assert abs(w[:, 0].mean() - F) < 4 * w[:, 0].std() / math.sqrt(n)
