@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the GPSS renderer on GB300: million path vertices per second.
+
+A *path vertex* is one real scattering event of a path (free flight into it,
+next-event estimation and phase sampling at it).  One benchmark step is one full
+forward render of the workload; the default workload is the heterogeneous GPSS
+(128^3 sphere-noise mean, variance ramp, 512x512, 64 spp, 32 bounces, sky light).
+
+Output: one JSON line (rank 0).  ``value`` is the whole-job throughput with the
+scene resident in HBM; ``e2e`` is the same metric through the C-ABI with host
+buffers (grids uploaded and the image read back every step); ``roofline`` is
+the FP32-issue bound of the render kernel; ``cpu_baseline`` is the FP64 oracle
+on a bounded sample of the same workload on this machine's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M path-vertices/s at 1 GB300 (fwd; fwd+adjoint) and fraction of FP32-issue roofline"
+UNIT = "M path-vertices/s"
+# Algorithmic FP32 work per unit: one extinction
+# evaluation (field fetch + sigma_t) per tentative collision, plus the shading of
+# each real vertex (phase sampling + NEE phase evaluation + MIS).
+OPS_PER_SIGMA_T = 130
+OPS_PER_VERTEX_SHADING = 330
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["heterogeneous", "tiny_slab"], default="heterogeneous")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, seed_offset=0):
+    from paper_2603_00280_gb300 import workloads as W
+    if name == "tiny_slab":
+        wl = W.tiny_slab()
+    else:
+        wl = W.heterogeneous()
+    wl["opts"] = dict(wl["opts"], seed=wl["opts"]["seed"] + seed_offset)
+    return wl
+
+
+def config_of(wl, l2):
+    cam, opts = wl["camera"], wl["opts"]
+    obj = wl["scene"]["objects"][0]
+    return {"workload": wl["name"], "grid": list(obj["mean"].shape[::-1]), "image": [cam["width"], cam["height"]],
+            "spp": opts["spp"], "max_bounces": opts["max_bounces"], "light": wl["scene"]["light"]["type"],
+            "l2": l2}
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- roofline
+def peak_fp32_tops(torch):
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    mhz = None
+    try:
+        mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+        src = "MEASURED_PEAKS.json sm_max_mhz"
+    except Exception:
+        src = "nominal 2070 MHz"
+        mhz = 2070.0
+    return sms * 128 * mhz * 1e6 / 1e12, sms, mhz, src
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2603_00280_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(workload_name):
+    """DRAM bytes per launch of the render kernel from a committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+        e = t[workload_name]
+        if e.get("source_hash") == kernel_source_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def algorithmic_ops(st):
+    evals = st["vertices"] + st["null_collisions"] + st["shadow_steps"]
+    return OPS_PER_SIGMA_T * evals + OPS_PER_VERTEX_SHADING * st["vertices"]
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+def oracle_sample(wl, target_seconds, threads=0):
+    """Renders a bounded block of pixels of the workload at its full spp and
+    bounce limit with the FP64 oracle; returns (vertices/s, description, cores)."""
+    import oracle
+    O = oracle.Scene(wl["scene"])
+    cam, opts = wl["camera"], wl["opts"]
+    H, W = cam["height"], cam["width"]
+    cy, cx = H // 2, W // 2
+    cols = 8
+    t0 = time.perf_counter()
+    _, _, st = oracle.render(O, cam, opts, rows=(cy, cy + 1, 1), cols=(cx - cols // 2, cx + cols // 2), threads=threads)
+    dt = time.perf_counter() - t0
+    per_px = dt / cols
+    n_rows = max(1, min(H // 4, int(target_seconds / max(per_px * 16, 1e-6))))
+    step = max(1, (H // 2) // n_rows)
+    rows = (H // 4, H // 4 + n_rows * step, step)
+    c0, c1 = cx - 8, cx + 8
+    t0 = time.perf_counter()
+    _, _, st = oracle.render(O, cam, opts, rows=rows, cols=(c0, c1), threads=threads)
+    dt = time.perf_counter() - t0
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
+    desc = "%d pixels (rows %d:%d:%d, cols %d:%d) x %d spp, %d paths, %d vertices, %.1f s" % (
+        n_rows * 16, rows[0], rows[1], rows[2], c0, c1, opts["spp"], st["paths"], st["vertices"], dt)
+    return st["vertices"] / dt / 1e6, desc, cores, dt
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, cores, dt = oracle_sample(wl, max(2.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup))))
+        if i >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.median(v for v, _ in vals)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(d for _, d in vals),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_of(wl, "n/a (CPU)"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2603_00280_gb300 import gpss
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    gpss.load()
+    wl = workload(args.workload, seed_offset=1000 * rank)
+    cam, opts = wl["camera"], wl["opts"]
+    S = gpss.Scene(wl["scene"])
+    H, W = cam["height"], cam["width"]
+    image = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+    for _ in range(args.warmup):
+        gpss.render(S, cam, opts, image=image, stats=False)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, kernel_ms, verts, ops = [], [], 0, 0
+    stats = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, stats = gpss.render(S, cam, opts, image=image, stats=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kernel_ms.append(stats["ms"])
+        verts += stats["vertices"]
+        ops += algorithmic_ops(stats)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms, float(verts)], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tmax[1:2], op=dist.ReduceOp.SUM)
+        t = tmax
+    total_ms, all_verts = float(t[0]), float(t[1])
+    value = all_verts / (total_ms / 1e3) / 1e6
+
+    # e2e through the C-ABI with host buffers: upload the grids from pinned host
+    # memory (scene update + majorant rebuild) and read the image back, every step
+    e2e = None
+    if not args.no_e2e:
+        objs = []
+        h2d = 0
+        for o in wl["scene"]["objects"]:
+            d = {k: o[k] for k in ("bbox_min", "bbox_max", "length_scale")}
+            for k in ("mean", "var", "albedo"):
+                d[k] = torch.from_numpy(np.ascontiguousarray(o[k])).pin_memory()
+                h2d += d[k].numel() * 4
+            objs.append(d)
+        host_img = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+        e2e_ms, e2e_verts = [], 0
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S.update(objs)
+            _, _, st = gpss.render(S, cam, opts, image=host_img.numpy(), stats=True)
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                e2e_ms.append(1e3 * (t1 - t0))
+                e2e_verts += st["vertices"]
+        et = torch.tensor([sum(e2e_ms), float(e2e_verts)], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(et[0:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(et[1:2], op=dist.ReduceOp.SUM)
+        e2e = {"value": float(et[1]) / (float(et[0]) / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": H * W * 3 * 4}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, sms, mhz, peak_src = peak_fp32_tops(torch)
+    achieved = ops / (sum(kernel_ms) / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": measured_traffic(wl["name"]),
+            "note": "FP32 issue roofline: %d SMs x 128 lanes x %.0f MHz (%s), one FMA = one op; algorithmic ops = "
+                    "%d per extinction evaluation + %d per vertex" % (sms, mhz, peak_src, OPS_PER_SIGMA_T,
+                                                                       OPS_PER_VERTEX_SHADING)}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl, "flushed between steps (256 MB write)"),
+           "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+           "clocks": clk,
+           "work": {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
+                    "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
+                    "kernel_ms": statistics.mean(kernel_ms)}}
+    if world == 1 and not args.no_cpu_baseline:
+        v, desc, cores, _ = oracle_sample(wl, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,203 @@
+/*
+ * gpss.h -- C-ABI of the GB300 (sm_103a) renderer for Gaussian process
+ * statistical surfaces (GPSS), after "Macrofacet Theory for Gaussian Process
+ * Statistical Surfaces" (Huang, Cui, Wang, Yan).
+ *
+ * A GPSS object is a Gaussian process f ~ GP(mu(x), kappa) with the
+ * squared-exponential kernel (Eq. se_kernel).  The library renders it as the
+ * classic exponential participating medium the paper derives (Sec. 4):
+ *   extinction   sigma_t(x,d) = rho(x) sigma(d)          (Eq. generalized_sigma_t)
+ *   density      rho = phi(mu;0,sigma^2)/Phi(mu;0,sigma^2)  (Eq. macro_sigma_t)
+ *   proj. area   sigma(d) = Lambda(d) cos(theta)           (Eq. generalized_lambda)
+ *   NDF          D(m) = int_0^inf t^3 P(t m) dt            (Eq. gdf_to_ndf, macro_ndf)
+ *   phase        p(d,d') = F D_d(m) / (4 |d.m|)            (Eq. phase, microfacet_vndf)
+ * with per-pixel Monte Carlo path tracing ("null scattering", Sec. 5): delta
+ * tracking, ratio-tracking next-event estimation, and the mixture sampler of
+ * Sec. 4.2.2 (Beckmann visible normals with probability R, else uniform).
+ *
+ * Conventions
+ *  - d is the marching direction of a ray (the paper's omega_o for extinction;
+ *    for the phase function omega_o = incoming d, omega_i = outgoing d').
+ *  - Grids are node-centred over the object's box, x fastest:
+ *    index = i + nx*(j + ny*k); fields are interpolated trilinearly and the
+ *    normal direction is the gradient of the interpolated mean.
+ *  - Unless stated otherwise, pointers to per-element data are DEVICE pointers
+ *    and every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream).  The caller owns every buffer it passes.
+ *  - Errors: every function returns a gpss_status; no exception crosses the
+ *    ABI.  Arguments are validated before any work is queued; a failing call
+ *    leaves outputs unspecified.  gpss_last_error() gives a message for the
+ *    calling thread.  CUDA faults surface as GPSS_ERR_CUDA on the call that
+ *    observes them.
+ */
+#ifndef GPSS_H
+#define GPSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpss_scene_s* gpss_scene;
+typedef struct gpss_batch_s* gpss_batch;
+typedef void* gpss_stream; /* cudaStream_t */
+
+typedef enum {
+  GPSS_OK = 0,
+  GPSS_ERR_INVALID_ARG = 1,
+  GPSS_ERR_CUDA = 2,
+  GPSS_ERR_OOM = 3,
+  GPSS_ERR_TIMEOUT = 4,
+  GPSS_ERR_UNSUPPORTED = 5
+} gpss_status;
+
+/* One GPSS object.  mean/variance/albedo may be host or device memory (they are
+ * copied by gpss_scene_create / gpss_scene_update with cudaMemcpyDefault). */
+typedef struct {
+  int nx, ny, nz;              /* nodes per axis, each >= 2                        */
+  float bbox_min[3], bbox_max[3];
+  const float* mean;           /* nx*ny*nz mean mu (a signed distance)             */
+  const float* variance;       /* nx*ny*nz variance sigma^2, finite and > 0        */
+  const float* albedo;         /* albedo_channels planes of nx*ny*nz, F in [0,1]   */
+  int albedo_channels;         /* 1 or 3                                           */
+  float length_scale;          /* isotropic SE correlation l > 0 (Eq. roughness)   */
+} gpss_object_desc;
+
+typedef enum { GPSS_LIGHT_DIRECTIONAL = 0, GPSS_LIGHT_SKY = 1, GPSS_LIGHT_UNIFORM = 2 } gpss_light_type;
+
+/* Directional: dir = unit vector toward the light, radiance = irradiance (RGB).
+ * Sky: for w_z >= 0 lerp((1,1,1), (0.35,0.55,1), w_z), else (0.25,0.22,0.20),
+ * times radiance.  Uniform: constant radiance in every direction. */
+typedef struct {
+  int type;
+  float dir[3];
+  float radiance[3];
+} gpss_light_desc;
+
+typedef enum { GPSS_CAMERA_ORTHO = 0, GPSS_CAMERA_PERSPECTIVE = 1 } gpss_camera_type;
+
+/* forward f = normalize(look_at - eye), right = normalize(f x up),
+ * image-up = right x f; pixel (0,0) is the top-left; ndc x = 2(px+jx)/W - 1,
+ * y = 1 - 2(py+jy)/H.  Ortho: origin = eye + x ortho_w/2 right + y ortho_h/2 up,
+ * direction f.  Perspective: origin eye, direction
+ * normalize(f + x tan(fov_y/2) W/H right + y tan(fov_y/2) up). */
+typedef struct {
+  int type;
+  float eye[3], look_at[3], up[3];
+  float fov_y_deg, ortho_w, ortho_h;
+  int width, height;
+} gpss_camera;
+
+/* flags */
+#define GPSS_FLAG_KEEP_PATH_RADIANCE 1u /* keep per-path radiance for a later adjoint */
+
+typedef struct {
+  int spp;                 /* samples per pixel, >= 1                               */
+  int max_bounces;         /* max real scattering events per path, >= 1 (no RR)     */
+  uint64_t seed;           /* Philox key                                            */
+  float mix_R;             /* Beckmann share of the sampling mixture, 0 < R < 1     */
+  uint32_t flags;
+} gpss_render_opts;
+
+typedef struct {
+  uint64_t paths, vertices, null_collisions, shadow_steps, majorant_cells, truncated, aborted;
+  float ms;                /* device time of the render kernel                      */
+} gpss_stats;
+
+/* ---------------------------------------------------------------- scenes */
+
+/* Creates a scene: validates the descriptors, copies the grids into the
+ * library's layout ((mean, variance) interleaved per node, albedo planes) and
+ * builds the majorant grid (an upper bound of sigma_t over all directions per
+ * cell of `majorant_brick` x the finest field cell; 0 selects 1).  1 <= n_objs <= 4.
+ * light may be NULL (directional light from +z, irradiance 1).  Synchronises
+ * `stream` (device-side validation).  INVALID_ARG on bad sizes, non-positive or
+ * non-finite variance, albedo outside [0,1], channels not 1/3, l <= 0. */
+gpss_status gpss_scene_create(const gpss_object_desc* objs, int n_objs, const gpss_light_desc* light,
+                              int majorant_brick, gpss_stream stream, gpss_scene* out);
+/* Re-copies the grids (same sizes as at creation) and rebuilds the majorant. */
+gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* objs, int n_objs, gpss_stream stream);
+/* Frees the scene.  Call after the stream's work on it has completed. */
+gpss_status gpss_scene_destroy(gpss_scene s);
+/* Majorant grid geometry: dims[3] cells and their values (device copy, may be NULL). */
+gpss_status gpss_scene_majorant(gpss_scene s, int dims[3], float* values, gpss_stream stream);
+
+/* ---------------------------------------------------------------- rendering */
+
+/* Forward render (Sec. 5 integrator on the Sec. 4 medium).  image: H*W*3 floats,
+ * overwritten with the per-pixel mean radiance; sqsum (nullable): H*W*3 floats,
+ * overwritten with the per-pixel sum over samples of the squared path radiance.
+ * image/sqsum may be device or host memory (host: rendered into a scene-owned
+ * film, then copied back).  stats (host, nullable): filled after the stream is
+ * synchronised.  With GPSS_FLAG_KEEP_PATH_RADIANCE the scene keeps each path's
+ * radiance for gpss_render_adjoint with the same camera and options. */
+gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts, float* image,
+                        float* sqsum, gpss_stats* stats, gpss_stream stream);
+
+/* Path-replay adjoint.  d_image: H*W*3 (dLoss/dimage, device).  Gradients are
+ * ACCUMULATED (+=) into d_mean, d_variance (nx*ny*nz each, object 0), d_albedo
+ * (channels planes) and d_length_scale (1 float); any output may be NULL.
+ * Paths are replayed from the same random numbers as gpss_render with equal
+ * camera and options. */
+gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts,
+                                const float* d_image, float* d_mean, float* d_variance, float* d_albedo,
+                                float* d_length_scale, gpss_stats* stats, gpss_stream stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/* A batch renders n scenes (each with its own camera and options) in one
+ * persistent launch captured in a CUDA graph.  Launch shape chosen by the
+ * library's autotuner (0 = autotune, else the given block size). */
+gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_camera* cams, const gpss_render_opts* opts,
+                              int n, int block_size, gpss_stream stream, gpss_batch* out);
+/* images[i]: device H_i*W_i*3 floats (overwritten). */
+gpss_status gpss_batch_render(gpss_batch b, float* const* images, gpss_stream stream);
+gpss_status gpss_batch_destroy(gpss_batch b);
+
+/* ---------------------------------------------------------------- deterministic evaluators
+ * Per-query kernels used by the parity tests; all arrays are device memory. */
+
+/* sigma_t(x, d) summed over objects (Eq. generalized_sigma_t); pos3, dir3: n*3. */
+gpss_status gpss_eval_sigma_t(gpss_scene s, int n, const float* pos3, const float* dir3, float* out,
+                              gpss_stream stream);
+/* Phase function of object k at x (Eq. phase): p3_out n*3 (includes F per channel),
+ * pdf_out n (density of the sampling mixture over d_out). */
+gpss_status gpss_eval_phase(gpss_scene s, int object, int n, const float* pos3, const float* d_in3,
+                            const float* d_out3, float mix_R, float* p3_out, float* pdf_out, gpss_stream stream);
+/* Samples the mixture with the given uniforms u3 (n*3): d_out3, weight p/pdf (n*3), pdf (n). */
+gpss_status gpss_sample_phase(gpss_scene s, int object, int n, const float* pos3, const float* d_in3,
+                              const float* u3, float mix_R, float* d_out3, float* w3_out, float* pdf_out,
+                              gpss_stream stream);
+/* NDF in the paper's local frame, mean gradient (0,0,G), roughness ax, ay, az (Eq. macro_ndf). */
+gpss_status gpss_eval_ndf(int n, const float* m3, float G, float ax, float ay, float az, float* out,
+                          gpss_stream stream);
+/* Projected area sigma(w) in the same frame (Eq. generalized_lambda times cos). */
+gpss_status gpss_eval_projected_area(int n, const float* w3, float G, float ax, float ay, float az, float* out,
+                                     gpss_stream stream);
+/* Transmittance exp(-int_0^tmax sigma_t) by per-cell Gauss-Legendre quadrature (Eq. sm2tr). */
+gpss_status gpss_eval_transmittance(gpss_scene s, int n, const float* org3, const float* dir3, const float* tmax,
+                                    float* out, gpss_stream stream);
+/* Ratio-tracking estimate of the same transmittance (mean of `samples` estimates),
+ * using the renderer's majorant traversal. */
+gpss_status gpss_estimate_transmittance(gpss_scene s, int n, const float* org3, const float* dir3,
+                                        const float* tmax, int samples, uint64_t seed, float* mean_out,
+                                        gpss_stream stream);
+/* Delta-tracking free-flight distances along each ray (INFINITY = no collision),
+ * `samples` per ray: out n*samples. */
+gpss_status gpss_sample_free_flight(gpss_scene s, int n, const float* org3, const float* dir3, int samples,
+                                    uint64_t seed, float* out, gpss_stream stream);
+/* Philox4x32-10 (Salmon et al. 2011): ctr4 n*4, key2 n*2, out4 n*4 (uint32). */
+gpss_status gpss_philox4x32_10(int n, const uint32_t* ctr4, const uint32_t* key2, uint32_t* out4,
+                               gpss_stream stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gpss_last_error(void);
+/* Library version, (major << 16) | minor. */
+int gpss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,658 @@
+// gpss_device.cuh -- device-side data layout and arithmetic of the GPSS medium.
+//
+// Everything here is FP32 CUDA for sm_103a.  It implements, from the paper
+// "Macrofacet Theory for Gaussian Process Statistical Surfaces":
+//   - trilinear field fetch of the mean (a signed distance), variance and albedo
+//     grids, with the analytic gradient of the interpolant (Sec. 4: the normal is
+//     the normalised gradient of the SDF);
+//   - the extinction sigma_t = rho * sigma(d)  (Eq. generalized_sigma_t,
+//     Eq. generalized_lambda), rho = phi/Phi of mu/sigma over sigma;
+//   - the NDF D(m) = int_0^inf t^3 P(t m) dt (Eq. gdf_to_ndf with Eq. gdf) in closed
+//     form through moments M_k(q) = int_0^inf s^k exp(-s^2 + 2 q s) ds;
+//   - the conductor phase function (Eq. phase, Eq. microfacet_vndf) and the
+//     sampling mixture R * Beckmann-vNDF + (1-R) * uniform hemisphere (end of
+//     Sec. 4.2.2);
+//   - Philox4x32-10 (Salmon et al., SC'11) keyed by (seed) with counter
+//     (pixel, sample, bounce | purpose << 16, draw);
+//   - Amanatides-Woo traversal of the majorant grid.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace gpss {
+
+constexpr int kMaxObjects = 4;
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kInv4Pi = 0.07957747154594767280f;
+constexpr float kInvSqrtPi = 0.56418958354775628695f;
+constexpr float kSqrtPi = 1.77245385090551602730f;
+constexpr float kSqrt2 = 1.41421356237309504880f;
+constexpr float kInvSqrt2 = 0.70710678118654752440f;
+constexpr float kSqrt2OverPi = 0.79788456080286535588f;
+constexpr float kInvPi32 = 0.17958712212516656f;  // pi^(-3/2)
+
+// ---------------------------------------------------------------- layouts
+
+// One GPSS object: node-centred grids over [bmin, bmax], x fastest.
+struct ObjectDev {
+  float bmin[3], bmax[3];
+  float inv_h[3];          // (n-1)/(bmax-bmin)
+  int n[3];
+  int channels;            // albedo channels, 1 or 3
+  float alpha_scale;       // sqrt(2)/l: alpha = sigma * alpha_scale (Eq. roughness)
+  const float2* mv;        // (mean, variance) per node
+  const float* albedo;     // channels planes
+};
+
+// Majorant grid: piecewise-constant upper bound of sigma_t over all directions.
+struct MajorantDev {
+  float gmin[3];
+  float cell[3];
+  float inv_cell[3];
+  int dims[3];
+  const float* maj;
+};
+
+enum LightKind : int { kLightDirectional = 0, kLightSky = 1, kLightUniform = 2 };
+
+struct LightDev {
+  int kind;
+  float dir[3];            // directional: unit vector toward the light
+  float radiance[3];
+};
+
+struct SceneDev {
+  int n_objs;
+  ObjectDev obj[kMaxObjects];
+  MajorantDev mg;
+  LightDev light;
+};
+
+struct CameraDev {
+  int ortho;
+  float eye[3], fwd[3], right[3], up[3];
+  float half_w, half_h;    // ortho: half film extent; perspective: tan(fov/2)*aspect, tan(fov/2)
+  int width, height;
+};
+
+// ---------------------------------------------------------------- small vector helpers
+struct V3 { float x, y, z; };
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 normalize(V3 a) { return rsqrtf(dot(a, a)) * a; }
+__device__ __forceinline__ V3 fma3(float s, V3 a, V3 b) { return {fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)}; }
+
+// ---------------------------------------------------------------- Philox4x32-10
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform in (0,1): 24 bits, centred
+__device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
+
+enum Purpose : uint32_t { kPurposeCamera = 0, kPurposeFlight = 1, kPurposeNee = 2, kPurposePhase = 3 };
+
+// Counter-based stream for one path: (pixel, sample, bounce|purpose<<16, draw).
+struct Rng {
+  uint32_t k0, k1, pixel, sample, tag, draw;
+  uint32_t b0, b1, b2, b3;
+  int avail;
+  __device__ __forceinline__ void init(uint64_t seed, uint32_t px, uint32_t s) {
+    k0 = (uint32_t)seed;
+    k1 = (uint32_t)(seed >> 32);
+    pixel = px;
+    sample = s;
+    tag = 0;
+    draw = 0;
+    avail = 0;
+  }
+  __device__ __forceinline__ void start(uint32_t bounce, uint32_t purpose) {
+    tag = (bounce & 0xFFFFu) | (purpose << 16);
+    draw = 0;
+    avail = 0;
+  }
+  __device__ __forceinline__ float next() {
+    if (avail == 0) {
+      const U4 r = philox4x32_10(U4{pixel, sample, tag, draw}, k0, k1);
+      ++draw;
+      b0 = r.x; b1 = r.y; b2 = r.z; b3 = r.w;
+      avail = 4;
+    }
+    const uint32_t v = b0;
+    b0 = b1; b1 = b2; b2 = b3;
+    --avail;
+    return u01(v);
+  }
+};
+
+// ---------------------------------------------------------------- special functions
+// lambda(u) = phi(u)/Phi(u) = sqrt(2/pi) / erfcx(-u/sqrt2)   (inverse Mills ratio)
+__device__ __forceinline__ float inv_mills(float u) { return kSqrt2OverPi / erfcxf(-u * kInvSqrt2); }
+
+// psi(a) = exp(-a^2)/(2 sqrt(pi)) - (a/2) erfc(a) = E[max(0, Z/sqrt2 - a)] with Z ~ N(0,1),
+// so the projected area is sigma(d) = alpha * psi((d . grad mu)/alpha).  For a > 2 the
+// difference cancels; there psi = erfc(a) * K(sqrt2 a) / (2 sqrt2) with Laplace's continued
+// fraction K(y) = 1/(y + 2/(y + 3/(y + ...))) of the Mills ratio (20 terms).
+__device__ __forceinline__ float psi(float a) {
+  if (a <= 2.0f) return fmaf(-0.5f * a, erfcf(a), 0.5f * kInvSqrtPi * expf(-a * a));
+  const float y = kSqrt2 * a;
+  float r = 0.0f;
+#pragma unroll
+  for (int k = 20; k >= 1; --k) r = (float)k / (y + r);
+  return erfcf(a) * r * (0.5f * kInvSqrt2);
+}
+
+// ---------------------------------------------------------------- fields
+struct Field {
+  float mu, var;
+  V3 g;        // gradient of the mean interpolant
+};
+
+// Cell lookup + trilinear weights; returns the node index of the cell's corner 000.
+__device__ __forceinline__ int cell_of(const ObjectDev& o, V3 x, float& wx, float& wy, float& wz) {
+  const float fx = (x.x - o.bmin[0]) * o.inv_h[0];
+  const float fy = (x.y - o.bmin[1]) * o.inv_h[1];
+  const float fz = (x.z - o.bmin[2]) * o.inv_h[2];
+  const int ix = min(max((int)floorf(fx), 0), o.n[0] - 2);
+  const int iy = min(max((int)floorf(fy), 0), o.n[1] - 2);
+  const int iz = min(max((int)floorf(fz), 0), o.n[2] - 2);
+  wx = fminf(fmaxf(fx - (float)ix, 0.0f), 1.0f);
+  wy = fminf(fmaxf(fy - (float)iy, 0.0f), 1.0f);
+  wz = fminf(fmaxf(fz - (float)iz, 0.0f), 1.0f);
+  return ix + o.n[0] * (iy + o.n[1] * iz);
+}
+
+__device__ __forceinline__ bool inside(const ObjectDev& o, V3 x) {
+  return x.x >= o.bmin[0] && x.x <= o.bmax[0] && x.y >= o.bmin[1] && x.y <= o.bmax[1] &&
+         x.z >= o.bmin[2] && x.z <= o.bmax[2];
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ Field fetch(const ObjectDev& o, V3 x) {
+  float wx, wy, wz;
+  const int b = cell_of(o, x, wx, wy, wz);
+  const int sx = 1, sy = o.n[0], sz = o.n[0] * o.n[1];
+  const float2 v000 = __ldg(o.mv + b), v100 = __ldg(o.mv + b + sx);
+  const float2 v010 = __ldg(o.mv + b + sy), v110 = __ldg(o.mv + b + sy + sx);
+  const float2 v001 = __ldg(o.mv + b + sz), v101 = __ldg(o.mv + b + sz + sx);
+  const float2 v011 = __ldg(o.mv + b + sz + sy), v111 = __ldg(o.mv + b + sz + sy + sx);
+  // mean: interpolate along x, keep the x-differences for the gradient
+  const float m00 = lerpf(v000.x, v100.x, wx), m10 = lerpf(v010.x, v110.x, wx);
+  const float m01 = lerpf(v001.x, v101.x, wx), m11 = lerpf(v011.x, v111.x, wx);
+  const float d00 = v100.x - v000.x, d10 = v110.x - v010.x, d01 = v101.x - v001.x, d11 = v111.x - v011.x;
+  const float m0 = lerpf(m00, m10, wy), m1 = lerpf(m01, m11, wy);
+  Field f;
+  f.mu = lerpf(m0, m1, wz);
+  f.g.x = lerpf(lerpf(d00, d10, wy), lerpf(d01, d11, wy), wz) * o.inv_h[0];
+  f.g.y = lerpf(m10 - m00, m11 - m01, wz) * o.inv_h[1];
+  f.g.z = (m1 - m0) * o.inv_h[2];
+  const float s00 = lerpf(v000.y, v100.y, wx), s10 = lerpf(v010.y, v110.y, wx);
+  const float s01 = lerpf(v001.y, v101.y, wx), s11 = lerpf(v011.y, v111.y, wx);
+  f.var = lerpf(lerpf(s00, s10, wy), lerpf(s01, s11, wy), wz);
+  return f;
+}
+
+// Albedo (F of Eq. phase) at x, per channel.
+__device__ __forceinline__ V3 fetch_albedo(const ObjectDev& o, V3 x) {
+  float wx, wy, wz;
+  const int b = cell_of(o, x, wx, wy, wz);
+  const int sy = o.n[0], sz = o.n[0] * o.n[1];
+  const int plane = sz * o.n[2];
+  float c[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    if (ch >= o.channels) { c[ch] = c[0]; continue; }
+    const float* a = o.albedo + ch * plane + b;
+    const float a0 = lerpf(lerpf(__ldg(a), __ldg(a + 1), wx), lerpf(__ldg(a + sy), __ldg(a + sy + 1), wx), wy);
+    const float a1 = lerpf(lerpf(__ldg(a + sz), __ldg(a + sz + 1), wx), lerpf(__ldg(a + sz + sy), __ldg(a + sz + sy + 1), wx), wy);
+    c[ch] = lerpf(a0, a1, wz);
+  }
+  return {c[0], c[1], c[2]};
+}
+
+// ---------------------------------------------------------------- extinction
+// Derived quantities of a field sample used by sigma_t and the phase function.
+struct Local {
+  float sigma;   // sqrt(var)
+  float alpha;   // sqrt(2) sigma / l
+  float rho;     // lambda(mu/sigma)/sigma
+};
+
+__device__ __forceinline__ Local local_of(const ObjectDev& o, const Field& f) {
+  Local l;
+  l.sigma = sqrtf(f.var);
+  l.alpha = l.sigma * o.alpha_scale;
+  l.rho = inv_mills(f.mu / l.sigma) / l.sigma;
+  return l;
+}
+
+// sigma(d) = Lambda(d) cos(theta) = alpha psi(d . grad mu / alpha)
+__device__ __forceinline__ float projected_area(V3 d, const Field& f, float alpha) {
+  return alpha * psi(dot(d, f.g) / alpha);
+}
+
+// sigma_t of one object at x for direction d (0 outside its box); fills f/l.
+__device__ __forceinline__ float sigma_t_object(const ObjectDev& o, V3 x, V3 d, Field& f, Local& l) {
+  f = fetch(o, x);
+  l = local_of(o, f);
+  return l.rho * projected_area(d, f, l.alpha);
+}
+
+// ---------------------------------------------------------------- NDF
+// Moments M3, M4 of exp(-s^2 + 2 q s) on [0, inf), returned scaled:
+//   q >= 0:        Mk * exp(-q^2), forward recurrence M_{k+1} = q M_k + (k/2) M_{k-1}
+//                  from M0 = sqrt(pi)/2 (1 + erf q), M1 = q M0 + exp(-q^2)/2 (all terms
+//                  positive, no cancellation);
+//   -3 <= q < 0:   Mk from a degree-10 Chebyshev fit of ln Mk (moment_fit.inc; there the
+//                  recurrence cancels in FP32);
+//   q < -3:        Mk from M0 = sqrt(pi)/2 erfcx(-q) and the continued fraction
+//                  M_k/M_{k-1} = (k/2)/(|q| + M_{k+1}/M_k) (24 terms).
+#include "moment_fit.inc"
+
+__device__ __forceinline__ float cheb_eval(const float* c, float x) {
+  float b1 = 0.0f, b2 = 0.0f;
+  const float x2 = 2.0f * x;
+#pragma unroll
+  for (int k = kMomentFitDeg; k >= 1; --k) {
+    const float t = fmaf(x2, b1, c[k] - b2);
+    b2 = b1;
+    b1 = t;
+  }
+  return fmaf(x, b1, c[0] - b2);
+}
+
+__device__ __forceinline__ void moments34(float q, float& m3, float& m4) {
+  if (q >= 0.0f) {
+    const float e = expf(-q * q);
+    const float M0 = 0.5f * kSqrtPi * (1.0f + erff(q));
+    const float M1 = fmaf(q, M0, 0.5f * e);
+    const float M2 = fmaf(q, M1, 0.5f * M0);
+    m3 = fmaf(q, M2, M1);
+    m4 = fmaf(q, m3, 1.5f * M2);
+  } else if (q >= kMomentFitLo) {
+    const float x = fmaf(q - kMomentFitLo, 2.0f / (kMomentFitHi - kMomentFitLo), -1.0f);
+    m3 = expf(cheb_eval(c_lnM3_cheb, x));
+    m4 = expf(cheb_eval(c_lnM4_cheb, x));
+  } else {
+    const float x = -q;
+    float r = 0.0f, r1 = 0.0f, r2 = 0.0f, r3 = 0.0f, r4 = 0.0f;
+#pragma unroll
+    for (int k = 24; k >= 1; --k) {
+      r = (0.5f * (float)k) / (x + r);
+      if (k == 4) r4 = r;
+      if (k == 3) r3 = r;
+      if (k == 2) r2 = r;
+      if (k == 1) r1 = r;
+    }
+    const float M0 = 0.5f * kSqrtPi * erfcxf(x);
+    m3 = M0 * r1 * r2 * r3;
+    m4 = m3 * r4;
+  }
+}
+
+// Isotropic world-frame NDF: g ~ N(grad mu, alpha^2/2 I).  With a = m . grad mu,
+// b^2 = |grad mu x m|^2, q = a/alpha:  D = alpha/pi^(3/2) * E * M3(q), where
+// E = exp(-b^2/alpha^2) for q >= 0 (moments scaled by exp(-q^2)) and
+// E = exp(-|grad mu|^2/alpha^2) for q < 0.   (Appendix A result, rearranged.)
+__device__ __forceinline__ float ndf_iso(V3 m, V3 g, float alpha, float* m4_over_m3 = nullptr) {
+  const float inv_a = 1.0f / alpha;
+  const float q = dot(m, g) * inv_a;
+  float m3, m4;
+  moments34(q, m3, m4);
+  float E;
+  if (q >= 0.0f) {
+    const V3 c = cross(g, m);
+    E = expf(-dot(c, c) * inv_a * inv_a);
+  } else {
+    E = expf(-dot(g, g) * inv_a * inv_a);
+  }
+  if (m4_over_m3) *m4_over_m3 = m4 / m3;
+  return alpha * kInvPi32 * E * m3;
+}
+
+// Local-frame NDF with mean gradient (0,0,G) and roughness alpha_x, alpha_y, alpha_z
+// (Eq. macro_ndf): D = exp(-C) M3(q) / (pi^(3/2) ax ay az A^2),  q = B/sqrt(A).
+__device__ __forceinline__ float ndf_local(V3 m, float G, float ax, float ay, float az) {
+  m = normalize(m);
+  const float A = m.x * m.x / (ax * ax) + m.y * m.y / (ay * ay) + m.z * m.z / (az * az);
+  const float B = G * m.z / (az * az);
+  const float C = G * G / (az * az);
+  const float sA = sqrtf(A);
+  const float q = B / sA;
+  float m3, m4;
+  moments34(q, m3, m4);
+  // q >= 0: exp(-C + q^2) = exp(-G^2 S/(az^2 A)) with S = mx^2/ax^2 + my^2/ay^2
+  float E;
+  if (q >= 0.0f) {
+    const float S = m.x * m.x / (ax * ax) + m.y * m.y / (ay * ay);
+    E = expf(-C * S / A);
+  } else {
+    E = expf(-C);
+  }
+  return E * m3 * kInvPi32 / (ax * ay * az * A * A);
+}
+
+// Local-frame projected area (Eq. generalized_lambda times cos theta, mean (0,0,G)).
+__device__ __forceinline__ float projected_area_local(V3 w, float G, float ax, float ay, float az) {
+  const float ae = sqrtf(ax * ax * w.x * w.x + ay * ay * w.y * w.y + az * az * w.z * w.z);
+  return ae * psi(G * w.z / ae);
+}
+
+// ---------------------------------------------------------------- sampling mixture
+// Orthonormal basis around a unit vector (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(V3 n, V3& t1, V3& t2) {
+  const float s = copysignf(1.0f, n.z);
+  const float a = -1.0f / (s + n.z);
+  const float b = n.x * n.y * a;
+  t1 = {1.0f + s * n.x * n.x * a, s * b, -s * n.x};
+  t2 = {b, s + n.y * n.y * a, -n.y};
+}
+
+// Beckmann proposal frame and roughness: z = sign(-d.n) n, alpha_B = clamp(alpha/|g|, 1e-3, 16);
+// z = -d where |g| < 1e-6.
+__device__ __forceinline__ void beckmann_frame(V3 d, V3 g, float alpha, V3& z, float& aB) {
+  const float G = sqrtf(dot(g, g));
+  if (G < 1e-6f) {
+    z = -d;
+    aB = 16.0f;
+    return;
+  }
+  const V3 n = (1.0f / G) * g;
+  z = (-dot(d, n) >= 0.0f) ? n : -n;
+  aB = fminf(fmaxf(alpha / G, 1e-3f), 16.0f);
+}
+
+// Beckmann visible-normal density <wi,m> D_B(m) / ((1+Lambda(wi)) cos theta_i).
+__device__ __forceinline__ float beckmann_vis_pdf(V3 m, V3 wi, V3 z, float a) {
+  const float wm = dot(wi, m);
+  const float c = dot(m, z);
+  if (wm <= 0.0f || c <= 0.0f) return 0.0f;
+  const float c2 = c * c;
+  const float t2 = (1.0f - c2) / c2;
+  const float D = expf(-t2 / (a * a)) / (kPi * a * a * c2 * c2);
+  const float ci = fmaxf(dot(wi, z), 0.0f);
+  const float si = sqrtf(fmaxf(0.0f, 1.0f - ci * ci));
+  float denom;
+  if (si <= 0.0f) {
+    denom = ci;
+  } else {
+    const float ac = ci / (a * si);
+    denom = 0.5f * ci * (1.0f + erff(ac)) + a * si * expf(-ac * ac) * (0.5f * kInvSqrtPi);
+  }
+  return wm * D / denom;
+}
+
+// Visible-normal sampling of the Beckmann NDF after Heitz & d'Eon (2014): stretch
+// the incident direction to unit roughness, draw the x slope by inverting its CDF
+// C(x) = cot (1+erf x)/2 + exp(-x^2)/(2 sqrt pi) (Newton, bracketed), the y slope
+// from its Gaussian conditional, rotate, unstretch, slope -> normal.
+__device__ __forceinline__ V3 beckmann_sample_vis(V3 wi, V3 z, float a, float u1, float u2) {
+  V3 t1, t2;
+  onb(z, t1, t2);
+  V3 ws = normalize(v3(a * dot(wi, t1), a * dot(wi, t2), dot(wi, z)));
+  const float ct = ws.z;
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+  float cphi = 1.0f, sphi = 0.0f;
+  if (st > 1e-7f) {
+    cphi = ws.x / st;
+    sphi = ws.y / st;
+  }
+  float sx;
+  const float ux = fminf(fmaxf(2.0f * u1 - 1.0f, -0.99999994f), 0.99999994f);
+  if (st < 1e-4f) {
+    sx = erfinvf(ux);
+  } else {
+    const float cot = ct / st;
+    const float total = 0.5f * cot * (1.0f + erff(cot)) + expf(-cot * cot) * (0.5f * kInvSqrtPi);
+    const float target = u1 * total;
+    float lo = -6.0f, hi = cot;
+    float x = fminf(fmaxf(erfinvf(ux), lo), hi);
+    for (int it = 0; it < 24; ++it) {
+      const float e = expf(-x * x);
+      const float Cx = 0.5f * cot * (1.0f + erff(x)) + e * (0.5f * kInvSqrtPi);
+      const float f = Cx - target;
+      if (fabsf(f) <= 2e-7f * total) break;
+      if (f > 0.0f) hi = x; else lo = x;
+      const float df = (cot - x) * e * kInvSqrtPi;
+      float xn = df > 0.0f ? x - f / df : 0.5f * (lo + hi);
+      if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+      if (hi - lo < 1e-6f * (1.0f + fabsf(x))) { x = xn; break; }
+      x = xn;
+    }
+    sx = x;
+  }
+  const float uy = fminf(fmaxf(2.0f * u2 - 1.0f, -0.99999994f), 0.99999994f);
+  const float sy = erfinvf(uy);
+  const float px = (cphi * sx - sphi * sy) * a;
+  const float py = (sphi * sx + cphi * sy) * a;
+  const V3 ml = normalize(v3(-px, -py, 1.0f));
+  return normalize(ml.x * t1 + ml.y * t2 + ml.z * z);
+}
+
+__device__ __forceinline__ V3 uniform_hemisphere(V3 wi, float u1, float u2) {
+  V3 t1, t2;
+  onb(wi, t1, t2);
+  const float c = u1, s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+  float sp, cp;
+  sincospif(2.0f * u2, &sp, &cp);
+  return normalize((s * cp) * t1 + (s * sp) * t2 + c * wi);
+}
+
+// mixture pdf over half-vectors m facing -d
+__device__ __forceinline__ float mixture_pdf_m(V3 d, V3 m, V3 g, float alpha, float R) {
+  const V3 wi = -d;
+  if (dot(wi, m) <= 0.0f) return 0.0f;
+  V3 z;
+  float aB;
+  beckmann_frame(d, g, alpha, z, aB);
+  return R * beckmann_vis_pdf(m, wi, z, aB) + (1.0f - R) * (1.0f / kTwoPi);
+}
+
+// Phase function p(d,d2)/F = D(m) / (4 sigma(d)) and the mixture pdf over d2.
+// Returns false where p = 0.
+__device__ __forceinline__ bool phase_eval(V3 d, V3 d2, const Field& f, float alpha, float R,
+                                           float& p_over_F, float& pdf) {
+  V3 m = d2 - d;
+  const float len2 = dot(m, m);
+  p_over_F = 0.0f;
+  pdf = 0.0f;
+  if (!(len2 > 0.0f)) return false;
+  m = rsqrtf(len2) * m;
+  const float dm = dot(d, m);
+  if (dm >= 0.0f) return false;
+  const float sd = projected_area(d, f, alpha);
+  p_over_F = ndf_iso(m, f.g, alpha) / (4.0f * sd);
+  pdf = mixture_pdf_m(d, m, f.g, alpha, R) / (4.0f * fabsf(dm));
+  return true;
+}
+
+// Samples d2; returns the weight p/pdf divided by F, and the pdf.
+__device__ __forceinline__ bool phase_sample(V3 d, const Field& f, float alpha, float R, float u0, float u1,
+                                             float u2, V3& d2, float& w_over_F, float& pdf) {
+  const V3 wi = -d;
+  V3 m;
+  if (u0 < R) {
+    V3 z;
+    float aB;
+    beckmann_frame(d, f.g, alpha, z, aB);
+    m = beckmann_sample_vis(wi, z, aB, u1, u2);
+  } else {
+    m = uniform_hemisphere(wi, u1, u2);
+  }
+  const float dm = dot(d, m);
+  w_over_F = 0.0f;
+  pdf = 0.0f;
+  if (!(dm < 0.0f)) return false;
+  d2 = normalize(fma3(-2.0f * dm, m, d));
+  const float pdf_m = mixture_pdf_m(d, m, f.g, alpha, R);
+  if (!(pdf_m > 0.0f)) return false;
+  const float sd = projected_area(d, f, alpha);
+  w_over_F = ndf_iso(m, f.g, alpha) * fabsf(dm) / (sd * pdf_m);
+  pdf = pdf_m / (4.0f * fabsf(dm));
+  return isfinite(w_over_F);
+}
+
+// ---------------------------------------------------------------- lights and camera
+__device__ __forceinline__ V3 env_radiance(const LightDev& L, V3 w) {
+  if (L.kind == kLightSky) {
+    V3 c;
+    if (w.z >= 0.0f) {
+      const float t = w.z;
+      c = {(1.0f - t) + t * 0.35f, (1.0f - t) + t * 0.55f, 1.0f};
+    } else {
+      c = {0.25f, 0.22f, 0.20f};
+    }
+    return {c.x * L.radiance[0], c.y * L.radiance[1], c.z * L.radiance[2]};
+  }
+  return {L.radiance[0], L.radiance[1], L.radiance[2]};
+}
+
+__device__ __forceinline__ void camera_ray(const CameraDev& c, int px, int py, float jx, float jy, V3& o, V3& d) {
+  const float x = 2.0f * ((float)px + jx) / (float)c.width - 1.0f;
+  const float y = 1.0f - 2.0f * ((float)py + jy) / (float)c.height;
+  const V3 f = {c.fwd[0], c.fwd[1], c.fwd[2]}, r = {c.right[0], c.right[1], c.right[2]}, u = {c.up[0], c.up[1], c.up[2]};
+  const V3 e = {c.eye[0], c.eye[1], c.eye[2]};
+  if (c.ortho) {
+    o = e + (x * c.half_w) * r + (y * c.half_h) * u;
+    d = f;
+  } else {
+    o = e;
+    d = normalize(f + (x * c.half_w) * r + (y * c.half_h) * u);
+  }
+}
+
+__device__ __forceinline__ float power_heuristic(float a, float b) {
+  const float a2 = a * a, b2 = b * b;
+  return a2 / (a2 + b2);
+}
+
+// ---------------------------------------------------------------- majorant traversal
+// Amanatides & Woo (1987) traversal of the majorant grid, consuming an optical
+// depth budget tau: advances to the next tentative collision (returns true) or to
+// the end of the ray (returns false).
+struct Walk {
+  int ix, iy, iz;
+  int sx, sy, sz;        // +1/-1
+  float tmx, tmy, tmz;   // parameter of the next face crossing per axis
+  float tdx, tdy, tdz;   // parameter step per cell per axis
+  float t, t_end;
+  float sbar;            // majorant at the current tentative collision
+};
+
+__device__ __forceinline__ bool walk_begin(const MajorantDev& g, V3 o, V3 d, float tmax, Walk& w) {
+  const float gmax[3] = {g.gmin[0] + g.cell[0] * g.dims[0], g.gmin[1] + g.cell[1] * g.dims[1],
+                         g.gmin[2] + g.cell[2] * g.dims[2]};
+  const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  float t0 = 0.0f, t1 = tmax;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (dd[a] == 0.0f) {
+      if (oo[a] < g.gmin[a] || oo[a] > gmax[a]) return false;
+    } else {
+      const float inv = 1.0f / dd[a];
+      float ta = (g.gmin[a] - oo[a]) * inv, tb = (gmax[a] - oo[a]) * inv;
+      if (ta > tb) { const float tmp = ta; ta = tb; tb = tmp; }
+      t0 = fmaxf(t0, ta);
+      t1 = fminf(t1, tb);
+    }
+  }
+  if (!(t1 > t0)) return false;
+  w.t = t0;
+  w.t_end = t1;
+  int idx[3], st[3];
+  float tm[3], td[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = fmaf(t0, dd[a], oo[a]);
+    int i = (int)floorf((p - g.gmin[a]) * g.inv_cell[a]);
+    i = min(max(i, 0), g.dims[a] - 1);
+    idx[a] = i;
+    if (dd[a] > 0.0f) {
+      st[a] = 1;
+      tm[a] = (g.gmin[a] + (float)(i + 1) * g.cell[a] - oo[a]) / dd[a];
+      td[a] = g.cell[a] / dd[a];
+    } else if (dd[a] < 0.0f) {
+      st[a] = -1;
+      tm[a] = (g.gmin[a] + (float)i * g.cell[a] - oo[a]) / dd[a];
+      td[a] = -g.cell[a] / dd[a];
+    } else {
+      st[a] = 0;
+      tm[a] = INFINITY;
+      td[a] = INFINITY;
+    }
+  }
+  w.ix = idx[0]; w.iy = idx[1]; w.iz = idx[2];
+  w.sx = st[0]; w.sy = st[1]; w.sz = st[2];
+  w.tmx = tm[0]; w.tmy = tm[1]; w.tmz = tm[2];
+  w.tdx = td[0]; w.tdy = td[1]; w.tdz = td[2];
+  return true;
+}
+
+// Consumes the optical-depth budget tau against the majorant; *steps counts cells.
+__device__ __forceinline__ bool walk_advance(const MajorantDev& g, Walk& w, float tau, uint32_t& steps) {
+  for (;;) {
+    const float tn = fminf(fminf(w.tmx, w.tmy), fminf(w.tmz, w.t_end));
+    const float sbar = __ldg(g.maj + w.ix + g.dims[0] * (w.iy + g.dims[1] * w.iz));
+    const float dt = tn - w.t;
+    const float need = sbar * dt;
+    ++steps;
+    if (tau < need) {
+      w.t += tau / sbar;
+      w.sbar = sbar;
+      return true;
+    }
+    tau -= fmaxf(need, 0.0f);
+    w.t = tn;
+    if (tn >= w.t_end) return false;
+    if (w.tmx <= w.tmy && w.tmx <= w.tmz) {
+      w.ix += w.sx;
+      w.tmx += w.tdx;
+      if ((unsigned)w.ix >= (unsigned)g.dims[0]) return false;
+    } else if (w.tmy <= w.tmz) {
+      w.iy += w.sy;
+      w.tmy += w.tdy;
+      if ((unsigned)w.iy >= (unsigned)g.dims[1]) return false;
+    } else {
+      w.iz += w.sz;
+      w.tmz += w.tdz;
+      if ((unsigned)w.iz >= (unsigned)g.dims[2]) return false;
+    }
+  }
+}
+
+// Total extinction of the scene at x (objects add) and the field of the object
+// that an extinction-proportional choice with uniform u picks (index in *k).
+__device__ __forceinline__ float scene_sigma_t(const SceneDev& s, V3 x, V3 d) {
+  float tot = 0.0f;
+  for (int k = 0; k < s.n_objs; ++k) {
+    if (!inside(s.obj[k], x)) continue;
+    Field f;
+    Local l;
+    tot += sigma_t_object(s.obj[k], x, d, f, l);
+  }
+  return tot;
+}
+
+}  // namespace gpss

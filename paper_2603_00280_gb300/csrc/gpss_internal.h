@@ -1,0 +1,75 @@
+// gpss_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gpss.h"
+#include "gpss_device.cuh"
+
+namespace gpss {
+
+// Per-call work counters, accumulated on the device (u64 each).
+enum Counter : int {
+  kCntPaths = 0,
+  kCntVertices,
+  kCntNull,
+  kCntShadow,
+  kCntCells,
+  kCntTruncated,
+  kCntAborted,
+  kCntNum
+};
+
+struct ObjectHost {
+  int n[3];
+  float bmin[3], bmax[3];
+  int channels;
+  float length_scale;
+  float2* mv = nullptr;      // device (mean, variance)
+  float* albedo = nullptr;   // device planes
+  size_t nodes = 0;
+};
+
+}  // namespace gpss
+
+struct gpss_scene_s {
+  int device = 0;
+  int n_objs = 0;
+  gpss::ObjectHost obj[gpss::kMaxObjects];
+  gpss::LightDev light{};
+  gpss::MajorantDev mg{};
+  float* maj = nullptr;            // device majorant grid
+  int brick = 1;                   // majorant cell = brick x finest field cell
+  // scratch owned by the scene
+  unsigned long long* counters = nullptr;   // kCntNum u64 + work cursor
+  float* tmp_planes = nullptr;     // staging for uploads (2 x max nodes)
+  size_t tmp_capacity = 0;
+  int* flags = nullptr;            // validation / error flags (device)
+  float* film = nullptr;           // film used when the caller's image is host memory
+  size_t film_capacity = 0;
+  float* path_radiance = nullptr;  // per-path radiance kept for the adjoint (optional)
+  size_t path_capacity = 0;
+  uint64_t path_tag = 0;           // identifies the render that filled path_radiance
+};
+
+namespace gpss {
+
+void set_error(const char* fmt, ...);
+gpss_status cuda_fail(cudaError_t e, const char* what);
+
+gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cudaStream_t st);
+gpss_status build_majorant(gpss_scene s, cudaStream_t st);
+SceneDev scene_dev(const gpss_scene_s* s);
+bool camera_dev(const gpss_camera* c, CameraDev* out);
+
+// kernels (launch wrappers)
+cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
+                          float* sqsum, float* path_radiance, unsigned long long* counters, int grid, int block,
+                          cudaStream_t st);
+int render_block_size();
+int render_grid_size(int device, int block);
+
+}  // namespace gpss

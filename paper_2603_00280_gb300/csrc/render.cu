@@ -1,0 +1,315 @@
+// render.cu -- forward path tracing of the GPSS medium (persistent kernel).
+//
+// Integrator (Sec. 5 of the paper: null scattering on the classic exponential
+// medium of Sec. 4):
+//   - free flight by delta tracking against the majorant grid: tentative
+//     collisions at optical depth -ln(u) of the majorant, accepted as real with
+//     probability sigma_t / majorant;
+//   - at each real vertex, next-event estimation with a ratio-tracking shadow ray
+//     (T *= 1 - sigma_t/majorant at each tentative collision), MIS (power
+//     heuristic) against phase sampling for environment lights;
+//   - phase sampling with the mixture of Sec. 4.2.2; at most max_bounces real
+//     vertices, no continuation after the last, no Russian roulette.
+//
+// Execution model: one persistent thread per resident lane.  Each iteration of
+// the main loop advances every active lane by ONE tentative collision of its
+// current ray (the free-flight ray or the shadow ray), so all lanes of a warp run
+// the same field fetch + extinction code together; shading at real vertices is
+// the only divergent section.  A lane whose path has finished takes the next
+// (sample, pixel) index from a warp-private chunk of the global work cursor
+// (one atomic per chunk; ranks from __ballot_sync/__popc).  Path state lives in
+// registers.  Path index = sample * npix + pixel, so a chunk covers adjacent
+// pixels at the same sample.
+#include "gpss_internal.h"
+
+namespace gpss {
+
+constexpr int kRenderBlock = 128;
+constexpr int kChunk = 256;
+constexpr uint32_t kMaxEventsPerPath = 1u << 24;  // runaway guard (counted as aborted)
+
+struct RenderArgs {
+  int spp, max_bounces;
+  uint64_t seed;
+  float mix_R;
+  int npix;
+  long long total;
+  float inv_spp;
+};
+
+enum Mode : int { kFlight = 0, kShadow = 1 };
+
+__device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d, float& st_k0, Field& f0, Local& l0) {
+  // Single object: fast path.  Several objects: extinctions add.
+  if (S.n_objs == 1) {
+    if (!inside(S.obj[0], x)) { st_k0 = 0.0f; return 0.0f; }
+    st_k0 = sigma_t_object(S.obj[0], x, d, f0, l0);
+    return st_k0;
+  }
+  float tot = 0.0f;
+  st_k0 = 0.0f;
+  for (int k = 0; k < S.n_objs; ++k) {
+    if (!inside(S.obj[k], x)) continue;
+    Field f;
+    Local l;
+    tot += sigma_t_object(S.obj[k], x, d, f, l);
+  }
+  return tot;
+}
+
+// Picks the scattering object in proportion to its extinction (Q13) and returns its field.
+__device__ __forceinline__ int choose_object(const SceneDev& S, V3 x, V3 d, float total, float u, Field& f, Local& l) {
+  float acc = 0.0f;
+  int last = -1;
+  const float pick = u * total;
+  for (int k = 0; k < S.n_objs; ++k) {
+    if (!inside(S.obj[k], x)) continue;
+    Field fk;
+    Local lk;
+    const float s = sigma_t_object(S.obj[k], x, d, fk, lk);
+    if (s <= 0.0f) continue;
+    last = k;
+    f = fk;
+    l = lk;
+    acc += s;
+    if (pick < acc) return k;
+  }
+  return last;
+}
+
+__global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const CameraDev C, const RenderArgs P,
+                                                        float* __restrict__ image, float* __restrict__ sqsum,
+                                                        float* __restrict__ path_radiance,
+                                                        unsigned long long* __restrict__ counters) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  unsigned long long* cursor = counters + kCntNum;
+  const bool env = S.light.kind != kLightDirectional;
+
+  long long chunk_next = 0, chunk_end = 0;
+  bool exhausted = false;
+
+  bool active = false;
+  long long pidx = 0;
+  uint32_t pixel = 0;
+  Rng rng;
+  V3 o{}, d{}, beta{}, L{}, pend{}, d_next{}, beta_next{};
+  float prev_pdf = -1.0f, T = 1.0f, pdf_next = 0.0f;
+  int bounce = 0, mode = kFlight;
+  bool cont = false, walk_ok = false;
+  uint32_t events = 0;
+  Walk w;
+
+  uint32_t c_paths = 0, c_vert = 0, c_null = 0, c_shadow = 0, c_cells = 0, c_trunc = 0, c_abort = 0;
+
+  for (;;) {
+    // ------------------------------------------------ regeneration (warp-converged)
+    const unsigned need = __ballot_sync(FULL, !active);
+    if (need && !exhausted) {
+      const int n_need = __popc(need);
+      const int rank = __popc(need & ((1u << lane) - 1u));
+      long long avail = chunk_end - chunk_next;
+      long long mine = -1;
+      if (avail >= n_need) {
+        if (!active) mine = chunk_next + rank;
+        chunk_next += n_need;
+      } else {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)kChunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (!active) mine = rank < avail ? chunk_next + rank : (long long)base + (rank - avail);
+        chunk_next = (long long)base + (n_need - avail);
+        chunk_end = (long long)base + kChunk;
+        if ((long long)base >= P.total) exhausted = true;
+      }
+      if (!active && mine >= 0 && mine < P.total) {
+        // ---- new path
+        pidx = mine;
+        const int sample = (int)(mine / P.npix);
+        pixel = (uint32_t)(mine - (long long)sample * P.npix);
+        rng.init(P.seed, pixel, (uint32_t)sample);
+        rng.start(0, kPurposeCamera);
+        const float jx = rng.next(), jy = rng.next();
+        camera_ray(C, (int)(pixel % (uint32_t)C.width), (int)(pixel / (uint32_t)C.width), jx, jy, o, d);
+        beta = v3(1.0f, 1.0f, 1.0f);
+        L = v3(0.0f, 0.0f, 0.0f);
+        prev_pdf = -1.0f;
+        bounce = 0;
+        mode = kFlight;
+        events = 0;
+        rng.start(0, kPurposeFlight);
+        walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+        active = true;
+      }
+    }
+    if (__ballot_sync(FULL, active) == 0) {
+      if (exhausted || chunk_next >= P.total) break;
+      continue;
+    }
+    if (!active) continue;
+
+    // ------------------------------------------------ one tentative collision
+    bool hit = false;
+    if (walk_ok) hit = walk_advance(S.mg, w, -__logf(rng.next()), c_cells);
+    bool finish = false;
+    if (hit) {
+      ++events;
+      const V3 x = fma3(w.t, d, o);
+      Field f;
+      Local l;
+      float st0;
+      const float st = sigma_t_at(S, x, d, st0, f, l);
+      if (mode == kFlight) {
+        const float ua = rng.next();
+        if (ua * w.sbar < st) {
+          // ---------------------------------------- real scattering vertex
+          ++c_vert;
+          int k = 0;
+          if (S.n_objs > 1) k = choose_object(S, x, d, st, rng.next(), f, l);
+          const ObjectDev& ob = S.obj[k];
+          const V3 F = fetch_albedo(ob, x);
+          o = x;
+          cont = bounce + 1 < P.max_bounces;
+          if (cont) {
+            rng.start((uint32_t)bounce, kPurposePhase);
+            const float u0 = rng.next(), u1 = rng.next(), u2 = rng.next();
+            float wF, pdf;
+            V3 d2;
+            if (phase_sample(d, f, l.alpha, P.mix_R, u0, u1, u2, d2, wF, pdf)) {
+              d_next = d2;
+              beta_next = v3(beta.x * F.x * wF, beta.y * F.y * wF, beta.z * F.z * wF);
+              pdf_next = pdf;
+            } else {
+              cont = false;
+            }
+          } else {
+            ++c_trunc;
+          }
+          rng.start((uint32_t)bounce, kPurposeNee);
+          V3 wl;
+          float scale;
+          if (!env) {
+            wl = v3(S.light.dir[0], S.light.dir[1], S.light.dir[2]);
+            float pF, pdf_ph;
+            phase_eval(d, wl, f, l.alpha, P.mix_R, pF, pdf_ph);
+            scale = pF;
+            pend = v3(beta.x * F.x * scale * S.light.radiance[0], beta.y * F.y * scale * S.light.radiance[1],
+                      beta.z * F.z * scale * S.light.radiance[2]);
+          } else {
+            const float z = 1.0f - 2.0f * rng.next();
+            const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+            float sp, cp;
+            sincospif(2.0f * rng.next(), &sp, &cp);
+            wl = v3(r * cp, r * sp, z);
+            float pF, pdf_ph;
+            phase_eval(d, wl, f, l.alpha, P.mix_R, pF, pdf_ph);
+            const V3 Le = env_radiance(S.light, wl);
+            scale = pF * power_heuristic(kInv4Pi, pdf_ph) * (4.0f * kPi);
+            pend = v3(beta.x * F.x * scale * Le.x, beta.y * F.y * scale * Le.y, beta.z * F.z * scale * Le.z);
+          }
+          ++bounce;
+          if (scale > 0.0f) {
+            mode = kShadow;
+            d = wl;
+            T = 1.0f;
+            walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+          } else if (cont) {
+            d = d_next;
+            beta = beta_next;
+            prev_pdf = pdf_next;
+            rng.start((uint32_t)bounce, kPurposeFlight);
+            walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+          } else {
+            finish = true;
+          }
+        } else {
+          ++c_null;
+        }
+      } else {
+        ++c_shadow;
+        T *= fmaxf(0.0f, 1.0f - st / w.sbar);
+      }
+      if (events >= kMaxEventsPerPath) {
+        ++c_abort;
+        finish = true;
+      }
+    } else {
+      if (mode == kFlight) {
+        if (env) {
+          const V3 Le = env_radiance(S.light, d);
+          const float wm = prev_pdf < 0.0f ? 1.0f : power_heuristic(prev_pdf, kInv4Pi);
+          L = v3(fmaf(beta.x * Le.x, wm, L.x), fmaf(beta.y * Le.y, wm, L.y), fmaf(beta.z * Le.z, wm, L.z));
+        }
+        finish = true;
+      } else {
+        L = v3(fmaf(pend.x, T, L.x), fmaf(pend.y, T, L.y), fmaf(pend.z, T, L.z));
+        if (cont) {
+          mode = kFlight;
+          d = d_next;
+          beta = beta_next;
+          prev_pdf = pdf_next;
+          rng.start((uint32_t)bounce, kPurposeFlight);
+          walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+        } else {
+          finish = true;
+        }
+      }
+    }
+    if (finish) {
+      float* px = image + 3 * (size_t)pixel;
+      atomicAdd(px + 0, L.x * P.inv_spp);
+      atomicAdd(px + 1, L.y * P.inv_spp);
+      atomicAdd(px + 2, L.z * P.inv_spp);
+      if (sqsum) {
+        float* q = sqsum + 3 * (size_t)pixel;
+        atomicAdd(q + 0, L.x * L.x);
+        atomicAdd(q + 1, L.y * L.y);
+        atomicAdd(q + 2, L.z * L.z);
+      }
+      if (path_radiance) {
+        float* pr = path_radiance + 3 * pidx;
+        pr[0] = L.x;
+        pr[1] = L.y;
+        pr[2] = L.z;
+      }
+      ++c_paths;
+      active = false;
+    }
+  }
+
+  // ------------------------------------------------ counters: warp reduce, one atomic per warp
+  uint32_t vals[7] = {c_paths, c_vert, c_null, c_shadow, c_cells, c_trunc, c_abort};
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    unsigned long long v = vals[i];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+    if (lane == 0 && v) atomicAdd(counters + i, v);
+  }
+}
+
+int render_block_size() { return kRenderBlock; }
+
+int render_grid_size(int device, int block) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render, block, 0);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
+                          float* sqsum, float* path_radiance, unsigned long long* counters, int grid, int block,
+                          cudaStream_t st) {
+  RenderArgs P;
+  P.spp = o.spp;
+  P.max_bounces = o.max_bounces;
+  P.seed = o.seed;
+  P.mix_R = o.mix_R;
+  P.npix = C.width * C.height;
+  P.total = (long long)P.npix * o.spp;
+  P.inv_spp = 1.0f / (float)o.spp;
+  k_render<<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters);
+  return cudaGetLastError();
+}
+
+}  // namespace gpss

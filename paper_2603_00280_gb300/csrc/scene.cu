@@ -1,0 +1,158 @@
+// scene.cu -- scene upload (grids -> library layout) and the majorant grid.
+//
+// Layout in HBM per object: (mean, variance) interleaved as float2 per node so
+// one 8-byte gather serves both fields of a corner; albedo as separate planes
+// (read only at real collisions).  The majorant grid is a separate float grid
+// over the union of the object boxes whose cells are `brick` x the finest field
+// cell; for one object it is aligned with the field cells.
+#include <cstdio>
+#include <cstring>
+
+#include "gpss_internal.h"
+
+namespace gpss {
+
+__global__ void k_interleave(const float* __restrict__ mean, const float* __restrict__ var, float2* __restrict__ mv,
+                             size_t n, int* flags) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float m = mean[i], v = var[i];
+    if (!isfinite(m)) atomicOr(flags, 1);
+    if (!(v > 0.0f) || !isfinite(v)) atomicOr(flags, 2);
+    mv[i] = make_float2(m, v);
+  }
+}
+
+__global__ void k_check_albedo(const float* __restrict__ a, size_t n, int* flags) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = a[i];
+    if (!(v >= 0.0f && v <= 1.0f)) atomicOr(flags, 4);
+  }
+}
+
+// Upper bound of sigma_t over a majorant cell, over all directions (row A3):
+//   mu >= mu_lo, var in [v_lo, v_hi], |grad mu| <= G_hi (each gradient component of
+//   the trilinear interpolant is a convex combination of edge differences / h);
+//   lambda is decreasing, so rho <= lambda(mu_lo/sigma_hi)/sigma_lo for mu_lo >= 0 and
+//   lambda(mu_lo/sigma_lo)/sigma_lo otherwise;  sigma(d) = E[max(0,-d.g)] <= G_hi +
+//   alpha_hi/(2 sqrt(pi)).  Objects' bounds add.  A 1e-3 relative margin covers FP32
+//   rounding of the per-sample evaluation.
+__global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
+  const long long ncell = (long long)g.dims[0] * g.dims[1] * g.dims[2];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % g.dims[0]);
+    const int cj = (int)((c / g.dims[0]) % g.dims[1]);
+    const int ck = (int)(c / ((long long)g.dims[0] * g.dims[1]));
+    const int cidx[3] = {ci, cj, ck};
+    float total = 0.0f;
+    for (int k = 0; k < S.n_objs; ++k) {
+      const ObjectDev& o = S.obj[k];
+      int lo[3], hi[3];
+      bool overlap = true;
+      for (int a = 0; a < 3; ++a) {
+        const float wlo = g.gmin[a] + cidx[a] * g.cell[a];
+        const float whi = wlo + g.cell[a];
+        if (whi < o.bmin[a] || wlo > o.bmax[a]) { overlap = false; break; }
+        const float flo = (wlo - o.bmin[a]) * o.inv_h[a];
+        const float fhi = (whi - o.bmin[a]) * o.inv_h[a];
+        int i0 = (int)floorf(flo + 1e-3f);
+        int i1 = (int)ceilf(fhi - 1e-3f) - 1;
+        i0 = min(max(i0, 0), o.n[a] - 2);
+        i1 = min(max(i1, i0), o.n[a] - 2);
+        lo[a] = i0;
+        hi[a] = i1 + 1;  // node range
+      }
+      if (!overlap) continue;
+      float mu_lo = INFINITY, v_lo = INFINITY, v_hi = 0.0f, ex = 0.0f, ey = 0.0f, ez = 0.0f;
+      const int sy = o.n[0], sz = o.n[0] * o.n[1];
+      for (int kk = lo[2]; kk <= hi[2]; ++kk)
+        for (int jj = lo[1]; jj <= hi[1]; ++jj)
+          for (int ii = lo[0]; ii <= hi[0]; ++ii) {
+            const int idx = ii + sy * jj + sz * kk;
+            const float2 v = o.mv[idx];
+            mu_lo = fminf(mu_lo, v.x);
+            v_lo = fminf(v_lo, v.y);
+            v_hi = fmaxf(v_hi, v.y);
+            if (ii < hi[0]) ex = fmaxf(ex, fabsf(o.mv[idx + 1].x - v.x));
+            if (jj < hi[1]) ey = fmaxf(ey, fabsf(o.mv[idx + sy].x - v.x));
+            if (kk < hi[2]) ez = fmaxf(ez, fabsf(o.mv[idx + sz].x - v.x));
+          }
+      const float gx = ex * o.inv_h[0], gy = ey * o.inv_h[1], gz = ez * o.inv_h[2];
+      const float G_hi = sqrtf(gx * gx + gy * gy + gz * gz);
+      const float s_lo = sqrtf(v_lo), s_hi = sqrtf(v_hi);
+      const float u = mu_lo >= 0.0f ? mu_lo / s_hi : mu_lo / s_lo;
+      const float rho_ub = inv_mills(u) / s_lo;
+      const float area_ub = G_hi + s_hi * o.alpha_scale * (0.5f * kInvSqrtPi);
+      total += rho_ub * area_ub;
+    }
+    maj[c] = total * 1.001f;
+  }
+}
+
+static int blocks_for(size_t n, int block) {
+  size_t b = (n + block - 1) / block;
+  return (int)(b < 65536 ? (b ? b : 1) : 65536);
+}
+
+gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(s->flags, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset flags");
+  for (int k = 0; k < n; ++k) {
+    ObjectHost& o = s->obj[k];
+    const size_t nodes = o.nodes;
+    e = cudaMemcpyAsync(s->tmp_planes, objs[k].mean, nodes * sizeof(float), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy mean");
+    e = cudaMemcpyAsync(s->tmp_planes + nodes, objs[k].variance, nodes * sizeof(float), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy variance");
+    k_interleave<<<blocks_for(nodes, 256), 256, 0, st>>>(s->tmp_planes, s->tmp_planes + nodes, o.mv, nodes, s->flags);
+    e = cudaMemcpyAsync(o.albedo, objs[k].albedo, nodes * o.channels * sizeof(float), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy albedo");
+    k_check_albedo<<<blocks_for(nodes * o.channels, 256), 256, 0, st>>>(o.albedo, nodes * o.channels, s->flags);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "upload kernels");
+  int flags = 0;
+  e = cudaMemcpyAsync(&flags, s->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "read flags");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload");
+  if (flags & 1) { set_error("mean contains non-finite values"); return GPSS_ERR_INVALID_ARG; }
+  if (flags & 2) { set_error("variance must be finite and > 0"); return GPSS_ERR_INVALID_ARG; }
+  if (flags & 4) { set_error("albedo must lie in [0,1]"); return GPSS_ERR_INVALID_ARG; }
+  return GPSS_OK;
+}
+
+SceneDev scene_dev(const gpss_scene_s* s) {
+  SceneDev d;
+  memset(&d, 0, sizeof(d));
+  d.n_objs = s->n_objs;
+  for (int k = 0; k < s->n_objs; ++k) {
+    const ObjectHost& h = s->obj[k];
+    ObjectDev& o = d.obj[k];
+    for (int a = 0; a < 3; ++a) {
+      o.bmin[a] = h.bmin[a];
+      o.bmax[a] = h.bmax[a];
+      o.n[a] = h.n[a];
+      o.inv_h[a] = (float)(h.n[a] - 1) / (h.bmax[a] - h.bmin[a]);
+    }
+    o.channels = h.channels;
+    o.alpha_scale = kSqrt2 / h.length_scale;
+    o.mv = h.mv;
+    o.albedo = h.albedo;
+  }
+  d.mg = s->mg;
+  d.mg.maj = s->maj;
+  d.light = s->light;
+  return d;
+}
+
+gpss_status build_majorant(gpss_scene s, cudaStream_t st) {
+  const SceneDev S = scene_dev(s);
+  const long long ncell = (long long)s->mg.dims[0] * s->mg.dims[1] * s->mg.dims[2];
+  k_majorant<<<blocks_for((size_t)ncell, 128), 128, 0, st>>>(S, s->mg, s->maj);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "majorant kernel");
+  return GPSS_OK;
+}
+
+}  // namespace gpss

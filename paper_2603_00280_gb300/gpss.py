@@ -1,0 +1,376 @@
+"""Python binding of the GPSS C-ABI (``include/gpss.h``).
+
+Argument marshalling only: every step of the renderer runs in the CUDA library
+``libgpss.so``.  PyTorch supplies device memory and streams.  There is no CPU
+fallback -- if the library cannot be built or loaded, every call raises.
+
+Scene, camera, light and option dictionaries follow ``workloads.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GpssError(RuntimeError):
+    def __init__(self, fn: str, status: int, message: str):
+        super().__init__("%s failed (status %d): %s" % (fn, status, message))
+        self.status = status
+
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "UNSUPPORTED"}
+FLAG_KEEP_PATH_RADIANCE = 1
+
+
+class ObjectDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bbox_min", ctypes.c_float * 3), ("bbox_max", ctypes.c_float * 3),
+                ("mean", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
+                ("albedo_channels", ctypes.c_int), ("length_scale", ctypes.c_float)]
+
+
+class LightDesc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("dir", ctypes.c_float * 3), ("radiance", ctypes.c_float * 3)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("eye", ctypes.c_float * 3), ("look_at", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("fov_y_deg", ctypes.c_float), ("ortho_w", ctypes.c_float),
+                ("ortho_h", ctypes.c_float), ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("spp", ctypes.c_int), ("max_bounces", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("mix_R", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("paths", ctypes.c_uint64), ("vertices", ctypes.c_uint64), ("null_collisions", ctypes.c_uint64),
+                ("shadow_steps", ctypes.c_uint64), ("majorant_cells", ctypes.c_uint64),
+                ("truncated", ctypes.c_uint64), ("aborted", ctypes.c_uint64), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+
+# name -> argtypes (restype is always int status, except noted)
+_SIGS = {
+    "gpss_scene_create": [ctypes.POINTER(ObjectDesc), _I, ctypes.POINTER(LightDesc), _I, _VP, ctypes.POINTER(_VP)],
+    "gpss_scene_update": [_VP, ctypes.POINTER(ObjectDesc), _I, _VP],
+    "gpss_scene_destroy": [_VP],
+    "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
+    "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
+    "gpss_render_adjoint": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, _VP, _VP, _VP,
+                            ctypes.POINTER(Stats), _VP],
+    "gpss_batch_create": [ctypes.POINTER(_VP), ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _I, _I, _VP,
+                          ctypes.POINTER(_VP)],
+    "gpss_batch_render": [_VP, ctypes.POINTER(_VP), _VP],
+    "gpss_batch_destroy": [_VP],
+    "gpss_eval_sigma_t": [_VP, _I, _VP, _VP, _VP, _VP],
+    "gpss_eval_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP],
+    "gpss_sample_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP],
+    "gpss_eval_ndf": [_I, _VP, _F, _F, _F, _F, _VP, _VP],
+    "gpss_eval_projected_area": [_I, _VP, _F, _F, _F, _F, _VP, _VP],
+    "gpss_eval_transmittance": [_VP, _I, _VP, _VP, _VP, _VP, _VP],
+    "gpss_estimate_transmittance": [_VP, _I, _VP, _VP, _VP, _I, ctypes.c_uint64, _VP, _VP],
+    "gpss_sample_free_flight": [_VP, _I, _VP, _VP, _I, ctypes.c_uint64, _VP, _VP],
+    "gpss_philox4x32_10": [_I, _VP, _VP, _VP, _VP],
+}
+
+
+def load():
+    """Builds (if stale) and loads libgpss.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(_build.build())
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.gpss_last_error.restype = ctypes.c_char_p
+            L.gpss_last_error.argtypes = []
+            L.gpss_version.restype = ctypes.c_int
+            L.gpss_version.argtypes = []
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _call(name, *args):
+    L = load()
+    st = getattr(L, name)(*args)
+    if st != 0:
+        raise GpssError(name, st, L.gpss_last_error().decode())
+    return st
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the GPSS library needs a CUDA device")
+    return torch
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    assert x.is_contiguous()
+    return ctypes.c_void_p(x.data_ptr())
+
+
+_LIGHT = {"directional": 0, "sky": 1, "uniform": 2}
+_CAM = {"ortho": 0, "perspective": 1}
+
+
+def light_desc(light: dict) -> LightDesc:
+    L = LightDesc()
+    L.type = _LIGHT[light["type"]]
+    for a in range(3):
+        L.dir[a] = float(light.get("dir", (0, 0, 1))[a])
+        L.radiance[a] = float(light.get("radiance", (1, 1, 1))[a])
+    return L
+
+
+def camera_desc(cam: dict) -> Camera:
+    c = Camera()
+    c.type = _CAM[cam["type"]]
+    for a in range(3):
+        c.eye[a] = float(cam["eye"][a])
+        c.look_at[a] = float(cam["look_at"][a])
+        c.up[a] = float(cam["up"][a])
+    c.fov_y_deg = float(cam.get("fov_y_deg", 40.0))
+    c.ortho_w = float(cam.get("ortho_w", 1.0))
+    c.ortho_h = float(cam.get("ortho_h", 1.0))
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    return c
+
+
+def render_opts(opts: dict, flags: int = 0) -> RenderOpts:
+    o = RenderOpts()
+    o.spp = int(opts["spp"])
+    o.max_bounces = int(opts["max_bounces"])
+    o.seed = int(opts.get("seed", 0))
+    o.mix_R = float(opts.get("mix_R", 0.5))
+    o.flags = int(opts.get("flags", 0)) | flags
+    return o
+
+
+def _object_descs(objects, keep):
+    descs = (ObjectDesc * len(objects))()
+    for k, o in enumerate(objects):
+        mean, var, alb = o["mean"], o["variance"] if "variance" in o else o["var"], o["albedo"]
+        arrs = []
+        for a in (mean, var, alb):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float32)
+            else:
+                a = a.contiguous().float()
+            arrs.append(a)
+        keep.extend(arrs)
+        mean, var, alb = arrs
+        nz, ny, nx = mean.shape
+        D = descs[k]
+        D.nx, D.ny, D.nz = nx, ny, nz
+        for a in range(3):
+            D.bbox_min[a] = float(o["bbox_min"][a])
+            D.bbox_max[a] = float(o["bbox_max"][a])
+        D.mean = _ptr(mean).value
+        D.variance = _ptr(var).value
+        D.albedo = _ptr(alb).value
+        D.albedo_channels = 1 if alb.ndim == 3 else int(alb.shape[0])
+        D.length_scale = float(o["length_scale"])
+    return descs
+
+
+class Scene:
+    """A scene owned by the library (grids copied into its layout)."""
+
+    def __init__(self, scene: dict, majorant_brick: int = 0, stream=None):
+        load()
+        self.handle = ctypes.c_void_p()
+        keep = []
+        descs = _object_descs(scene["objects"], keep)
+        self.n_objs = len(scene["objects"])
+        self.shapes = [tuple(o["mean"].shape) for o in scene["objects"]]
+        self.channels = [1 if o["albedo"].ndim == 3 else int(o["albedo"].shape[0]) for o in scene["objects"]]
+        L = light_desc(scene.get("light", {"type": "directional", "dir": (0, 0, 1), "radiance": (1, 1, 1)}))
+        _call("gpss_scene_create", descs, self.n_objs, ctypes.byref(L), int(majorant_brick), _stream(stream),
+              ctypes.byref(self.handle))
+
+    def update(self, objects, stream=None):
+        keep = []
+        descs = _object_descs(objects, keep)
+        _call("gpss_scene_update", self.handle, descs, len(objects), _stream(stream))
+        del keep
+
+    def majorant(self, stream=None):
+        torch = _torch()
+        dims = (ctypes.c_int * 3)()
+        _call("gpss_scene_majorant", self.handle, dims, None, _stream(stream))
+        out = torch.empty((dims[2], dims[1], dims[0]), device="cuda", dtype=torch.float32)
+        _call("gpss_scene_majorant", self.handle, dims, _ptr(out), _stream(stream))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().gpss_scene_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def render(scene: Scene, camera: dict, opts: dict, image=None, sqsum=None, want_sqsum=False, stats=True,
+           keep_path_radiance=False, stream=None):
+    """Forward render.  Returns (image, sqsum or None, stats dict or None).
+    image/sqsum may be preallocated torch CUDA tensors or numpy host arrays (H, W, 3)."""
+    torch = _torch()
+    H, W = int(camera["height"]), int(camera["width"])
+    if image is None:
+        image = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+    if sqsum is None and want_sqsum:
+        sqsum = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+    st = Stats() if stats else None
+    c = camera_desc(camera)
+    o = render_opts(opts, FLAG_KEEP_PATH_RADIANCE if keep_path_radiance else 0)
+    _call("gpss_render", scene.handle, ctypes.byref(c), ctypes.byref(o), _ptr(image), _ptr(sqsum),
+          ctypes.byref(st) if st is not None else None, _stream(stream))
+    return image, sqsum, (st.as_dict() if st is not None else None)
+
+
+def render_adjoint(scene: Scene, camera: dict, opts: dict, d_image, d_mean=None, d_variance=None, d_albedo=None,
+                   d_length_scale=None, stats=True, stream=None):
+    st = Stats() if stats else None
+    c = camera_desc(camera)
+    o = render_opts(opts)
+    _call("gpss_render_adjoint", scene.handle, ctypes.byref(c), ctypes.byref(o), _ptr(d_image), _ptr(d_mean),
+          _ptr(d_variance), _ptr(d_albedo), _ptr(d_length_scale), ctypes.byref(st) if st is not None else None,
+          _stream(stream))
+    return st.as_dict() if st is not None else None
+
+
+def _dev(x):
+    torch = _torch()
+    return torch.as_tensor(np.asarray(x, dtype=np.float32) if not hasattr(x, "device") else x,
+                           dtype=torch.float32).cuda().contiguous()
+
+
+def eval_sigma_t(scene: Scene, pos, dirs, stream=None):
+    torch = _torch()
+    pos, dirs = _dev(pos).reshape(-1, 3), _dev(dirs).reshape(-1, 3)
+    out = torch.empty(len(pos), device="cuda", dtype=torch.float32)
+    _call("gpss_eval_sigma_t", scene.handle, len(pos), _ptr(pos), _ptr(dirs), _ptr(out), _stream(stream))
+    return out
+
+
+def eval_phase(scene: Scene, k: int, pos, d_in, d_out, mix_R=0.5, stream=None):
+    torch = _torch()
+    pos, d_in, d_out = (_dev(a).reshape(-1, 3) for a in (pos, d_in, d_out))
+    p = torch.empty((len(pos), 3), device="cuda", dtype=torch.float32)
+    pdf = torch.empty(len(pos), device="cuda", dtype=torch.float32)
+    _call("gpss_eval_phase", scene.handle, int(k), len(pos), _ptr(pos), _ptr(d_in), _ptr(d_out), float(mix_R),
+          _ptr(p), _ptr(pdf), _stream(stream))
+    return p, pdf
+
+
+def sample_phase(scene: Scene, k: int, pos, d_in, u, mix_R=0.5, stream=None):
+    torch = _torch()
+    pos, d_in, u = (_dev(a).reshape(-1, 3) for a in (pos, d_in, u))
+    d_out = torch.empty((len(pos), 3), device="cuda", dtype=torch.float32)
+    w = torch.empty((len(pos), 3), device="cuda", dtype=torch.float32)
+    pdf = torch.empty(len(pos), device="cuda", dtype=torch.float32)
+    _call("gpss_sample_phase", scene.handle, int(k), len(pos), _ptr(pos), _ptr(d_in), _ptr(u), float(mix_R),
+          _ptr(d_out), _ptr(w), _ptr(pdf), _stream(stream))
+    return d_out, w, pdf
+
+
+def eval_ndf(m, G, ax, ay, az, stream=None):
+    torch = _torch()
+    m = _dev(m).reshape(-1, 3)
+    out = torch.empty(len(m), device="cuda", dtype=torch.float32)
+    _call("gpss_eval_ndf", len(m), _ptr(m), float(G), float(ax), float(ay), float(az), _ptr(out), _stream(stream))
+    return out
+
+
+def eval_projected_area(w, G, ax, ay, az, stream=None):
+    torch = _torch()
+    w = _dev(w).reshape(-1, 3)
+    out = torch.empty(len(w), device="cuda", dtype=torch.float32)
+    _call("gpss_eval_projected_area", len(w), _ptr(w), float(G), float(ax), float(ay), float(az), _ptr(out),
+          _stream(stream))
+    return out
+
+
+def eval_transmittance(scene: Scene, org, dirs, tmax, stream=None):
+    torch = _torch()
+    org, dirs = _dev(org).reshape(-1, 3), _dev(dirs).reshape(-1, 3)
+    tmax = _dev(tmax).reshape(-1)
+    out = torch.empty(len(org), device="cuda", dtype=torch.float32)
+    _call("gpss_eval_transmittance", scene.handle, len(org), _ptr(org), _ptr(dirs), _ptr(tmax), _ptr(out),
+          _stream(stream))
+    return out
+
+
+def estimate_transmittance(scene: Scene, org, dirs, tmax, samples, seed=0, stream=None):
+    torch = _torch()
+    org, dirs = _dev(org).reshape(-1, 3), _dev(dirs).reshape(-1, 3)
+    tmax = _dev(tmax).reshape(-1)
+    out = torch.empty(len(org), device="cuda", dtype=torch.float32)
+    _call("gpss_estimate_transmittance", scene.handle, len(org), _ptr(org), _ptr(dirs), _ptr(tmax), int(samples),
+          int(seed), _ptr(out), _stream(stream))
+    return out
+
+
+def sample_free_flight(scene: Scene, org, dirs, samples, seed=0, stream=None):
+    torch = _torch()
+    org, dirs = _dev(org).reshape(-1, 3), _dev(dirs).reshape(-1, 3)
+    out = torch.empty((len(org), int(samples)), device="cuda", dtype=torch.float32)
+    _call("gpss_sample_free_flight", scene.handle, len(org), _ptr(org), _ptr(dirs), int(samples), int(seed),
+          _ptr(out), _stream(stream))
+    return out
+
+
+def philox4x32_10(ctr, key, stream=None):
+    torch = _torch()
+    c = torch.as_tensor(np.asarray(ctr, dtype=np.uint32).view(np.int32)).cuda().contiguous()
+    k = torch.as_tensor(np.asarray(key, dtype=np.uint32).view(np.int32)).cuda().contiguous()
+    n = c.numel() // 4
+    out = torch.empty(4 * n, device="cuda", dtype=torch.int32)
+    _call("gpss_philox4x32_10", n, _ptr(c), _ptr(k), _ptr(out), _stream(stream))
+    return out.cpu().numpy().view(np.uint32).reshape(n, 4)

@@ -1,0 +1,231 @@
+"""GPU parity of the deterministic quantities (through the C-ABI) against the
+FP64 oracle: extinction, NDF, projected area, phase function and its pdf,
+transmittance; plus Philox known answers and the stochastic trackers."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_00280_gb300 import gpss
+from paper_2603_00280_gb300 import workloads as W
+from tests import gpu_common as C
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hetero():
+    sc = C.dyadic_hetero(5)
+    return sc, gpss.Scene(sc), oracle.Scene(sc)
+
+
+@pytest.fixture(scope="module")
+def hetero_rgb():
+    sc = C.dyadic_hetero(4, length_scale=0.05, channels=3, seed=3)
+    return sc, gpss.Scene(sc), oracle.Scene(sc)
+
+
+def test_philox_known_answers(gpss):
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    v = np.array([[int(x, 16) for x in r] for r in rows], dtype=np.uint64)
+    out = gpss.philox4x32_10(v[:, 0:4].astype(np.uint32), v[:, 4:6].astype(np.uint32))
+    np.testing.assert_array_equal(out.astype(np.uint64), v[:, 6:10])
+
+
+def test_sigma_t_parity(hetero):
+    sc, G, O = hetero
+    x = C.dyadic_points(4000, 1)
+    d = C.unit_dirs(4000, 2)
+    g = gpss.eval_sigma_t(G, x, d).cpu().numpy()
+    o = oracle.sigma_t(O, x.astype(np.float64), d.astype(np.float64))
+    scale = o.max()
+    err = C.rel_err(g, o, floor=1e-6 * scale)
+    assert np.quantile(err, 1.0) < C.REL, (err.max(), np.argmax(err))
+    assert (o > 1e-3 * scale).sum() > 200  # the sample reaches the shell
+
+
+def test_sigma_t_edge_cases(hetero):
+    sc, G, O = hetero
+    # outside the box, on the faces, at the corners
+    x = np.array([[0.6, 0, 0], [-0.5, 0, 0], [0.5, 0.5, 0.5], [-0.5, -0.5, -0.5], [0, 0, 2.0]], np.float32)
+    d = np.tile(np.array([[0, 0, 1]], np.float32), (len(x), 1))
+    g = gpss.eval_sigma_t(G, x, d).cpu().numpy()
+    o = oracle.sigma_t(O, x.astype(np.float64), d.astype(np.float64))
+    assert g[0] == 0 and g[4] == 0
+    np.testing.assert_allclose(g, o, rtol=C.REL, atol=1e-30)
+
+
+@pytest.mark.parametrize("G,ax,ay,az", [(1.0, 0.5, 0.5, 0.5), (1.0, 0.3, 0.7, 1.2), (0.6, 1.0, 1.0, 1.0),
+                                        (1.0, 0.2, 0.2, 0.01), (1.3, 3.0, 2.0, 0.8), (0.0, 0.7, 0.7, 0.7)])
+def test_ndf_and_projected_area_parity(G, ax, ay, az):
+    rng = np.random.default_rng(5)
+    m = rng.normal(size=(2000, 3))
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    m = m.astype(np.float32)
+    g = gpss.eval_ndf(m, G, ax, ay, az).cpu().numpy()
+    o = np.array([oracle.ndf_local(v.astype(np.float64), G, ax, ay, az) for v in m])
+    scale = o.max()
+    err = C.rel_err(g, o, floor=1e-6 * scale)
+    assert err.max() < C.REL, (err.max(), m[np.argmax(err)])
+    ga = gpss.eval_projected_area(m, G, ax, ay, az).cpu().numpy()
+    oa = np.array([oracle.projected_area_local(v.astype(np.float64), G, ax, ay, az) for v in m])
+    err = C.rel_err(ga, oa, floor=1e-6 * oa.max())
+    assert err.max() < C.REL, (err.max(), m[np.argmax(err)])
+
+
+def _beckmann_conditioning(O, x, d, d2):
+    """Relative sensitivity of the Beckmann part of the mixture pdf to FP32
+    rounding of m = (d2-d)/|d2-d| and of the interpolated gradient: with
+    c = m.z, D_B = exp(-(1-c^2)/(a^2 c^2))/(pi a^2 c^4) has
+    |d ln D_B / d c| = |2 (1-c^2)/(a^2 c^3) - 4/c|; FP32 carries an absolute error
+    of ~2^-23 in c."""
+    out = np.zeros(len(x))
+    for i in range(len(x)):
+        f = oracle.field(O, 0, x[i].astype(np.float64))
+        g = f["grad"]
+        G = np.linalg.norm(g)
+        alpha = math.sqrt(2 * f["var"]) / O._objs[0].length_scale
+        if G < 1e-6:
+            continue
+        a = min(max(alpha / G, 1e-3), 16.0)
+        m = d2[i].astype(np.float64) - d[i]
+        m /= np.linalg.norm(m)
+        c = abs(m @ g) / G
+        if c <= 1e-9:
+            continue
+        out[i] = abs(2 * (1 - c * c) / (a * a * c ** 3) - 4 / c) * 2.0 ** -23
+    return out
+
+
+@pytest.mark.parametrize("which", ["hetero", "hetero_rgb"])
+def test_phase_eval_parity(which, request):
+    """p within 1e-5 everywhere; the pdf within 1e-5 plus the FP32 conditioning
+    of the Beckmann density at half-vectors nearly perpendicular to grad mu."""
+    sc, G, O = request.getfixturevalue(which)
+    n = 1500
+    x = C.dyadic_points(n, 11, -0.4, 0.4)
+    d = C.unit_dirs(n, 12)
+    d2 = C.unit_dirs(n, 13)
+    cond = _beckmann_conditioning(O, x, d, d2)
+    for R in (0.5, 0.2):
+        gp, gpdf = gpss.eval_phase(G, 0, x, d, d2, R)
+        op, opdf = oracle.phase_eval(O, 0, x.astype(np.float64), d.astype(np.float64), d2.astype(np.float64), R)
+        gp, gpdf = gp.cpu().numpy(), gpdf.cpu().numpy()
+        e1 = C.rel_err(gp, op, floor=1e-6 * op.max())
+        e2 = C.rel_err(gpdf, opdf, floor=1e-6 * opdf.max())
+        assert e1.max() < C.REL, (e1.max(), np.unravel_index(np.argmax(e1), e1.shape))
+        tol = C.REL + 4 * cond
+        assert np.all(e2 < tol), (e2.max(), np.argmax(e2 / tol), cond[np.argmax(e2 / tol)])
+        assert np.mean(e2 < C.REL) > 0.99
+
+
+def test_phase_sampler_weights_and_histogram(hetero):
+    """GPU samples: the returned weight and pdf equal the oracle's p/pdf at the
+    GPU's own sampled direction, and the sample histogram follows the pdf."""
+    sc, G, O = hetero
+    x0 = C.dyadic_points(1, 21, -0.3, 0.3)[0]
+    d0 = C.unit_dirs(1, 22)[0]
+    n = 200000
+    u = np.random.default_rng(23).random((n, 3)).astype(np.float32)
+    xs = np.tile(x0, (n, 1))
+    ds = np.tile(d0, (n, 1))
+    d2, w, pdf = gpss.sample_phase(G, 0, xs, ds, u)
+    d2, w, pdf = d2.cpu().numpy(), w.cpu().numpy(), pdf.cpu().numpy()
+    assert np.all(pdf > 0)
+    # away from grazing half-vectors, where re-deriving m from the FP32-rounded d2 cancels
+    mh = d2 - d0
+    mh /= np.linalg.norm(mh, axis=1, keepdims=True)
+    keep = np.nonzero(np.abs(mh @ d0) > 0.05)[0][:300]
+    op, opdf = oracle.phase_eval(O, 0, xs[keep].astype(np.float64), ds[keep].astype(np.float64),
+                                 d2[keep].astype(np.float64))
+    np.testing.assert_allclose(pdf[keep], opdf, rtol=2e-4)
+    np.testing.assert_allclose(w[keep, 0], op[:, 0] / opdf, rtol=2e-4)
+    # E[w] = F (energy conservation of Eq. phase through the sampler)
+    F = oracle.field(O, 0, x0.astype(np.float64))["albedo"][0]
+    assert abs(w[:, 0].mean() - F) < 5 * w[:, 0].std() / math.sqrt(n)
+    # histogram of half vectors vs the oracle pdf on (cos, phi) bins about -d
+    m = d2 - d0
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    fx, fy, fz = H.frame(-d0.astype(np.float64))
+    c = m @ fz
+    ph = np.mod(np.arctan2(m @ fy, m @ fx), 2 * math.pi)
+    nb = 8
+    obs, _, _ = np.histogram2d(c, ph, bins=[np.linspace(0, 1, nb + 1), np.linspace(0, 2 * math.pi, nb + 1)])
+    gx, gw = np.polynomial.legendre.leggauss(6)
+    exp_p = np.zeros((nb, nb))
+    for i in range(nb):
+        cc = (i + 0.5 + 0.5 * gx) / nb
+        for j in range(nb):
+            pp = (j + 0.5 + 0.5 * gx) * 2 * math.pi / nb
+            CC, PP = np.meshgrid(cc, pp, indexing="ij")
+            WW = np.outer(0.5 * gw / nb, 0.5 * gw * 2 * math.pi / nb).reshape(-1)
+            s = np.sqrt(1 - CC ** 2)
+            mm = ((s * np.cos(PP))[..., None] * fx + (s * np.sin(PP))[..., None] * fy + CC[..., None] * fz).reshape(-1, 3)
+            dd2 = d0 - 2 * (mm @ d0)[:, None] * mm
+            _, pb = oracle.phase_eval(O, 0, np.tile(x0, (len(mm), 1)).astype(np.float64),
+                                      np.tile(d0, (len(mm), 1)).astype(np.float64), dd2)
+            exp_p[i, j] = np.sum(WW * pb * 4 * np.abs(mm @ d0))
+    from scipy.stats import chisquare
+    stat, pval = chisquare(obs.ravel(), exp_p.ravel() / exp_p.sum() * obs.sum())
+    assert obs.sum() > 0.999 * n
+    assert pval > 1e-4, (stat, pval)
+
+
+def test_transmittance_quadrature_parity(hetero):
+    sc, G, O = hetero
+    n = 64
+    o = C.dyadic_points(n, 31, -0.45, 0.45)
+    d = C.unit_dirs(n, 32)
+    tmax = np.full(n, 0.6, np.float32)
+    g = gpss.eval_transmittance(G, o, d, tmax).cpu().numpy()
+    ref = np.array([oracle.transmittance(O, o[i].astype(np.float64), d[i].astype(np.float64), 0.6) for i in range(n)])
+    err = C.rel_err(g, ref, floor=1e-6)
+    assert err.max() < C.REL, (err.max(), np.argmax(err), g[np.argmax(err)], ref[np.argmax(err)])
+    assert (ref < 0.9).sum() > 5 and (ref > 0.1).sum() > 5
+
+
+def test_slab_transmittance_closed_form():
+    S = gpss.Scene(H.dyadic_slab())
+    d45 = np.array([[math.cos(math.pi / 4), 0, -math.sin(math.pi / 4)]], np.float32)
+    o = np.array([[-0.25, 0.0, 0.125]], np.float32)
+    ts = np.array([0.05, 0.1, 0.2, 0.3], np.float32)
+    g = gpss.eval_transmittance(S, np.repeat(o, 4, 0), np.repeat(d45, 4, 0), ts).cpu().numpy()
+    for t, v in zip(ts, g):
+        z1 = 0.125 + float(t) * float(d45[0, 2])
+        ref = math.exp(-H.slab_optical_depth(0.125, z1, d45[0].astype(np.float64)))
+        assert v == pytest.approx(ref, rel=C.REL)
+
+
+def test_ratio_tracking_is_unbiased(hetero):
+    """The renderer's ratio tracker: mean over many estimates vs the oracle's
+    deterministic transmittance (z-test per ray)."""
+    sc, G, O = hetero
+    n = 48
+    o = C.dyadic_points(n, 41, -0.45, 0.45)
+    d = C.unit_dirs(n, 42)
+    tmax = np.full(n, np.inf, np.float32)
+    ref = np.array([oracle.transmittance(O, o[i].astype(np.float64), d[i].astype(np.float64)) for i in range(n)])
+    m1 = gpss.estimate_transmittance(G, o, d, tmax, 20000, seed=1).cpu().numpy().astype(np.float64)
+    m2 = gpss.estimate_transmittance(G, o, d, tmax, 20000, seed=2).cpu().numpy().astype(np.float64)
+    # variance of the mean from two independent halves is unknown per ray; bound it by Tr(1-Tr)/N
+    se = np.sqrt(np.maximum(ref * (1 - ref), 1e-6) / 20000)
+    z = ((m1 + m2) / 2 - ref) / (se / math.sqrt(2))
+    assert np.mean(np.abs(z) > 4) < 0.05, z
+    assert abs(np.mean((m1 + m2) / 2 - ref)) < 4 * np.sqrt(np.sum(se ** 2) / 2) / n
+
+
+def test_delta_tracking_distance_distribution(hetero):
+    """P(t_hit <= s) = 1 - Tr(s) for the renderer's free-flight sampler."""
+    sc, G, O = hetero
+    o = np.array([[-0.45, 0.0, 0.0]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0]], np.float32)
+    n = 200000
+    t = gpss.sample_free_flight(G, o, d, n, seed=5).cpu().numpy()[0]
+    for s in (0.1, 0.15, 0.2, 0.3, 0.5, 0.8):
+        p = float(np.mean(t <= s))
+        ref = 1 - oracle.transmittance(O, o[0].astype(np.float64), d[0].astype(np.float64), s)
+        assert abs(p - ref) < 5 * math.sqrt(max(ref * (1 - ref), 1e-8) / n) + 1e-4, (s, p, ref)

@@ -1,0 +1,155 @@
+"""GPU image parity of the forward renderer against the FP64 oracle and
+against closed forms, through the C-ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_00280_gb300 import gpss
+from paper_2603_00280_gb300 import workloads as W
+from tests import gpu_common as C
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+D45 = np.array([math.cos(math.pi / 4), 0.0, -math.sin(math.pi / 4)])
+
+
+def _gpu_render(scene_dict, cam, opts, brick=0):
+    S = gpss.Scene(scene_dict, majorant_brick=brick)
+    img, sq, st = gpss.render(S, cam, opts, want_sqsum=True)
+    return img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64), st
+
+
+def test_single_scattering_matches_closed_form():
+    """max_bounces = 1 on the plane-mean slab: every interior pixel has the exact
+    value of a 1-D integral of closed forms (integrator + extinction + phase)."""
+    ref = H.slab_single_scatter(D45, np.array([0.0, 0.0, 1.0]), 0.75)
+    cam = W.ortho_camera_45(16, 16, film=0.5)
+    spp = 16384
+    for brick in (1, 4):
+        img, sq, st = _gpu_render(H.dyadic_slab(albedo=0.75), cam, {"spp": spp, "max_bounces": 1, "seed": 7}, brick)
+        v = img[4:12, 4:12, 0]
+        se = np.sqrt(np.maximum(sq[4:12, 4:12, 0] / spp - v ** 2, 0) / spp)
+        z = (v - ref) / se
+        assert np.mean(np.abs(z) > 3) <= 0.05, z
+        assert abs((v.mean() - ref) / (np.sqrt(np.sum(se ** 2)) / v.size)) < 4
+        assert st["aborted"] == 0 and st["paths"] == 16 * 16 * spp
+
+
+def test_white_furnace():
+    sc = H.dyadic_slab(albedo=1.0, mean=0.0625, light=W.uniform_light(1.0))
+    cam = W.ortho_camera_45(16, 16, film=0.5)
+    spp = 8192
+    img, sq, st = _gpu_render(sc, cam, {"spp": spp, "max_bounces": 512, "seed": 3})
+    assert st["truncated"] == 0
+    v = img[6:10, 6:10, 0]
+    m = v.mean()
+    var = sq[6:10, 6:10, 0].sum() / (16 * spp) - m * m
+    se = math.sqrt(var / (16 * spp))
+    assert abs(m - 1.0) < 4 * se, (m, se)
+
+
+def _parity(sc, cam, opts, orc_spp, gpu_spp, rows=None, cols=None, brick=0):
+    img, sq, st = _gpu_render(sc, cam, dict(opts, spp=gpu_spp, seed=101), brick)
+    O = oracle.Scene(sc)
+    s, s2, ost = oracle.render(O, cam, dict(opts, spp=orc_spp, seed=202), rows=rows, cols=cols)
+    H_, W_ = cam["height"], cam["width"]
+    r = rows or (0, H_, 1)
+    c = cols or (0, W_)
+    sel = (slice(r[0], r[1], r[2] if len(r) > 2 else 1), slice(c[0], c[1]))
+    z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], gpu_spp, s[sel], s2[sel], orc_spp)
+    ok, info = C.check_image_parity(gm, gse, om, ose)
+    assert ok, info
+    assert st["aborted"] == 0
+    return st, ost
+
+
+def test_tiny_slab_image_parity():
+    """The tiny workload (64x64 orthographic view of the slab, 8 bounces) vs the oracle."""
+    wl = W.tiny_slab()
+    _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=64, gpu_spp=1024, rows=(0, 64, 4))
+
+
+@pytest.mark.parametrize("brick", [1, 4])
+def test_heterogeneous_image_parity(brick):
+    wl = W.heterogeneous(n=32, width=24, height=24, spp=32, max_bounces=16)
+    _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=64, gpu_spp=2048, brick=brick)
+
+
+def two_spheres_rgb():
+    """Two overlapping GPSS spheres on their own dyadic grids, RGB albedo: the
+    extinctions add and the scattering object is chosen by extinction."""
+    objs = []
+    rng = np.random.default_rng(4)
+    for c, r, v, lo, hi in [((-0.1, 0, 0), 0.25, 4e-3, (-0.5, -0.375, -0.375), (0.25, 0.375, 0.375)),
+                            ((0.15, 0.05, 0), 0.2, 1e-2, (-0.125, -0.25, -0.25), (0.5, 0.375, 0.375))]:
+        n = (int(round((hi[0] - lo[0]) * 32)) + 1, int(round((hi[1] - lo[1]) * 32)) + 1, int(round((hi[2] - lo[2]) * 32)) + 1)
+        p = W.node_coords(lo, hi, n)
+        alb = rng.uniform(0.3, 0.95, size=(3, n[2], n[1], n[0])).astype(np.float32)
+        objs.append(W.make_object(W.sdf_sphere(p, c, r), v, alb, lo, hi, 0.05))
+    return {"objects": objs, "light": W.sky_light()}
+
+
+def test_rgb_albedo_and_multiple_objects_parity():
+    sc = two_spheres_rgb()
+    cam = W.perspective_camera(20, 20, eye=(0.0, -1.6, 0.6))
+    _parity(sc, cam, {"spp": 16, "max_bounces": 8, "mix_R": 0.5}, orc_spp=48, gpu_spp=2048)
+
+
+def test_sky_only_pixels_are_exact():
+    """Rays that miss every object return the sky radiance exactly."""
+    sc = C.dyadic_hetero(4)
+    cam = {"type": "ortho", "eye": (3.0, 3.0, 2.0), "look_at": (4.0, 4.0, 3.0), "up": (0, 0, 1),
+           "ortho_w": 0.5, "ortho_h": 0.5, "width": 8, "height": 8}
+    img, sq, st = _gpu_render(sc, cam, {"spp": 4, "max_bounces": 4, "seed": 1})
+    d = np.array([1.0, 1.0, 1.0]) / math.sqrt(3)
+    t = d[2]
+    sky = np.array([(1 - t) + t * 0.35, (1 - t) + t * 0.55, 1.0])
+    np.testing.assert_allclose(img.reshape(-1, 3), np.tile(sky, (64, 1)), rtol=2e-6)
+    assert st["vertices"] == 0
+
+
+def test_ragged_sizes_edge_cases_and_stats():
+    sc = C.dyadic_hetero(4)
+    for (w, h, spp, mb) in [(37, 23, 3, 5), (1, 1, 1, 1), (33, 1, 7, 2), (5, 129, 1, 32)]:
+        cam = W.perspective_camera(w, h)
+        img, sq, st = _gpu_render(sc, cam, {"spp": spp, "max_bounces": mb, "seed": 9})
+        assert img.shape == (h, w, 3)
+        assert np.all(np.isfinite(img)) and np.all(img >= 0)
+        assert st["paths"] == w * h * spp
+        assert st["aborted"] == 0
+
+
+def test_same_seed_same_image_and_host_output():
+    wl = W.heterogeneous(n=32, width=40, height=30, spp=8, max_bounces=8)
+    S = gpss.Scene(wl["scene"])
+    a, _, _ = gpss.render(S, wl["camera"], wl["opts"])
+    b, _, _ = gpss.render(S, wl["camera"], wl["opts"])
+    host = np.zeros((30, 40, 3), np.float32)
+    gpss.render(S, wl["camera"], wl["opts"], image=host)
+    a = a.cpu().numpy()
+    np.testing.assert_allclose(a, b.cpu().numpy(), rtol=1e-5, atol=1e-7)   # only the order of float atomics differs
+    np.testing.assert_allclose(a, host, rtol=1e-5, atol=1e-7)
+    c, _, _ = gpss.render(S, wl["camera"], dict(wl["opts"], seed=99))
+    assert not np.allclose(a, c.cpu().numpy())
+
+
+def test_full_size_workload_sampled_pixels():
+    """The benchmarked configuration (128^3 grid, 512x512, 64 spp, 32 bounces) in
+    the launch configuration the benchmark uses; a sample of pixels is checked
+    against the oracle one by one."""
+    wl = W.heterogeneous()
+    S = gpss.Scene(wl["scene"])
+    img, sq, st = gpss.render(S, wl["camera"], wl["opts"], want_sqsum=True)
+    img, sq = img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64)
+    assert st["paths"] == 512 * 512 * 64 and st["aborted"] == 0
+    assert np.all(np.isfinite(img))
+    O = oracle.Scene(wl["scene"])
+    orc_spp = 32
+    rows, cols = (236, 276, 5), (246, 250)      # 8 x 4 pixels over the sphere's shell
+    s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=orc_spp, seed=5), rows=rows, cols=cols)
+    sel = (slice(*rows), slice(*cols))
+    z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], 64, s[sel], s2[sel], orc_spp)
+    ok, info = C.check_image_parity(gm, gse, om, ose, frac4=0.1, block=2)
+    assert ok, info
