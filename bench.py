@@ -49,16 +49,24 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--image", type=int, default=0, help="override the image side (profiling of small cases)")
+    ap.add_argument("--spp", type=int, default=0, help="override samples per pixel (profiling of small cases)")
     return ap.parse_args()
 
 
-def workload(name, seed_offset=0):
+def workload(name, seed_offset=0, image=0, spp=0):
     from paper_2603_00280_gb300 import workloads as W
     if name == "tiny_slab":
         wl = W.tiny_slab()
     else:
         wl = W.heterogeneous()
     wl["opts"] = dict(wl["opts"], seed=wl["opts"]["seed"] + seed_offset)
+    if image:
+        wl["camera"] = dict(wl["camera"], width=image, height=image)
+        wl["name"] += "_img%d" % image
+    if spp:
+        wl["opts"]["spp"] = spp
+        wl["name"] += "_spp%d" % spp
     return wl
 
 
@@ -192,7 +200,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = workload(args.workload)
+    wl = workload(args.workload, image=args.image, spp=args.spp)
     vals = []
     desc = ""
     for i in range(args.warmup + args.steps):
@@ -223,7 +231,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     gpss.load()
-    wl = workload(args.workload, seed_offset=1000 * rank)
+    wl = workload(args.workload, seed_offset=1000 * rank, image=args.image, spp=args.spp)
     cam, opts = wl["camera"], wl["opts"]
     S = gpss.Scene(wl["scene"])
     H, W = cam["height"], cam["width"]
@@ -314,6 +322,7 @@ def run_ours(args):
            "clocks": clk,
            "work": {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
                     "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
+                    "majorant_cells_per_step": stats["majorant_cells"],
                     "kernel_ms": statistics.mean(kernel_ms)}}
     if world == 1 and not args.no_cpu_baseline:
         v, desc, cores, _ = oracle_sample(wl, args.cpu_seconds)

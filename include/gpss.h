@@ -119,6 +119,13 @@ gpss_status gpss_scene_create(const gpss_object_desc* objs, int n_objs, const gp
                               int majorant_brick, gpss_stream stream, gpss_scene* out);
 /* Re-copies the grids (same sizes as at creation) and rebuilds the majorant. */
 gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* objs, int n_objs, gpss_stream stream);
+/* Empty-space skipping of the majorant traversal: each majorant cell stores the
+ * largest radius r in {0, 1, 2, ..., 2^(skip_levels-1)} whose cube of (2r+1)^3
+ * cells has a max majorant M_r with M_r * r * h_min <= kappa; a ray crosses such
+ * a cube in one step at M_r.  skip_levels in [0, 6] (0 disables skipping),
+ * kappa >= 0.  Defaults: 5 and 0.5.  Every choice is unbiased; they trade
+ * traversal steps against null collisions (the autotuner's knobs). */
+gpss_status gpss_scene_set_traversal(gpss_scene s, int skip_levels, float kappa, gpss_stream stream);
 /* Frees the scene.  Call after the stream's work on it has completed. */
 gpss_status gpss_scene_destroy(gpss_scene s);
 /* Majorant grid geometry: dims[3] cells and their values (device copy, may be NULL). */

@@ -130,6 +130,8 @@ static void free_scene(gpss_scene s) {
     cudaFree(s->obj[k].albedo);
   }
   cudaFree(s->maj);
+  cudaFree(s->skip);
+  cudaFree(s->skip_tmp);
   cudaFree(s->counters);
   cudaFree(s->tmp_planes);
   cudaFree(s->flags);
@@ -166,6 +168,9 @@ static gpss_status setup_majorant(gpss_scene s) {
   cudaError_t e = cudaMalloc(&s->maj, ncell * sizeof(float));
   if (e != cudaSuccess) return cuda_fail(e, "majorant allocation");
   s->mg.maj = s->maj;
+  if ((e = cudaMalloc(&s->skip, ncell * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "skip grid allocation");
+  if ((e = cudaMalloc(&s->skip_tmp, 3 * ncell * sizeof(float))) != cudaSuccess) return cuda_fail(e, "skip scratch allocation");
+  s->mg.skip = s->skip;
   return GPSS_OK;
 }
 
@@ -261,6 +266,15 @@ extern "C" gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* o
   if ((st = scene_upload(s, objs, n_objs, cs)) != GPSS_OK) return st;
   s->path_tag = 0;
   return build_majorant(s, cs);
+}
+
+extern "C" gpss_status gpss_scene_set_traversal(gpss_scene s, int skip_levels, float kappa, gpss_stream stream) {
+  if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
+  if (skip_levels < 0 || skip_levels > 6) { set_error("skip_levels must be in [0, 6]"); return GPSS_ERR_INVALID_ARG; }
+  if (!(kappa >= 0.0f) || !std::isfinite(kappa)) { set_error("kappa must be finite and >= 0"); return GPSS_ERR_INVALID_ARG; }
+  s->skip_levels = skip_levels;
+  s->kappa = kappa;
+  return build_skip(s, (cudaStream_t)stream);
 }
 
 extern "C" gpss_status gpss_scene_destroy(gpss_scene s) {

@@ -190,10 +190,10 @@ __global__ void k_estimate_tr(const SceneDev S, int n, const float* org, const f
     Walk w;
     float T = 1.0f;
     if (walk_begin(S.mg, o, d, tmax[i], w)) {
-      while (walk_advance(S.mg, w, -__logf(rng.next()), cells)) {
+      while (walk_advance(S.mg, o, d, w, -__logf(rng.next()), cells)) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
-        T *= fmaxf(0.0f, 1.0f - st / w.sbar);
+        if (!ratio_step(T, st, w.sbar, rng)) break;
       }
     }
     acc += T;
@@ -215,7 +215,7 @@ __global__ void k_free_flight(const SceneDev S, int n, const float* org, const f
     Walk w;
     float t_hit = INFINITY;
     if (walk_begin(S.mg, o, d, INFINITY, w)) {
-      while (walk_advance(S.mg, w, -__logf(rng.next()), cells)) {
+      while (walk_advance(S.mg, o, d, w, -__logf(rng.next()), cells)) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
         if (rng.next() * w.sbar < st) {

@@ -48,13 +48,20 @@ struct ObjectDev {
   const float* albedo;     // channels planes
 };
 
-// Majorant grid: piecewise-constant upper bound of sigma_t over all directions.
+// Majorant grid: piecewise-constant upper bound of sigma_t over all directions,
+// per cell of `brick` field cells.  For traversal each cell also stores a skip
+// entry (M_r, r): the largest radius r in {0, 1, 2, 4, 8, 16} such that the max
+// M_r of the majorant over the cube of cells [c-r, c+r]^3 satisfies
+// M_r * r * h_min <= kappa (r = 0: the cell's own majorant).  A ray inside cell c
+// stays inside that cube for at least r cells, so one load covers up to r cells
+// of empty or thin space with a valid (larger) majorant.
 struct MajorantDev {
   float gmin[3];
-  float cell[3];
+  float cell[3];           // cell size
   float inv_cell[3];
-  int dims[3];
-  const float* maj;
+  int dims[3];             // cells per axis
+  const float* maj;        // per-cell majorant
+  const float2* skip;      // per-cell (M_r, r)
 };
 
 enum LightKind : int { kLightDirectional = 0, kLightSky = 1, kLightUniform = 2 };
@@ -549,30 +556,35 @@ __device__ __forceinline__ float power_heuristic(float a, float b) {
 }
 
 // ---------------------------------------------------------------- majorant traversal
-// Amanatides & Woo (1987) traversal of the majorant grid, consuming an optical
-// depth budget tau: advances to the next tentative collision (returns true) or to
-// the end of the ray (returns false).
+// Majorant traversal consuming an optical-depth budget tau: advances to the next
+// tentative collision (returns true, w.t and w.sbar set) or to the end of the ray
+// (returns false).  Each step looks up the skip entry of the cell ahead of the
+// current point and covers the segment to the exit of that entry's cube at its
+// majorant -- a single cell (r = 0, Amanatides-Woo-style face stepping) or a cube
+// of (2r+1)^3 cells in thin space.  Every segment is sampled against a valid
+// upper bound of sigma_t, so delta and ratio tracking stay unbiased.
 struct Walk {
-  int ix, iy, iz;
-  int sx, sy, sz;        // +1/-1
-  float tmx, tmy, tmz;   // parameter of the next face crossing per axis
-  float tdx, tdy, tdz;   // parameter step per cell per axis
   float t, t_end;
   float sbar;            // majorant at the current tentative collision
+  float idx, idy, idz;   // 1/d per axis (0 where d = 0)
+  int cx, cy, cz;        // current cell (exact integer stepping, no position nudging)
 };
 
+__device__ __forceinline__ int cell_index(float p, float gmin, float inv_cell, int dims) {
+  return min(max((int)floorf((p - gmin) * inv_cell), 0), dims - 1);
+}
+
 __device__ __forceinline__ bool walk_begin(const MajorantDev& g, V3 o, V3 d, float tmax, Walk& w) {
-  const float gmax[3] = {g.gmin[0] + g.cell[0] * g.dims[0], g.gmin[1] + g.cell[1] * g.dims[1],
-                         g.gmin[2] + g.cell[2] * g.dims[2]};
   const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
   float t0 = 0.0f, t1 = tmax;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    const float gmax = g.gmin[a] + g.cell[a] * g.dims[a];
     if (dd[a] == 0.0f) {
-      if (oo[a] < g.gmin[a] || oo[a] > gmax[a]) return false;
+      if (oo[a] < g.gmin[a] || oo[a] > gmax) return false;
     } else {
       const float inv = 1.0f / dd[a];
-      float ta = (g.gmin[a] - oo[a]) * inv, tb = (gmax[a] - oo[a]) * inv;
+      float ta = (g.gmin[a] - oo[a]) * inv, tb = (gmax - oo[a]) * inv;
       if (ta > tb) { const float tmp = ta; ta = tb; tb = tmp; }
       t0 = fmaxf(t0, ta);
       t1 = fminf(t1, tb);
@@ -581,65 +593,92 @@ __device__ __forceinline__ bool walk_begin(const MajorantDev& g, V3 o, V3 d, flo
   if (!(t1 > t0)) return false;
   w.t = t0;
   w.t_end = t1;
-  int idx[3], st[3];
-  float tm[3], td[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float p = fmaf(t0, dd[a], oo[a]);
-    int i = (int)floorf((p - g.gmin[a]) * g.inv_cell[a]);
-    i = min(max(i, 0), g.dims[a] - 1);
-    idx[a] = i;
-    if (dd[a] > 0.0f) {
-      st[a] = 1;
-      tm[a] = (g.gmin[a] + (float)(i + 1) * g.cell[a] - oo[a]) / dd[a];
-      td[a] = g.cell[a] / dd[a];
-    } else if (dd[a] < 0.0f) {
-      st[a] = -1;
-      tm[a] = (g.gmin[a] + (float)i * g.cell[a] - oo[a]) / dd[a];
-      td[a] = -g.cell[a] / dd[a];
-    } else {
-      st[a] = 0;
-      tm[a] = INFINITY;
-      td[a] = INFINITY;
-    }
-  }
-  w.ix = idx[0]; w.iy = idx[1]; w.iz = idx[2];
-  w.sx = st[0]; w.sy = st[1]; w.sz = st[2];
-  w.tmx = tm[0]; w.tmy = tm[1]; w.tmz = tm[2];
-  w.tdx = td[0]; w.tdy = td[1]; w.tdz = td[2];
+  w.idx = d.x != 0.0f ? 1.0f / d.x : 0.0f;
+  w.idy = d.y != 0.0f ? 1.0f / d.y : 0.0f;
+  w.idz = d.z != 0.0f ? 1.0f / d.z : 0.0f;
+  w.cx = cell_index(fmaf(t0, d.x, o.x), g.gmin[0], g.inv_cell[0], g.dims[0]);
+  w.cy = cell_index(fmaf(t0, d.y, o.y), g.gmin[1], g.inv_cell[1], g.dims[1]);
+  w.cz = cell_index(fmaf(t0, d.z, o.z), g.gmin[2], g.inv_cell[2], g.dims[2]);
   return true;
 }
 
-// Consumes the optical-depth budget tau against the majorant; *steps counts cells.
-__device__ __forceinline__ bool walk_advance(const MajorantDev& g, Walk& w, float tau, uint32_t& steps) {
-  for (;;) {
-    const float tn = fminf(fminf(w.tmx, w.tmy), fminf(w.tmz, w.t_end));
-    const float sbar = __ldg(g.maj + w.ix + g.dims[0] * (w.iy + g.dims[1] * w.iz));
-    const float dt = tn - w.t;
-    const float need = sbar * dt;
+// parameter at which the ray leaves the slab [lo, hi] of one axis (INFINITY if parallel)
+__device__ __forceinline__ float slab_exit(float lo, float hi, float o, float inv, float dcomp) {
+  if (dcomp == 0.0f) return INFINITY;
+  return ((dcomp > 0.0f ? hi : lo) - o) * inv;
+}
+
+__device__ __forceinline__ bool walk_advance(const MajorantDev& g, V3 o, V3 d, Walk& w, float tau, uint32_t& steps) {
+  // Each step moves the cell index strictly past the face the ray left by; the
+  // cap only guards against non-finite input (the ray then counts as leaving).
+  for (int guard = 0; guard < (1 << 22); ++guard) {
+    const float2 sk = __ldg(g.skip + w.cx + g.dims[0] * (w.cy + g.dims[1] * w.cz));
+    const int r = (int)sk.y;
+    const int lx = max(w.cx - r, 0), hx = min(w.cx + r, g.dims[0] - 1);
+    const int ly = max(w.cy - r, 0), hy = min(w.cy + r, g.dims[1] - 1);
+    const int lz = max(w.cz - r, 0), hz = min(w.cz + r, g.dims[2] - 1);
+    const float ex = slab_exit(g.gmin[0] + (float)lx * g.cell[0], g.gmin[0] + (float)(hx + 1) * g.cell[0], o.x, w.idx, d.x);
+    const float ey = slab_exit(g.gmin[1] + (float)ly * g.cell[1], g.gmin[1] + (float)(hy + 1) * g.cell[1], o.y, w.idy, d.y);
+    const float ez = slab_exit(g.gmin[2] + (float)lz * g.cell[2], g.gmin[2] + (float)(hz + 1) * g.cell[2], o.z, w.idz, d.z);
+    const float seg_end = fminf(fminf(ex, ey), fminf(ez, w.t_end));
+    const float need = sk.x * (seg_end - w.t);
     ++steps;
     if (tau < need) {
-      w.t += tau / sbar;
-      w.sbar = sbar;
+      w.t += tau / sk.x;
+      w.sbar = sk.x;
       return true;
     }
     tau -= fmaxf(need, 0.0f);
-    w.t = tn;
-    if (tn >= w.t_end) return false;
-    if (w.tmx <= w.tmy && w.tmx <= w.tmz) {
-      w.ix += w.sx;
-      w.tmx += w.tdx;
-      if ((unsigned)w.ix >= (unsigned)g.dims[0]) return false;
-    } else if (w.tmy <= w.tmz) {
-      w.iy += w.sy;
-      w.tmy += w.tdy;
-      if ((unsigned)w.iy >= (unsigned)g.dims[1]) return false;
+    w.t = fmaxf(w.t, seg_end);
+    if (seg_end >= w.t_end) return false;
+    // step to the cell beyond the exit face; after a cube jump the other axes are
+    // re-derived from the exit point (rounding there only yields empty segments)
+    if (ex <= ey && ex <= ez) {
+      w.cx = d.x > 0.0f ? hx + 1 : lx - 1;
+      if ((unsigned)w.cx >= (unsigned)g.dims[0]) return false;
+      if (r > 0) {
+        w.cy = cell_index(fmaf(w.t, d.y, o.y), g.gmin[1], g.inv_cell[1], g.dims[1]);
+        w.cz = cell_index(fmaf(w.t, d.z, o.z), g.gmin[2], g.inv_cell[2], g.dims[2]);
+      }
+    } else if (ey <= ez) {
+      w.cy = d.y > 0.0f ? hy + 1 : ly - 1;
+      if ((unsigned)w.cy >= (unsigned)g.dims[1]) return false;
+      if (r > 0) {
+        w.cx = cell_index(fmaf(w.t, d.x, o.x), g.gmin[0], g.inv_cell[0], g.dims[0]);
+        w.cz = cell_index(fmaf(w.t, d.z, o.z), g.gmin[2], g.inv_cell[2], g.dims[2]);
+      }
     } else {
-      w.iz += w.sz;
-      w.tmz += w.tdz;
-      if ((unsigned)w.iz >= (unsigned)g.dims[2]) return false;
+      w.cz = d.z > 0.0f ? hz + 1 : lz - 1;
+      if ((unsigned)w.cz >= (unsigned)g.dims[2]) return false;
+      if (r > 0) {
+        w.cx = cell_index(fmaf(w.t, d.x, o.x), g.gmin[0], g.inv_cell[0], g.dims[0]);
+        w.cy = cell_index(fmaf(w.t, d.y, o.y), g.gmin[1], g.inv_cell[1], g.dims[1]);
+      }
     }
   }
+  return false;
+}
+
+// One ratio-tracking step (NEE transmittance): T *= 1 - sigma_t/majorant.  Below
+// kRatioRR the estimate plays Russian roulette: it survives with probability
+// T/kRatioRR and is then set to kRatioRR, else it ends at 0.  Unbiased (the
+// expectation of the new T is the old T), and it ends shadow rays that cross
+// dense interiors after a few steps instead of a step per unit majorant depth.
+// Returns false when the estimate reached 0.
+constexpr float kRatioRR = 0.1f;
+
+__device__ __forceinline__ bool ratio_step(float& T, float st, float sbar, Rng& rng) {
+  T *= fmaxf(0.0f, 1.0f - st / sbar);
+  if (T < kRatioRR) {
+    if (T <= 0.0f) return false;
+    if (rng.next() * kRatioRR < T) {
+      T = kRatioRR;
+    } else {
+      T = 0.0f;
+      return false;
+    }
+  }
+  return true;
 }
 
 // Total extinction of the scene at x (objects add) and the field of the object

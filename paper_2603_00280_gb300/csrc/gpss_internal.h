@@ -41,7 +41,11 @@ struct gpss_scene_s {
   gpss::ObjectHost obj[gpss::kMaxObjects];
   gpss::LightDev light{};
   gpss::MajorantDev mg{};
-  float* maj = nullptr;            // device majorant grid
+  float* maj = nullptr;            // device majorant grid (fine level)
+  float2* skip = nullptr;          // device skip grid (M_r, r) per majorant cell
+  float* skip_tmp = nullptr;       // 3 x cells scratch for the skip build
+  int skip_levels = 5;             // radii 1, 2, ..., 2^(levels-1)
+  float kappa = 0.5f;              // expected majorant depth allowed per skip
   int brick = 1;                   // majorant cell = brick x finest field cell
   // scratch owned by the scene
   unsigned long long* counters = nullptr;   // kCntNum u64 + work cursor
@@ -62,6 +66,7 @@ gpss_status cuda_fail(cudaError_t e, const char* what);
 
 gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cudaStream_t st);
 gpss_status build_majorant(gpss_scene s, cudaStream_t st);
+gpss_status build_skip(gpss_scene s, cudaStream_t st);
 SceneDev scene_dev(const gpss_scene_s* s);
 bool camera_dev(const gpss_camera* c, CameraDev* out);
 

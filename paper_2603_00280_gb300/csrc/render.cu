@@ -6,10 +6,11 @@
 //     collisions at optical depth -ln(u) of the majorant, accepted as real with
 //     probability sigma_t / majorant;
 //   - at each real vertex, next-event estimation with a ratio-tracking shadow ray
-//     (T *= 1 - sigma_t/majorant at each tentative collision), MIS (power
-//     heuristic) against phase sampling for environment lights;
+//     (T *= 1 - sigma_t/majorant at each tentative collision, Russian roulette
+//     below T = 0.1), MIS (power heuristic) against phase sampling for
+//     environment lights;
 //   - phase sampling with the mixture of Sec. 4.2.2; at most max_bounces real
-//     vertices, no continuation after the last, no Russian roulette.
+//     vertices, no continuation after the last, no Russian roulette on paths.
 //
 // Execution model: one persistent thread per resident lane.  Each iteration of
 // the main loop advances every active lane by ONE tentative collision of its
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
 
     // ------------------------------------------------ one tentative collision
     bool hit = false;
-    if (walk_ok) hit = walk_advance(S.mg, w, -__logf(rng.next()), c_cells);
+    if (walk_ok) hit = walk_advance(S.mg, o, d, w, -__logf(rng.next()), c_cells);
     bool finish = false;
     if (hit) {
       ++events;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
         }
       } else {
         ++c_shadow;
-        T *= fmaxf(0.0f, 1.0f - st / w.sbar);
+        if (!ratio_step(T, st, w.sbar, rng)) walk_ok = false;  // T = 0: the shadow ray ends here
       }
       if (events >= kMaxEventsPerPath) {
         ++c_abort;

@@ -89,6 +89,37 @@ __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
   }
 }
 
+// Skip grid (see MajorantDev): running max filters over cubes of radius
+// 1, 2, 4, ... cells, built separably; the radius-2r max along an axis is the max
+// of the radius-r maxima at offsets -r and +r (indices clamped at the grid edge,
+// so a cube is clipped to the grid).
+__global__ void k_max_axis(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz, int axis,
+                           int off, int with_center) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const int dim = axis == 0 ? nx : axis == 1 ? ny : nz;
+    const int p = axis == 0 ? i : axis == 1 ? j : k;
+    const long long stride = axis == 0 ? 1 : axis == 1 ? nx : (long long)nx * ny;
+    const int lo = max(p - off, 0), hi = min(p + off, dim - 1);
+    float m = fmaxf(in[c + (lo - p) * stride], in[c + (hi - p) * stride]);
+    if (with_center) m = fmaxf(m, in[c]);
+    out[c] = m;
+  }
+}
+
+__global__ void k_skip_init(const float* __restrict__ maj, float2* __restrict__ skip, long long n) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    skip[c] = make_float2(maj[c], 0.0f);
+}
+
+__global__ void k_skip_select(const float* __restrict__ mr, float2* __restrict__ skip, long long n, int r, float limit) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const float m = mr[c];
+    if (m * (float)r <= limit && skip[c].y == (float)(r >> 1)) skip[c] = make_float2(m, (float)r);
+  }
+}
+
 static int blocks_for(size_t n, int block) {
   size_t b = (n + block - 1) / block;
   return (int)(b < 65536 ? (b ? b : 1) : 65536);
@@ -122,6 +153,32 @@ gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cuda
   return GPSS_OK;
 }
 
+gpss_status build_skip(gpss_scene s, cudaStream_t st) {
+  const int nx = s->mg.dims[0], ny = s->mg.dims[1], nz = s->mg.dims[2];
+  const long long n = (long long)nx * ny * nz;
+  const int nb = blocks_for((size_t)n, 256);
+  k_skip_init<<<nb, 256, 0, st>>>(s->maj, s->skip, n);
+  if (s->skip_levels > 0) {
+    float* P = s->skip_tmp;
+    float* Q = P + n;
+    float* R = Q + n;
+    const float hmin = fminf(fminf(s->mg.cell[0], s->mg.cell[1]), s->mg.cell[2]);
+    const float limit = s->kappa / hmin;  // M_r * r * h_min <= kappa
+    for (int lev = 0; lev < s->skip_levels; ++lev) {
+      const int r = 1 << lev;
+      const int off = lev == 0 ? 1 : r >> 1;
+      const float* src = lev == 0 ? s->maj : P;
+      k_max_axis<<<nb, 256, 0, st>>>(src, Q, nx, ny, nz, 0, off, lev == 0);
+      k_max_axis<<<nb, 256, 0, st>>>(Q, R, nx, ny, nz, 1, off, lev == 0);
+      k_max_axis<<<nb, 256, 0, st>>>(R, P, nx, ny, nz, 2, off, lev == 0);
+      k_skip_select<<<nb, 256, 0, st>>>(P, s->skip, n, r, limit);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "skip grid kernels");
+  return GPSS_OK;
+}
+
 SceneDev scene_dev(const gpss_scene_s* s) {
   SceneDev d;
   memset(&d, 0, sizeof(d));
@@ -142,6 +199,7 @@ SceneDev scene_dev(const gpss_scene_s* s) {
   }
   d.mg = s->mg;
   d.mg.maj = s->maj;
+  d.mg.skip = s->skip;
   d.light = s->light;
   return d;
 }
@@ -152,7 +210,7 @@ gpss_status build_majorant(gpss_scene s, cudaStream_t st) {
   k_majorant<<<blocks_for((size_t)ncell, 128), 128, 0, st>>>(S, s->mg, s->maj);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "majorant kernel");
-  return GPSS_OK;
+  return build_skip(s, st);
 }
 
 }  // namespace gpss

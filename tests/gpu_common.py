@@ -57,7 +57,12 @@ def image_z(gpu_mean, gpu_sqsum, gpu_spp, orc_sum, orc_sumsq, orc_spp):
     gv = np.maximum(np.asarray(gpu_sqsum, np.float64) / gpu_spp - gm ** 2, 0.0) / gpu_spp
     gv = np.maximum(gv, (FILM_REL * np.abs(gm)) ** 2)
     om = orc_sum / orc_spp
-    ov = np.maximum(orc_sumsq / orc_spp - om ** 2, 0.0) / orc_spp
+    ovar = np.maximum(orc_sumsq / orc_spp - om ** 2, 0.0)
+    # Under the null hypothesis both sides sample the same per-pixel distribution;
+    # the path weights are heavy tailed, so the smaller sample's variance estimate is
+    # raised to the pooled estimate (dominated by the larger, GPU sample).
+    pooled = (gv * gpu_spp * gpu_spp + ovar * orc_spp) / (gpu_spp + orc_spp)
+    ov = np.maximum(ovar, pooled) / orc_spp
     se = np.sqrt(gv + ov)
     z = np.where(se > 0, (gm - om) / np.where(se > 0, se, 1.0), np.where(np.abs(gm - om) > 1e-6, np.inf, 0.0))
     return z, gm, om, np.sqrt(gv), np.sqrt(ov)
