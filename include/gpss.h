@@ -126,6 +126,10 @@ gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* objs, int n_
  * kappa >= 0.  Defaults: 5 and 0.5.  Every choice is unbiased; they trade
  * traversal steps against null collisions (the autotuner's knobs). */
 gpss_status gpss_scene_set_traversal(gpss_scene s, int skip_levels, float kappa, gpss_stream stream);
+/* Warp scheduling of the render kernel: a warp shades its lanes that reached a
+ * real scattering vertex once at least `shade_min` (1..32) of them wait, or no
+ * other lane can advance.  Default 24.  Results do not depend on it. */
+gpss_status gpss_scene_set_schedule(gpss_scene s, int shade_min);
 /* Frees the scene.  Call after the stream's work on it has completed. */
 gpss_status gpss_scene_destroy(gpss_scene s);
 /* Majorant grid geometry: dims[3] cells and their values (device copy, may be NULL). */

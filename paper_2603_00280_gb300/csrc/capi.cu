@@ -277,6 +277,13 @@ extern "C" gpss_status gpss_scene_set_traversal(gpss_scene s, int skip_levels, f
   return build_skip(s, (cudaStream_t)stream);
 }
 
+extern "C" gpss_status gpss_scene_set_schedule(gpss_scene s, int shade_min) {
+  if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
+  if (shade_min < 1 || shade_min > 32) { set_error("shade_min must be in [1, 32]"); return GPSS_ERR_INVALID_ARG; }
+  s->shade_min = shade_min;
+  return GPSS_OK;
+}
+
 extern "C" gpss_status gpss_scene_destroy(gpss_scene s) {
   if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
   free_scene(s);
@@ -353,7 +360,7 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
   }
   const int block = render_block_size();
   const int grid = render_grid_size(s->device, block);
-  e = launch_render(scene_dev(s), C, *opts, dimg, dsq, path_rad, s->counters, grid, block, cs);
+  e = launch_render(scene_dev(s), C, *opts, dimg, dsq, path_rad, s->counters, grid, block, s->shade_min, cs);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   if (stats) cudaEventRecord(ev1, cs);
   if (host_img && (e = cudaMemcpyAsync(image, dimg, 3 * npx * sizeof(float), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)

@@ -115,6 +115,10 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// Out-of-line copy used by the path streams: the ten unrolled rounds then exist
+// once in the kernel instead of at every draw site (instruction-cache footprint).
+static __device__ __noinline__ U4 philox_block(U4 c, uint32_t k0, uint32_t k1) { return philox4x32_10(c, k0, k1); }
+
 // uniform in (0,1): 24 bits, centred
 __device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
 
@@ -141,7 +145,7 @@ struct Rng {
   }
   __device__ __forceinline__ float next() {
     if (avail == 0) {
-      const U4 r = philox4x32_10(U4{pixel, sample, tag, draw}, k0, k1);
+      const U4 r = philox_block(U4{pixel, sample, tag, draw}, k0, k1);
       ++draw;
       b0 = r.x; b1 = r.y; b2 = r.z; b3 = r.w;
       avail = 4;
@@ -165,7 +169,7 @@ __device__ __forceinline__ float psi(float a) {
   if (a <= 2.0f) return fmaf(-0.5f * a, erfcf(a), 0.5f * kInvSqrtPi * expf(-a * a));
   const float y = kSqrt2 * a;
   float r = 0.0f;
-#pragma unroll
+#pragma unroll 1
   for (int k = 20; k >= 1; --k) r = (float)k / (y + r);
   return erfcf(a) * r * (0.5f * kInvSqrt2);
 }
@@ -305,7 +309,7 @@ __device__ __forceinline__ void moments34(float q, float& m3, float& m4) {
   } else {
     const float x = -q;
     float r = 0.0f, r1 = 0.0f, r2 = 0.0f, r3 = 0.0f, r4 = 0.0f;
-#pragma unroll
+#pragma unroll 1
     for (int k = 24; k >= 1; --k) {
       r = (0.5f * (float)k) / (x + r);
       if (k == 4) r4 = r;
@@ -519,6 +523,32 @@ __device__ __forceinline__ bool phase_sample(V3 d, const Field& f, float alpha, 
   w_over_F = ndf_iso(m, f.g, alpha) * fabsf(dm) / (sd * pdf_m);
   pdf = pdf_m / (4.0f * fabsf(dm));
   return isfinite(w_over_F);
+}
+
+// Out-of-line entry points used at real vertices (rare compared with the
+// extinction evaluations of the traversal loop); results are returned by value.
+struct PhaseEval {
+  float p_over_F, pdf;
+  int ok;
+};
+struct PhaseSample {
+  V3 d2;
+  float w_over_F, pdf;
+  int ok;
+};
+
+static __device__ __noinline__ PhaseEval phase_eval_call(V3 d, V3 d2, Field f, float alpha, float R) {
+  PhaseEval r;
+  r.ok = phase_eval(d, d2, f, alpha, R, r.p_over_F, r.pdf);
+  return r;
+}
+
+static __device__ __noinline__ PhaseSample phase_sample_call(V3 d, Field f, float alpha, float R, float u0, float u1,
+                                                      float u2) {
+  PhaseSample r;
+  r.d2 = d;
+  r.ok = phase_sample(d, f, alpha, R, u0, u1, u2, r.d2, r.w_over_F, r.pdf);
+  return r;
 }
 
 // ---------------------------------------------------------------- lights and camera

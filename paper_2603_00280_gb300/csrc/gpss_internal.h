@@ -46,6 +46,7 @@ struct gpss_scene_s {
   float* skip_tmp = nullptr;       // 3 x cells scratch for the skip build
   int skip_levels = 5;             // radii 1, 2, ..., 2^(levels-1)
   float kappa = 0.5f;              // expected majorant depth allowed per skip
+  int shade_min = 24;              // lanes a warp gathers before shading real vertices
   int brick = 1;                   // majorant cell = brick x finest field cell
   // scratch owned by the scene
   unsigned long long* counters = nullptr;   // kCntNum u64 + work cursor
@@ -73,7 +74,7 @@ bool camera_dev(const gpss_camera* c, CameraDev* out);
 // kernels (launch wrappers)
 cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
                           float* sqsum, float* path_radiance, unsigned long long* counters, int grid, int block,
-                          cudaStream_t st);
+                          int shade_min, cudaStream_t st);
 int render_block_size();
 int render_grid_size(int device, int block);
 

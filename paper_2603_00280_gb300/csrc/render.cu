@@ -15,12 +15,15 @@
 // Execution model: one persistent thread per resident lane.  Each iteration of
 // the main loop advances every active lane by ONE tentative collision of its
 // current ray (the free-flight ray or the shadow ray), so all lanes of a warp run
-// the same field fetch + extinction code together; shading at real vertices is
-// the only divergent section.  A lane whose path has finished takes the next
-// (sample, pixel) index from a warp-private chunk of the global work cursor
-// (one atomic per chunk; ranks from __ballot_sync/__popc).  Path state lives in
-// registers.  Path index = sample * npix + pixel, so a chunk covers adjacent
-// pixels at the same sample.
+// the same traversal + extinction code together.  A lane whose flight ends in a
+// real collision waits; the warp shades its waiting lanes together once at least
+// `shade_min` of them wait (or no lane can step), so the long shading code runs
+// with many lanes active.  Shading functions and the Philox block are out of
+// line, keeping the traversal loop small in the instruction cache.  A lane whose
+// path has finished takes the next (sample, pixel) index from a warp-private
+// chunk of the global work cursor (one atomic per chunk; ranks from
+// __ballot_sync/__popc).  Path state lives in registers.  Path index =
+// sample * npix + pixel, so a chunk covers adjacent pixels at the same sample.
 #include "gpss_internal.h"
 
 namespace gpss {
@@ -36,44 +39,46 @@ struct RenderArgs {
   int npix;
   long long total;
   float inv_spp;
+  int shade_min;
 };
 
 enum Mode : int { kFlight = 0, kShadow = 1 };
 
-__device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d, float& st_k0, Field& f0, Local& l0) {
-  // Single object: fast path.  Several objects: extinctions add.
+// Total extinction at x (single object fast path; several objects add).
+__device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d) {
   if (S.n_objs == 1) {
-    if (!inside(S.obj[0], x)) { st_k0 = 0.0f; return 0.0f; }
-    st_k0 = sigma_t_object(S.obj[0], x, d, f0, l0);
-    return st_k0;
-  }
-  float tot = 0.0f;
-  st_k0 = 0.0f;
-  for (int k = 0; k < S.n_objs; ++k) {
-    if (!inside(S.obj[k], x)) continue;
+    if (!inside(S.obj[0], x)) return 0.0f;
     Field f;
     Local l;
-    tot += sigma_t_object(S.obj[k], x, d, f, l);
+    return sigma_t_object(S.obj[0], x, d, f, l);
   }
-  return tot;
+  return scene_sigma_t(S, x, d);
 }
 
-// Picks the scattering object in proportion to its extinction (Q13) and returns its field.
-__device__ __forceinline__ int choose_object(const SceneDev& S, V3 x, V3 d, float total, float u, Field& f, Local& l) {
-  float acc = 0.0f;
-  int last = -1;
-  const float pick = u * total;
+// The scattering object, chosen in proportion to its extinction (reading Q13),
+// and its field at x.
+static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, float u, Field& f, Local& l) {
+  float tot = 0.0f;
   for (int k = 0; k < S.n_objs; ++k) {
     if (!inside(S.obj[k], x)) continue;
     Field fk;
     Local lk;
-    const float s = sigma_t_object(S.obj[k], x, d, fk, lk);
-    if (s <= 0.0f) continue;
+    tot += sigma_t_object(S.obj[k], x, d, fk, lk);
+  }
+  float acc = 0.0f;
+  int last = 0;
+  const float pick = u * tot;
+  for (int k = 0; k < S.n_objs; ++k) {
+    if (!inside(S.obj[k], x)) continue;
+    Field fk;
+    Local lk;
+    const float st = sigma_t_object(S.obj[k], x, d, fk, lk);
+    if (st <= 0.0f) continue;
     last = k;
     f = fk;
     l = lk;
-    acc += s;
-    if (pick < acc) return k;
+    acc += st;
+    if (pick < acc) break;
   }
   return last;
 }
@@ -90,7 +95,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
   long long chunk_next = 0, chunk_end = 0;
   bool exhausted = false;
 
-  bool active = false;
+  bool active = false, waiting = false, begin = false;
   long long pidx = 0;
   uint32_t pixel = 0;
   Rng rng;
@@ -124,7 +129,6 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
         if ((long long)base >= P.total) exhausted = true;
       }
       if (!active && mine >= 0 && mine < P.total) {
-        // ---- new path
         pidx = mine;
         const int sample = (int)(mine / P.npix);
         pixel = (uint32_t)(mine - (long long)sample * P.npix);
@@ -139,90 +143,110 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
         mode = kFlight;
         events = 0;
         rng.start(0, kPurposeFlight);
-        walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+        begin = true;
+        waiting = false;
         active = true;
       }
     }
-    if (__ballot_sync(FULL, active) == 0) {
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) {
       if (exhausted || chunk_next >= P.total) break;
       continue;
     }
-    if (!active) continue;
+
+    // ------------------------------------------------ deferred shading of real vertices
+    const unsigned wait_mask = __ballot_sync(FULL, waiting);
+    if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act) && waiting) {
+      waiting = false;
+      const V3 x = fma3(w.t, d, o);
+      Field f;
+      Local l;
+      int k = 0;
+      if (S.n_objs > 1) {
+        k = choose_object(S, x, d, rng.next(), f, l);
+      } else {
+        f = fetch(S.obj[0], x);
+        l = local_of(S.obj[0], f);
+      }
+      const V3 F = fetch_albedo(S.obj[k], x);
+      o = x;
+      cont = bounce + 1 < P.max_bounces;
+      if (cont) {
+        rng.start((uint32_t)bounce, kPurposePhase);
+        const float u0 = rng.next(), u1 = rng.next(), u2 = rng.next();
+        const PhaseSample ps = phase_sample_call(d, f, l.alpha, P.mix_R, u0, u1, u2);
+        if (ps.ok) {
+          d_next = ps.d2;
+          beta_next = v3(beta.x * F.x * ps.w_over_F, beta.y * F.y * ps.w_over_F, beta.z * F.z * ps.w_over_F);
+          pdf_next = ps.pdf;
+        } else {
+          cont = false;
+        }
+      } else {
+        ++c_trunc;
+      }
+      rng.start((uint32_t)bounce, kPurposeNee);
+      V3 wl, Le;
+      float lpdf_w;  // MIS weight / light pdf (directional: 1)
+      if (!env) {
+        wl = v3(S.light.dir[0], S.light.dir[1], S.light.dir[2]);
+        Le = v3(S.light.radiance[0], S.light.radiance[1], S.light.radiance[2]);
+      } else {
+        const float z = 1.0f - 2.0f * rng.next();
+        const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+        float sp, cp;
+        sincospif(2.0f * rng.next(), &sp, &cp);
+        wl = v3(r * cp, r * sp, z);
+        Le = env_radiance(S.light, wl);
+      }
+      const PhaseEval pe = phase_eval_call(d, wl, f, l.alpha, P.mix_R);
+      if (!env) {
+        lpdf_w = 1.0f;
+      } else {
+        lpdf_w = power_heuristic(kInv4Pi, pe.pdf) * (4.0f * kPi);
+      }
+      const float scale = pe.p_over_F * lpdf_w;
+      pend = v3(beta.x * F.x * scale * Le.x, beta.y * F.y * scale * Le.y, beta.z * F.z * scale * Le.z);
+      ++bounce;
+      if (scale > 0.0f) {
+        mode = kShadow;
+        d = wl;
+        T = 1.0f;
+        begin = true;
+      } else if (cont) {
+        mode = kFlight;
+        d = d_next;
+        beta = beta_next;
+        prev_pdf = pdf_next;
+        rng.start((uint32_t)bounce, kPurposeFlight);
+        begin = true;
+      } else {
+        // no shadow ray and no continuation: with walk_ok = false and beta = 0 the
+        // step below treats the lane as an escaped flight that adds nothing
+        mode = kFlight;
+        walk_ok = false;
+        begin = false;
+        d = v3(0.0f, 0.0f, 0.0f);
+        beta = v3(0.0f, 0.0f, 0.0f);
+      }
+    }
+    if (!active || waiting) continue;
 
     // ------------------------------------------------ one tentative collision
+    if (begin) {
+      walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+      begin = false;
+    }
     bool hit = false;
     if (walk_ok) hit = walk_advance(S.mg, o, d, w, -__logf(rng.next()), c_cells);
     bool finish = false;
     if (hit) {
       ++events;
-      const V3 x = fma3(w.t, d, o);
-      Field f;
-      Local l;
-      float st0;
-      const float st = sigma_t_at(S, x, d, st0, f, l);
+      const float st = sigma_t_at(S, fma3(w.t, d, o), d);
       if (mode == kFlight) {
-        const float ua = rng.next();
-        if (ua * w.sbar < st) {
-          // ---------------------------------------- real scattering vertex
+        if (rng.next() * w.sbar < st) {
           ++c_vert;
-          int k = 0;
-          if (S.n_objs > 1) k = choose_object(S, x, d, st, rng.next(), f, l);
-          const ObjectDev& ob = S.obj[k];
-          const V3 F = fetch_albedo(ob, x);
-          o = x;
-          cont = bounce + 1 < P.max_bounces;
-          if (cont) {
-            rng.start((uint32_t)bounce, kPurposePhase);
-            const float u0 = rng.next(), u1 = rng.next(), u2 = rng.next();
-            float wF, pdf;
-            V3 d2;
-            if (phase_sample(d, f, l.alpha, P.mix_R, u0, u1, u2, d2, wF, pdf)) {
-              d_next = d2;
-              beta_next = v3(beta.x * F.x * wF, beta.y * F.y * wF, beta.z * F.z * wF);
-              pdf_next = pdf;
-            } else {
-              cont = false;
-            }
-          } else {
-            ++c_trunc;
-          }
-          rng.start((uint32_t)bounce, kPurposeNee);
-          V3 wl;
-          float scale;
-          if (!env) {
-            wl = v3(S.light.dir[0], S.light.dir[1], S.light.dir[2]);
-            float pF, pdf_ph;
-            phase_eval(d, wl, f, l.alpha, P.mix_R, pF, pdf_ph);
-            scale = pF;
-            pend = v3(beta.x * F.x * scale * S.light.radiance[0], beta.y * F.y * scale * S.light.radiance[1],
-                      beta.z * F.z * scale * S.light.radiance[2]);
-          } else {
-            const float z = 1.0f - 2.0f * rng.next();
-            const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-            float sp, cp;
-            sincospif(2.0f * rng.next(), &sp, &cp);
-            wl = v3(r * cp, r * sp, z);
-            float pF, pdf_ph;
-            phase_eval(d, wl, f, l.alpha, P.mix_R, pF, pdf_ph);
-            const V3 Le = env_radiance(S.light, wl);
-            scale = pF * power_heuristic(kInv4Pi, pdf_ph) * (4.0f * kPi);
-            pend = v3(beta.x * F.x * scale * Le.x, beta.y * F.y * scale * Le.y, beta.z * F.z * scale * Le.z);
-          }
-          ++bounce;
-          if (scale > 0.0f) {
-            mode = kShadow;
-            d = wl;
-            T = 1.0f;
-            walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
-          } else if (cont) {
-            d = d_next;
-            beta = beta_next;
-            prev_pdf = pdf_next;
-            rng.start((uint32_t)bounce, kPurposeFlight);
-            walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
-          } else {
-            finish = true;
-          }
+          waiting = true;      // real scattering vertex: shaded with the warp's other waiting lanes
         } else {
           ++c_null;
         }
@@ -233,6 +257,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
       if (events >= kMaxEventsPerPath) {
         ++c_abort;
         finish = true;
+        waiting = false;
       }
     } else {
       if (mode == kFlight) {
@@ -250,7 +275,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const SceneDev S, const
           beta = beta_next;
           prev_pdf = pdf_next;
           rng.start((uint32_t)bounce, kPurposeFlight);
-          walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
+          begin = true;
         } else {
           finish = true;
         }
@@ -300,7 +325,7 @@ int render_grid_size(int device, int block) {
 
 cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
                           float* sqsum, float* path_radiance, unsigned long long* counters, int grid, int block,
-                          cudaStream_t st) {
+                          int shade_min, cudaStream_t st) {
   RenderArgs P;
   P.spp = o.spp;
   P.max_bounces = o.max_bounces;
@@ -309,6 +334,7 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   P.npix = C.width * C.height;
   P.total = (long long)P.npix * o.spp;
   P.inv_spp = 1.0f / (float)o.spp;
+  P.shade_min = shade_min;
   k_render<<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters);
   return cudaGetLastError();
 }

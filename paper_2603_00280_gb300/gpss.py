@@ -70,6 +70,7 @@ _SIGS = {
     "gpss_scene_update": [_VP, ctypes.POINTER(ObjectDesc), _I, _VP],
     "gpss_scene_destroy": [_VP],
     "gpss_scene_set_traversal": [_VP, _I, _F, _VP],
+    "gpss_scene_set_schedule": [_VP, _I],
     "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
     "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
     "gpss_render_adjoint": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, _VP, _VP, _VP,
@@ -230,6 +231,9 @@ class Scene:
         descs = _object_descs(objects, keep)
         _call("gpss_scene_update", self.handle, descs, len(objects), _stream(stream))
         del keep
+
+    def set_schedule(self, shade_min: int = 24):
+        _call("gpss_scene_set_schedule", self.handle, int(shade_min))
 
     def set_traversal(self, skip_levels: int = 5, kappa: float = 0.5, stream=None):
         _call("gpss_scene_set_traversal", self.handle, int(skip_levels), float(kappa), _stream(stream))
