@@ -147,6 +147,23 @@ gpss_status gpss_scene_majorant(gpss_scene s, int dims[3], float* values, gpss_s
 gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts, float* image,
                         float* sqsum, gpss_stats* stats, gpss_stream stream);
 
+/* Forward render that allocates no device memory during the call (the paper has
+ * no counterpart; it is an integration aid).  For callers that may not allocate
+ * at render time: applications that account for every device byte themselves,
+ * real-time loops where an allocation's latency or failure is unacceptable, or
+ * code recording work into a stream capture.  Same result as gpss_render with
+ * the same scene, camera and options (image only: no sqsum, no per-path
+ * radiance, stats->ms = 0).  The work counters and a film of at most 65536
+ * pixels (e.g. 256 x 256) live in a fixed 0.8 MB static device array that every
+ * GPU loading the library keeps until the process exits; larger images are
+ * rejected with GPSS_ERR_INVALID_ARG.  image: W*H*3 floats, host or device.
+ * The first call on a device looks up the array's device address (make that
+ * first call before any stream capture).  All calls share the array and clear
+ * it before use: calls that overlap on the GPU race and must be serialised by
+ * the caller. */
+gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts, float* image,
+                                gpss_stats* stats, gpss_stream stream);
+
 /* Path-replay adjoint.  d_image: H*W*3 (dLoss/dimage, device).  Gradients are
  * ACCUMULATED (+=) into d_mean, d_variance (nx*ny*nz each, object 0), d_albedo
  * (channels planes) and d_length_scale (1 float); any output may be NULL.

@@ -73,6 +73,7 @@ _SIGS = {
     "gpss_scene_set_schedule": [_VP, _I],
     "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
     "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
+    "gpss_render_noalloc": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, ctypes.POINTER(Stats), _VP],
     "gpss_render_adjoint": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, _VP, _VP, _VP,
                             ctypes.POINTER(Stats), _VP],
     "gpss_batch_create": [ctypes.POINTER(_VP), ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _I, _I, _VP,
