@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--image", type=int, default=0, help="override the image side (profiling of small cases)")
     ap.add_argument("--spp", type=int, default=0, help="override samples per pixel (profiling of small cases)")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -195,6 +196,41 @@ def oracle_sample(wl, target_seconds, threads=0):
     return st["vertices"] / dt / 1e6, desc, cores, dt
 
 
+# ----------------------------------------------------------------- forward + adjoint
+def measure_adjoint(args, gpss, torch, flush, rank):
+    """Forward render and path-replay adjoint of the differentiable workload
+    (64^3 grids, 256x256, 64 spp): M path-vertices/s over forward + adjoint time
+    and the ratio (t_fwd + t_adj) / t_fwd."""
+    from paper_2603_00280_gb300 import workloads as W
+    wl = W.differentiable(seed=12345 + 1000 * rank)
+    cam, opts = wl["camera"], wl["opts"]
+    S = gpss.Scene(wl["scene"])
+    H, Wd = cam["height"], cam["width"]
+    img = torch.empty((H, Wd, 3), device="cuda")
+    g = torch.ones((H, Wd, 3), device="cuda")
+    shape = wl["scene"]["objects"][0]["mean"].shape
+    dm, dv = torch.zeros(shape, device="cuda"), torch.zeros(shape, device="cuda")
+    da, dl = torch.zeros((1,) + shape, device="cuda"), torch.zeros(1, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        gpss.render(S, cam, opts, image=img, stats=False, keep_path_radiance=True)
+        gpss.render_adjoint(S, cam, opts, g, dm, dv, da, dl, stats=False)
+    tf, ta, verts = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        _, _, st = gpss.render(S, cam, opts, image=img, stats=True, keep_path_radiance=True)
+        tf.append(st["ms"])
+        verts += st["vertices"]
+        flush.zero_()
+        sa = gpss.render_adjoint(S, cam, opts, g, dm, dv, da, dl, stats=True)
+        ta.append(sa["ms"])
+        mism = sa["aborted"]
+    t_f, t_a = sum(tf), sum(ta)
+    return {"workload": wl["name"], "image": [Wd, H], "spp": opts["spp"], "max_bounces": opts["max_bounces"],
+            "value": verts / ((t_f + t_a) / 1e3) / 1e6, "unit": UNIT, "fwd_ms": t_f / args.steps,
+            "adj_ms": t_a / args.steps, "ratio_fwd_plus_adj_over_fwd": (t_f + t_a) / t_f,
+            "replay_mismatches": mism}
+
+
 # ----------------------------------------------------------------- arms
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -304,6 +340,8 @@ def run_ours(args):
         e2e = {"value": float(et[1]) / (float(et[0]) / 1e3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": H * W * 3 * 4}
 
+    adj = None if args.no_adjoint else measure_adjoint(args, gpss, torch, flush, rank)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -319,7 +357,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl, "flushed between steps (256 MB write)"),
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
-           "clocks": clk,
+           "clocks": clk, "fwd_adjoint": adj,
            "work": {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
                     "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
                     "majorant_cells_per_step": stats["majorant_cells"],

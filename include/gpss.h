@@ -164,11 +164,15 @@ gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const gpss_render_
 gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts, float* image,
                                 gpss_stats* stats, gpss_stream stream);
 
-/* Path-replay adjoint.  d_image: H*W*3 (dLoss/dimage, device).  Gradients are
- * ACCUMULATED (+=) into d_mean, d_variance (nx*ny*nz each, object 0), d_albedo
- * (channels planes) and d_length_scale (1 float); any output may be NULL.
- * Paths are replayed from the same random numbers as gpss_render with equal
- * camera and options. */
+/* Path-replay adjoint (gradients of the image's expectation).  d_image: H*W*3
+ * (dLoss/dimage, device).  Gradients are ACCUMULATED (+=) into d_mean, d_variance
+ * (nx*ny*nz each), d_albedo (channels planes) and d_length_scale (1 float); any
+ * output may be NULL.  Single-object scenes only (UNSUPPORTED otherwise).  The
+ * paths are those of gpss_render with equal camera and options: if the scene
+ * kept their per-path radiance (GPSS_FLAG_KEEP_PATH_RADIANCE on that render, no
+ * scene update since) it is reused, else the forward paths are traced first.
+ * stats->aborted counts replayed paths that did not reproduce their forward
+ * radiance (expected 0). */
 gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts,
                                 const float* d_image, float* d_mean, float* d_variance, float* d_albedo,
                                 float* d_length_scale, gpss_stats* stats, gpss_stream stream);

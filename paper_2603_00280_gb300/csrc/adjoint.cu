@@ -1,0 +1,137 @@
+// adjoint.cu -- gradients of a rendered image with respect to the scene's grids
+// (mean, variance, albedo) and the kernel length scale: the adjoint instance of
+// the persistent path kernel (see path_kernel.cuh for the estimator).
+#include <cstring>
+
+#include "path_kernel.cuh"
+
+namespace gpss {
+
+// Fingerprint of (camera, options without flags, scene contents): identifies the
+// render whose per-path radiance the scene keeps.
+uint64_t path_fingerprint(const gpss_camera* cam, const gpss_render_opts* o, uint64_t scene_version) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  gpss_render_opts oo = *o;
+  oo.flags = 0;
+  mix(cam, sizeof(*cam));
+  mix(&oo.spp, sizeof(oo.spp));
+  mix(&oo.max_bounces, sizeof(oo.max_bounces));
+  mix(&oo.seed, sizeof(oo.seed));
+  mix(&oo.mix_R, sizeof(oo.mix_R));
+  mix(&scene_version, sizeof(scene_version));
+  return h | 1ull;
+}
+
+gpss_status check_opts(const gpss_render_opts* o);
+
+}  // namespace gpss
+
+using namespace gpss;
+
+extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts,
+                                           const float* d_image, float* d_mean, float* d_variance, float* d_albedo,
+                                           float* d_length_scale, gpss_stats* stats, gpss_stream stream) {
+  if (!s || !d_image) { set_error("null scene or d_image"); return GPSS_ERR_INVALID_ARG; }
+  gpss_status st = check_opts(opts);
+  if (st != GPSS_OK) return st;
+  if (s->n_objs != 1) { set_error("the adjoint supports single-object scenes"); return GPSS_ERR_UNSUPPORTED; }
+  CameraDev C;
+  if (!camera_dev(cam, &C)) return GPSS_ERR_INVALID_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const size_t npx = (size_t)C.width * C.height;
+  const long long total = (long long)npx * opts->spp;
+  const uint64_t fp = path_fingerprint(cam, opts, s->version);
+  cudaError_t e;
+  const int block = render_block_size();
+  const int grid = render_grid_size(s->device, block);
+  if (s->path_tag != fp) {
+    // no kept radiance of this render: run the forward pass first (paths only)
+    const size_t nT = (size_t)total * opts->max_bounces;
+    if (s->path_capacity < 3 * (size_t)total) {
+      cudaFree(s->path_radiance);
+      s->path_radiance = nullptr;
+      s->path_capacity = 0;
+      if ((e = cudaMalloc(&s->path_radiance, 3 * (size_t)total * sizeof(float))) != cudaSuccess)
+        return cuda_fail(e, "path radiance allocation");
+      s->path_capacity = 3 * (size_t)total;
+    }
+    if (s->pathT_capacity < nT) {
+      cudaFree(s->path_T);
+      s->path_T = nullptr;
+      s->pathT_capacity = 0;
+      if ((e = cudaMalloc(&s->path_T, nT * sizeof(float))) != cudaSuccess)
+        return cuda_fail(e, "path transmittance allocation");
+      s->pathT_capacity = nT;
+    }
+    if (s->film_capacity < 6 * npx) {
+      cudaFree(s->film);
+      s->film = nullptr;
+      s->film_capacity = 0;
+      if ((e = cudaMalloc(&s->film, 6 * npx * sizeof(float))) != cudaSuccess) return cuda_fail(e, "film allocation");
+      s->film_capacity = 6 * npx;
+    }
+    if ((e = cudaMemsetAsync(s->film, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear film");
+    if ((e = cudaMemsetAsync(s->counters, 0, 16 * sizeof(unsigned long long), cs)) != cudaSuccess)
+      return cuda_fail(e, "clear counters");
+    e = launch_render(scene_dev(s), C, *opts, s->film, nullptr, s->path_radiance, s->path_T, s->counters, grid, block,
+                      s->shade_min, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    s->path_tag = fp;
+  }
+  if ((e = cudaMemsetAsync(s->counters, 0, 16 * sizeof(unsigned long long), cs)) != cudaSuccess)
+    return cuda_fail(e, "clear counters");
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (stats) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, cs);
+  }
+  PathArgs P;
+  P.spp = opts->spp;
+  P.max_bounces = opts->max_bounces;
+  P.seed = opts->seed;
+  P.mix_R = opts->mix_R;
+  P.npix = (int)npx;
+  P.total = total;
+  P.inv_spp = 1.0f / (float)opts->spp;
+  P.shade_min = s->shade_min;
+  AdjOut A;
+  A.d_image = d_image;
+  A.L_path = s->path_radiance;
+  A.T_path = s->path_T;
+  A.d_mean = d_mean;
+  A.d_var = d_variance;
+  A.d_alb = d_albedo;
+  A.d_l = d_length_scale;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true>, kPathBlock, 0);
+  const int agrid = sms * (per_sm > 0 ? per_sm : 1);
+  k_path<true><<<agrid, kPathBlock, 0, cs>>>(scene_dev(s), C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  if (stats) {
+    cudaEventRecord(ev1, cs);
+    unsigned long long c[16];
+    if ((e = cudaMemcpyAsync(c, s->counters, sizeof(c), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+      return cuda_fail(e, "stats copy");
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "adjoint");
+    stats->paths = c[kCntPaths];
+    stats->vertices = c[kCntVertices];
+    stats->null_collisions = c[kCntNull];
+    stats->shadow_steps = c[kCntShadow];
+    stats->majorant_cells = c[kCntCells];
+    stats->truncated = c[kCntTruncated];
+    stats->aborted = c[kCntAborted];
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    stats->ms = ms;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  return GPSS_OK;
+}

@@ -1,0 +1,130 @@
+// adjoint_math.cuh -- partial derivatives of the extinction and of the phase-function
+// factors, and their scatter to grid nodes (used by the adjoint instance of the path
+// kernel).  Derivations (u = mu/sigma, lambda = phi/Phi, a = d.grad mu/alpha,
+// alpha = sqrt2 sigma/l, q = m.grad mu/alpha, M_k the NDF moments):
+//   d sigma_t/d mu      = sigma(d) lambda'(u)/sigma^2,   lambda' = -lambda (u + lambda)
+//   d sigma_t/d grad mu = -rho erfc(a)/2 d
+//   d sigma_t/d sigma   = -sigma(d) (lambda' u + lambda)/sigma^2 + rho e^{-a^2}/(2 sqrt pi) alpha/sigma
+//   d sigma_t/d l       = -rho e^{-a^2}/(2 sqrt pi) alpha/l
+//   d ln D/d grad mu    = (2 M4/(alpha M3)) m - (2/alpha^2) grad mu
+//   d ln D/d alpha      = 1/alpha + 2|grad mu|^2/alpha^3 - 2 q M4/(alpha M3)
+//   d ln sigma(d)/d grad mu = -erfc(a)/(2 sigma(d)) d,   d ln sigma(d)/d alpha = e^{-a^2}/(2 sqrt pi sigma(d))
+#pragma once
+
+#include "gpss_device.cuh"
+
+namespace gpss {
+
+// psi(a) and the two ratios erfc(a)/psi(a), (e^{-a^2}/(2 sqrt pi))/psi(a), without
+// underflow for large a (continued fraction as in psi()).
+__device__ __forceinline__ void psi_ratios(float a, float& ps, float& ec_over, float& ea_over) {
+  if (a <= 2.0f) {
+    const float ec = erfcf(a);
+    const float ea = 0.5f * kInvSqrtPi * expf(-a * a);
+    ps = fmaf(-0.5f * a, ec, ea);
+    ec_over = ec / ps;
+    ea_over = ea / ps;
+  } else {
+    const float y = kSqrt2 * a;
+    float r = 0.0f;
+#pragma unroll 1
+    for (int k = 20; k >= 1; --k) r = (float)k / (y + r);
+    ps = erfcf(a) * r * (0.5f * kInvSqrt2);
+    ec_over = 2.0f * kSqrt2 / r;
+    ea_over = kSqrt2 * kInvSqrtPi / (erfcxf(a) * r);
+  }
+}
+
+// Extinction of one object and its partials at a field sample.
+struct DSig {
+  float st, dmu, dvar, dl;
+  V3 dg;
+};
+
+__device__ __forceinline__ DSig dsigma_t(const ObjectDev& o, const Field& f, V3 d) {
+  const float sig = sqrtf(f.var);
+  const float alpha = sig * o.alpha_scale;
+  const float u = f.mu / sig;
+  const float lam = inv_mills(u);
+  const float lamp = -lam * (u + lam);
+  const float rho = lam / sig;
+  float ps, ec_over, ea_over;
+  psi_ratios(dot(d, f.g) / alpha, ps, ec_over, ea_over);
+  const float S = alpha * ps;
+  DSig r;
+  r.st = rho * S;
+  r.dmu = S * lamp / f.var;
+  r.dg = (-0.5f * rho * ps * ec_over * alpha) * d;  // rho erfc(a)/2 with erfc = ec_over psi
+  const float dsig = S * (-(lamp * u + lam) / f.var) + rho * ps * ea_over * alpha / sig;
+  r.dvar = dsig / (2.0f * sig);
+  r.dl = -rho * ps * ea_over * alpha * (o.alpha_scale * kInvSqrt2);  // 1/l = alpha_scale/sqrt2
+  return r;
+}
+
+// d ln(D(m)/sigma(d)) with respect to grad mu, the variance and l.
+struct DPhase {
+  V3 dg;
+  float dvar, dl;
+};
+
+static __device__ __noinline__ DPhase dlog_phase(V3 d, V3 m, Field f, float alpha_scale) {
+  const float sig = sqrtf(f.var);
+  const float alpha = sig * alpha_scale;
+  float r4;
+  ndf_iso(m, f.g, alpha, &r4);
+  const float q = dot(m, f.g) / alpha;
+  const float G2 = dot(f.g, f.g);
+  const float inv_a = 1.0f / alpha;
+  V3 dg = fma3(-2.0f * inv_a * inv_a, f.g, (2.0f * r4 * inv_a) * m);
+  float dalpha = inv_a + 2.0f * G2 * inv_a * inv_a * inv_a - 2.0f * r4 * q * inv_a;
+  float ps, ec_over, ea_over;
+  psi_ratios(dot(d, f.g) * inv_a, ps, ec_over, ea_over);
+  // sigma(d) = alpha psi: d ln/d grad mu = -erfc/(2 alpha psi) d, d ln/d alpha = ea/(alpha psi)
+  dg = fma3(0.5f * ec_over * inv_a, d, dg);
+  dalpha -= ea_over * inv_a;
+  DPhase r;
+  r.dg = dg;
+  r.dvar = dalpha * alpha / (2.0f * f.var);
+  r.dl = -dalpha * alpha * (alpha_scale * kInvSqrt2);
+  return r;
+}
+
+// Scatters c_mu * dmu/d(node) + c_g . d(grad mu)/d(node) and c_var * dvar/d(node).
+static __device__ __noinline__ void scatter_field(const ObjectDev& o, V3 x, float cmu, V3 cg, float cvar,
+                                                  float* __restrict__ dmean, float* __restrict__ dvar) {
+  float wx, wy, wz;
+  const int b = cell_of(o, x, wx, wy, wz);
+  const int sy = o.n[0], sz = o.n[0] * o.n[1];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    const float ax = cx ? wx : 1.0f - wx, ay = cy ? wy : 1.0f - wy, az = cz ? wz : 1.0f - wz;
+    const float sx = cx ? 1.0f : -1.0f, syy = cy ? 1.0f : -1.0f, szz = cz ? 1.0f : -1.0f;
+    const float w = ax * ay * az;
+    const float gx = sx * ay * az * o.inv_h[0], gy = ax * syy * az * o.inv_h[1], gz = ax * ay * szz * o.inv_h[2];
+    const int idx = b + cx + sy * cy + sz * cz;
+    if (dmean) atomicAdd(dmean + idx, fmaf(cmu, w, fmaf(cg.x, gx, fmaf(cg.y, gy, cg.z * gz))));
+    if (dvar) atomicAdd(dvar + idx, cvar * w);
+  }
+}
+
+static __device__ __noinline__ void scatter_albedo(const ObjectDev& o, V3 x, V3 c, float* __restrict__ dalb) {
+  float wx, wy, wz;
+  const int b = cell_of(o, x, wx, wy, wz);
+  const int sy = o.n[0], sz = o.n[0] * o.n[1];
+  const int plane = sz * o.n[2];
+  const float cc[3] = {c.x, c.y, c.z};
+#pragma unroll
+  for (int corner = 0; corner < 8; ++corner) {
+    const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+    const float w = (cx ? wx : 1.0f - wx) * (cy ? wy : 1.0f - wy) * (cz ? wz : 1.0f - wz);
+    const int idx = b + cx + sy * cy + sz * cz;
+    if (o.channels == 1) {
+      atomicAdd(dalb + idx, (cc[0] + cc[1] + cc[2]) * w);
+    } else {
+      for (int ch = 0; ch < 3; ++ch) atomicAdd(dalb + ch * plane + idx, cc[ch] * w);
+    }
+  }
+}
+
+}  // namespace gpss

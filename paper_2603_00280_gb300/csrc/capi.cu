@@ -137,6 +137,7 @@ static void free_scene(gpss_scene s) {
   cudaFree(s->flags);
   cudaFree(s->film);
   cudaFree(s->path_radiance);
+  cudaFree(s->path_T);
   delete s;
 }
 
@@ -265,6 +266,7 @@ extern "C" gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* o
   cudaStream_t cs = (cudaStream_t)stream;
   if ((st = scene_upload(s, objs, n_objs, cs)) != GPSS_OK) return st;
   s->path_tag = 0;
+  ++s->version;
   return build_majorant(s, cs);
 }
 
@@ -343,10 +345,15 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
     if (host_sq) dsq = s->film + 3 * npx;
   }
   float* path_rad = nullptr;
+  float* path_T = nullptr;
   if (opts->flags & GPSS_FLAG_KEEP_PATH_RADIANCE) {
     if ((st = ensure(&s->path_radiance, &s->path_capacity, 3 * (size_t)total, "path radiance allocation")) != GPSS_OK)
       return st;
+    if ((st = ensure(&s->path_T, &s->pathT_capacity, (size_t)total * opts->max_bounces, "path transmittance allocation")) !=
+        GPSS_OK)
+      return st;
     path_rad = s->path_radiance;
+    path_T = s->path_T;
   }
   if ((e = cudaMemsetAsync(dimg, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear image");
   if (dsq && (e = cudaMemsetAsync(dsq, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear sqsum");
@@ -360,14 +367,14 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
   }
   const int block = render_block_size();
   const int grid = render_grid_size(s->device, block);
-  e = launch_render(scene_dev(s), C, *opts, dimg, dsq, path_rad, s->counters, grid, block, s->shade_min, cs);
+  e = launch_render(scene_dev(s), C, *opts, dimg, dsq, path_rad, path_T, s->counters, grid, block, s->shade_min, cs);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   if (stats) cudaEventRecord(ev1, cs);
   if (host_img && (e = cudaMemcpyAsync(image, dimg, 3 * npx * sizeof(float), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
     return cuda_fail(e, "image copy");
   if (host_sq && (e = cudaMemcpyAsync(sqsum, dsq, 3 * npx * sizeof(float), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
     return cuda_fail(e, "sqsum copy");
-  if (path_rad) s->path_tag = opts->seed ^ ((uint64_t)opts->spp << 48) ^ ((uint64_t)npx << 20) ^ 0x9E3779B97F4A7C15ull;
+  if (path_rad) s->path_tag = path_fingerprint(cam, opts, s->version);
   if (stats || host_img || host_sq) {
     unsigned long long c[16];
     if (stats && (e = cudaMemcpyAsync(c, s->counters, sizeof(c), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
@@ -392,12 +399,6 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
 }
 
 // ------------------------------------------------------------------ not yet available
-extern "C" gpss_status gpss_render_adjoint(gpss_scene, const gpss_camera*, const gpss_render_opts*, const float*,
-                                           float*, float*, float*, float*, gpss_stats*, gpss_stream) {
-  set_error("adjoint not built");
-  return GPSS_ERR_UNSUPPORTED;
-}
-
 extern "C" gpss_status gpss_batch_create(const gpss_scene*, const gpss_camera*, const gpss_render_opts*, int, int,
                                          gpss_stream, gpss_batch* out) {
   if (out) *out = nullptr;

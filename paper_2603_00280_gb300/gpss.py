@@ -383,3 +383,49 @@ def philox4x32_10(ctr, key, stream=None):
     out = torch.empty(4 * n, device="cuda", dtype=torch.int32)
     _call("gpss_philox4x32_10", n, _ptr(c), _ptr(k), _ptr(out), _stream(stream))
     return out.cpu().numpy().view(np.uint32).reshape(n, 4)
+
+
+# ----------------------------------------------------------------- differentiable rendering
+class _RenderFn:
+    """torch.autograd.Function wrapper (defined lazily so that importing this
+    module needs no CUDA).  Forward: upload the parameter tensors into the scene
+    (single object) and render.  Backward: gpss_render_adjoint with the incoming
+    image gradient; returns gradients for mean, variance, albedo, length scale."""
+    fn = None
+
+    @classmethod
+    def get(cls):
+        if cls.fn is None:
+            import torch
+
+            class RenderFunction(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, mean, var, albedo, length_scale, scene, obj, camera, opts):
+                    o = dict(obj)
+                    o["mean"], o["var"], o["albedo"] = mean.detach(), var.detach(), albedo.detach()
+                    o["length_scale"] = float(length_scale)
+                    scene.update([o])
+                    image, _, _ = render(scene, camera, opts, stats=False, keep_path_radiance=True)
+                    ctx.scene, ctx.camera, ctx.opts = scene, camera, opts
+                    ctx.shapes = (mean.shape, var.shape, albedo.shape)
+                    return image
+
+                @staticmethod
+                def backward(ctx, grad_image):
+                    g = grad_image.contiguous().float()
+                    dm = torch.zeros(ctx.shapes[0], device="cuda", dtype=torch.float32)
+                    dv = torch.zeros(ctx.shapes[1], device="cuda", dtype=torch.float32)
+                    da = torch.zeros(ctx.shapes[2], device="cuda", dtype=torch.float32)
+                    dl = torch.zeros(1, device="cuda", dtype=torch.float32)
+                    render_adjoint(ctx.scene, ctx.camera, ctx.opts, g, dm, dv, da, dl, stats=False)
+                    return dm, dv, da, dl[0], None, None, None, None
+
+            cls.fn = RenderFunction
+        return cls.fn
+
+
+def render_differentiable(scene: Scene, obj: dict, mean, var, albedo, length_scale, camera: dict, opts: dict):
+    """Differentiable render of a single-object scene.  mean/var/albedo are CUDA
+    tensors shaped like the scene's grids; length_scale a 0-d CUDA tensor.  obj
+    supplies the box (bbox_min, bbox_max).  Returns the (H, W, 3) image."""
+    return _RenderFn.get().apply(mean, var, albedo, length_scale, scene, obj, camera, opts)

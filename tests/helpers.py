@@ -129,11 +129,12 @@ def slab_optical_depth(z0, z1, d, sigma=SLAB_SIGMA, l=SLAB_L):
     return slab_projected_area(d, sigma, l) / d[2] * (sp.log_ndtr(z1 / sigma) - sp.log_ndtr(z0 / sigma))
 
 
-def slab_single_scatter(d, wl, albedo, sigma=SLAB_SIGMA, l=SLAB_L, irradiance=1.0, ztop=0.125, zbot=-0.125):
+def slab_single_scatter(d, wl, albedo, sigma=SLAB_SIGMA, l=SLAB_L, irradiance=1.0, ztop=0.125, zbot=-0.125, shift=0.0):
     """Exact single-scattered radiance for a ray entering the slab top along d
     (d_z < 0) and leaving through the bottom, lit by a directional light from
     wl (wl_z > 0, leaving through the top).  p is constant along the ray, so
-    L = int Tr_cam sigma_t p Tr_light E dt is a 1-D integral of closed forms."""
+    L = int Tr_cam sigma_t p Tr_light E dt is a 1-D integral of closed forms.
+    `shift` moves the mean to mu = z + shift (the box stays put)."""
     from scipy.integrate import quad
     alpha = math.sqrt(2) * sigma / l
     m = np.asarray(wl) - np.asarray(d)
@@ -143,10 +144,10 @@ def slab_single_scatter(d, wl, albedo, sigma=SLAB_SIGMA, l=SLAB_L, irradiance=1.
     p = albedo * D / (4 * sd)
 
     def f(z):
-        u = z / sigma
+        u = (z + shift) / sigma
         rho = math.exp(-0.5 * u * u - 0.5 * math.log(2 * math.pi) - sp.log_ndtr(u)) / sigma
-        tau_c = slab_optical_depth(ztop, z, d, sigma, l)
-        tau_l = slab_optical_depth(z, ztop, wl, sigma, l)
+        tau_c = slab_optical_depth(ztop + shift, z + shift, d, sigma, l)
+        tau_l = slab_optical_depth(z + shift, ztop + shift, wl, sigma, l)
         return math.exp(-tau_c - tau_l) * rho * sd * p * irradiance / abs(d[2])
 
     return quad(f, zbot, ztop, epsabs=0, epsrel=1e-12, limit=400)[0]

@@ -1,0 +1,198 @@
+"""Gradients of the path-replay adjoint (through the C-ABI) against exact
+derivatives, the oracle's finite differences with common random numbers, and
+the GPU forward's own finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_00280_gb300 import gpss
+from paper_2603_00280_gb300 import workloads as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+D45 = np.array([math.cos(math.pi / 4), 0.0, -math.sin(math.pi / 4)])
+WL = np.array([0.0, 0.0, 1.0])
+
+
+def _adjoint_runs(scene_dict, cam, opts, d_image, seeds):
+    """Adjoint estimates (one per seed) of: sum of d_mean, sum of var*d_var... returns dict of arrays."""
+    import torch
+    S = gpss.Scene(scene_dict)
+    obj = scene_dict["objects"][0]
+    shape = obj["mean"].shape
+    ch = obj["albedo"].shape[0]
+    g = torch.as_tensor(d_image, dtype=torch.float32).cuda().contiguous()
+    out = {"mean": [], "var": [], "albedo": [], "l": [], "dm": [], "dv": []}
+    for sd in seeds:
+        dm = torch.zeros(shape, device="cuda")
+        dv = torch.zeros(shape, device="cuda")
+        da = torch.zeros((ch,) + shape, device="cuda")
+        dl = torch.zeros(1, device="cuda")
+        st = gpss.render_adjoint(S, cam, dict(opts, seed=sd), g, dm, dv, da, dl)
+        assert st["paths"] > 0
+        assert st["aborted"] == 0  # every replay reproduced its forward path
+        out["mean"].append(float(dm.double().sum()))
+        out["var"].append(float(dv.double().sum()))
+        out["albedo"].append(float(da.double().sum()))
+        out["l"].append(float(dl[0]))
+        out["dm"].append(dm.cpu().numpy().astype(np.float64))
+        out["dv"].append(dv.cpu().numpy().astype(np.float64))
+    return {k: np.array(v) for k, v in out.items()}
+
+
+def _mean_se(a):
+    a = np.asarray(a, np.float64)
+    return a.mean(axis=0), a.std(axis=0, ddof=1) / math.sqrt(len(a))
+
+
+def test_single_scatter_gradients_are_exact():
+    """max_bounces = 1 on the plane-mean slab: the pixel value is a 1-D integral
+    of closed forms, so its derivatives with respect to a shift of the mean, the
+    variance, the length scale and the albedo are exact."""
+    F = 0.75
+    sc = H.dyadic_slab(albedo=F)
+    cam = W.ortho_camera_45(16, 16, film=0.5)
+    opts = {"spp": 8192, "max_bounces": 1, "mix_R": 0.5}
+    d_image = np.zeros((16, 16, 3))
+    d_image[4:12, 4:12, 0] = 1.0
+    npx = 64
+    res = _adjoint_runs(sc, cam, opts, d_image, seeds=range(1, 33))
+    sig, l = H.SLAB_SIGMA, H.SLAB_L
+    f0 = H.slab_single_scatter(D45, WL, F)
+    h = 1e-5
+    exact = {
+        "mean": (H.slab_single_scatter(D45, WL, F, shift=h) - H.slab_single_scatter(D45, WL, F, shift=-h)) / (2 * h),
+        "var": (H.slab_single_scatter(D45, WL, F, sigma=math.sqrt(sig * sig * (1 + 1e-4)))
+                - H.slab_single_scatter(D45, WL, F, sigma=math.sqrt(sig * sig * (1 - 1e-4)))) / (2e-4 * sig * sig),
+        "l": (H.slab_single_scatter(D45, WL, F, l=l * (1 + 1e-4)) - H.slab_single_scatter(D45, WL, F, l=l * (1 - 1e-4)))
+             / (2e-4 * l),
+        "albedo": f0 / F,
+    }
+    for k, ex in exact.items():
+        m, se = _mean_se(res[k])
+        assert abs(m - npx * ex) < 4 * se + 2e-3 * abs(npx * ex), (k, m, se, npx * ex)
+        # the mean-shift derivative is a small residual of large cancelling flight
+        # terms (per-seed spread ~80% of its value); the others are sharp
+        assert se < (0.3 if k == "mean" else 0.02) * abs(npx * ex), (k, se, npx * ex)
+
+
+def _small_hetero():
+    wl = W.heterogeneous(n=16, width=10, height=10, spp=64, max_bounces=4, length_scale=0.03)
+    return wl
+
+
+def test_gradients_match_oracle_finite_differences():
+    """Multi-bounce heterogeneous scene: the adjoint's d/dl and d/d(block of mean
+    nodes) against central differences of the FP64 oracle with common random
+    numbers (regular tracking makes those differences smooth)."""
+    wl = _small_hetero()
+    sc, cam = wl["scene"], wl["camera"]
+    d_image = np.zeros((10, 10, 3))
+    d_image[..., 0] = 1.0
+    res = _adjoint_runs(sc, cam, dict(wl["opts"], spp=4096), d_image, seeds=range(11, 19))
+    obj = sc["objects"][0]
+    # length scale
+    eps = 0.02
+    op, om = dict(obj), dict(obj)
+    op["length_scale"] = obj["length_scale"] * (1 + eps)
+    om["length_scale"] = obj["length_scale"] * (1 - eps)
+    Sp = oracle.Scene({"objects": [op], "light": sc["light"]})
+    Sm = oracle.Scene({"objects": [om], "light": sc["light"]})
+    ospp = 384
+    s, s2, _ = oracle.render_diff(Sp, Sm, cam, dict(wl["opts"], spp=ospp, seed=5))
+    h = 2 * eps * obj["length_scale"]
+    fd = s[..., 0].sum() / ospp / h
+    fd_se = math.sqrt(max(np.sum(s2[..., 0] / ospp - (s[..., 0] / ospp) ** 2), 0) / ospp) / h
+    m, se = _mean_se(res["l"])
+    assert abs(m - fd) < 4 * math.sqrt(se ** 2 + fd_se ** 2) + 0.02 * abs(fd), ("l", m, se, fd, fd_se)
+    # a block of mean nodes across the shell: nodes (x 8..11, y 4..7, z 6..9)
+    blk = (slice(6, 10), slice(4, 8), slice(8, 12))
+    epsm = 2e-3
+    op, om = dict(obj), dict(obj)
+    op["mean"] = obj["mean"].copy()
+    om["mean"] = obj["mean"].copy()
+    op["mean"][blk] += epsm
+    om["mean"][blk] -= epsm
+    Sp = oracle.Scene({"objects": [op], "light": sc["light"]})
+    Sm = oracle.Scene({"objects": [om], "light": sc["light"]})
+    s, s2, _ = oracle.render_diff(Sp, Sm, cam, dict(wl["opts"], spp=ospp, seed=6))
+    fd = s[..., 0].sum() / ospp / (2 * epsm)
+    fd_se = math.sqrt(max(np.sum(s2[..., 0] / ospp - (s[..., 0] / ospp) ** 2), 0) / ospp) / (2 * epsm)
+    blk_sum = np.array([dm[blk].sum() for dm in res["dm"]])
+    m, se = _mean_se(blk_sum)
+    assert abs(m - fd) < 4 * math.sqrt(se ** 2 + fd_se ** 2) + 0.02 * abs(fd), ("mean block", m, se, fd, fd_se)
+
+
+def test_gradients_match_gpu_finite_differences_with_common_random_numbers():
+    """d/dl and d/d(global variance scale) from the adjoint against central
+    differences of the GPU forward render with the same seeds."""
+    import torch
+    wl = _small_hetero()
+    sc, cam = wl["scene"], wl["camera"]
+    obj = sc["objects"][0]
+    d_image = np.zeros((10, 10, 3))
+    d_image[..., 0] = 1.0
+    seeds = list(range(21, 29))
+    res = _adjoint_runs(sc, cam, dict(wl["opts"], spp=4096), d_image, seeds=seeds)
+    eps = 0.01
+    fds_l, fds_v = [], []
+    for sd in seeds:
+        vals = []
+        for sign in (1, -1):
+            o = dict(obj)
+            o["length_scale"] = obj["length_scale"] * (1 + sign * eps)
+            S = gpss.Scene({"objects": [o], "light": sc["light"]})
+            img, _, _ = gpss.render(S, cam, dict(wl["opts"], spp=4096, seed=sd))
+            vals.append(float(img[..., 0].double().sum()))
+        fds_l.append((vals[0] - vals[1]) / (2 * eps * obj["length_scale"]))
+        vals = []
+        for sign in (1, -1):
+            o = dict(obj)
+            o["var"] = (obj["var"] * (1 + sign * eps)).astype(np.float32)
+            S = gpss.Scene({"objects": [o], "light": sc["light"]})
+            img, _, _ = gpss.render(S, cam, dict(wl["opts"], spp=4096, seed=sd))
+            vals.append(float(img[..., 0].double().sum()))
+        fds_v.append((vals[0] - vals[1]) / (2 * eps))
+    # adjoint of the variance scale: sum_j var_j d/dvar_j
+    adj_v = np.array([(dv * obj["var"]).sum() for dv in res["dv"]])
+    for name, fd, adj in (("l", fds_l, res["l"]), ("var scale", fds_v, adj_v)):
+        a, ase = _mean_se(adj)
+        f, fse = _mean_se(fd)
+        assert abs(a - f) < 4 * math.sqrt(ase ** 2 + fse ** 2) + 0.03 * abs(f), (name, a, ase, f, fse)
+
+
+def test_autograd_function_and_edge_cases():
+    import torch
+    wl = W.heterogeneous(n=16, width=8, height=8, spp=16, max_bounces=3, length_scale=0.03)
+    sc = wl["scene"]
+    obj = sc["objects"][0]
+    S = gpss.Scene(sc)
+    mean = torch.tensor(obj["mean"], device="cuda", requires_grad=True)
+    var = torch.tensor(obj["var"], device="cuda", requires_grad=True)
+    alb = torch.tensor(obj["albedo"], device="cuda", requires_grad=True)
+    l = torch.tensor(obj["length_scale"], device="cuda", requires_grad=True)
+    img = gpss.render_differentiable(S, obj, mean, var, alb, l, wl["camera"], wl["opts"])
+    loss = (img ** 2).sum()
+    loss.backward()
+    for t in (mean, var, alb, l):
+        assert t.grad is not None and torch.isfinite(t.grad).all()
+    assert float(alb.grad.abs().sum()) > 0 and float(l.grad.abs()) > 0
+    # kept radiance is reused: the adjoint after a keep render gives the same gradients as a cold one
+    g = torch.ones((8, 8, 3), device="cuda")
+    outs = []
+    for keep in (True, False):
+        S2 = gpss.Scene(sc)
+        if keep:
+            gpss.render(S2, wl["camera"], wl["opts"], keep_path_radiance=True)
+        dm = torch.zeros(obj["mean"].shape, device="cuda")
+        st = gpss.render_adjoint(S2, wl["camera"], wl["opts"], g, dm)
+        assert st["aborted"] == 0
+        outs.append(dm.cpu().numpy())
+    np.testing.assert_allclose(outs[0], outs[1], rtol=1e-4, atol=1e-6 * np.abs(outs[1]).max())
+    # multi-object scenes are not differentiable here
+    two = {"objects": [obj, obj], "light": sc["light"]}
+    with pytest.raises(gpss.GpssError) as e:
+        gpss.render_adjoint(gpss.Scene(two), wl["camera"], wl["opts"], torch.zeros((8, 8, 3), device="cuda"))
+    assert e.value.status == 5
