@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--image", type=int, default=0, help="override the image side (profiling of small cases)")
     ap.add_argument("--spp", type=int, default=0, help="override samples per pixel (profiling of small cases)")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64, help="scenes of the batched comparison")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="image/grid size scale of the batched scenes")
     return ap.parse_args()
 
 
@@ -231,6 +234,69 @@ def measure_adjoint(args, gpss, torch, flush, rank):
             "replay_mismatches": mism}
 
 
+# ----------------------------------------------------------------- batched launch
+def measure_batched(args, gpss, torch, flush):
+    """The uneven 64-scene batch (images 64^2..512^2, grids 32^3..256^3, spp 4..64):
+    one graph-replayed persistent launch with the autotuned shape against the 64
+    separate gpss_render launches of the same jobs, queued back to back on the same
+    stream.  Both trace identical paths (same indices, same random numbers), so
+    their per-pixel errors are identical."""
+    from paper_2603_00280_gb300 import workloads as W
+    t0 = time.perf_counter()
+    jobs = W.batched(args.batch_count, size_scale=args.batch_scale)
+    gen_s = time.perf_counter() - t0
+    scenes = [gpss.Scene(j["scene"]) for j in jobs]
+    cams = [j["camera"] for j in jobs]
+    opts = [j["opts"] for j in jobs]
+    nodes = sum(o["mean"].size for j in jobs for o in j["scene"]["objects"])
+    del jobs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = gpss.Batch(scenes, cams, opts, block_size=0)
+    tune_s = time.perf_counter() - t0
+    imgs = [torch.empty((c["height"], c["width"], 3), device="cuda") for c in cams]
+    stream = torch.cuda.current_stream()
+
+    def separate():
+        for S, c, o, im in zip(scenes, cams, opts, imgs):
+            gpss.render(S, c, o, image=im, stats=False)
+
+    for _ in range(max(1, args.warmup)):
+        B.render(images=imgs, stats=False)
+        separate()
+    torch.cuda.synchronize()
+    g_ms, s_ms, verts, paths = [], [], 0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st = B.render(images=imgs, stats=True)
+        e1.record(stream)
+        e1.synchronize()
+        g_ms.append(e0.elapsed_time(e1))
+        verts += st["vertices"]
+        paths = st["paths"]
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        separate()
+        e1.record(stream)
+        e1.synchronize()
+        s_ms.append(e0.elapsed_time(e1))
+    cfg = B.config
+    B.close()
+    for S in scenes:
+        S.close()
+    tg, ts = sum(g_ms), sum(s_ms)
+    return {"workload": "batched_%d_uneven" % args.batch_count, "scenes": args.batch_count,
+            "size_scale": args.batch_scale, "paths_per_step": paths, "vertices_per_step": verts // args.steps,
+            "grid_nodes": nodes, "graph_ms": tg / args.steps, "separate_ms": ts / args.steps,
+            "speedup_graph_over_separate": ts / tg, "value_graph": verts / (tg / 1e3) / 1e6,
+            "value_separate": verts / (ts / 1e3) / 1e6, "unit": UNIT, "launch": cfg,
+            "autotune_s": tune_s, "generate_s": gen_s,
+            "equal_error": "identical paths and random numbers in both arms"}
+
+
 # ----------------------------------------------------------------- arms
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -341,6 +407,7 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": H * W * 3 * 4}
 
     adj = None if args.no_adjoint else measure_adjoint(args, gpss, torch, flush, rank)
+    batched = None if (args.no_batched or world > 1) else measure_batched(args, gpss, torch, flush)
 
     if rank != 0:
         if dist:
@@ -357,7 +424,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl, "flushed between steps (256 MB write)"),
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
-           "clocks": clk, "fwd_adjoint": adj,
+           "clocks": clk, "fwd_adjoint": adj, "batched": batched,
            "work": {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
                     "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
                     "majorant_cells_per_step": stats["majorant_cells"],

@@ -179,13 +179,44 @@ gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss
 
 /* ---------------------------------------------------------------- batches */
 
-/* A batch renders n scenes (each with its own camera and options) in one
- * persistent launch captured in a CUDA graph.  Launch shape chosen by the
- * library's autotuner (0 = autotune, else the given block size). */
+/* A batch renders n scenes, each with its own camera and options, in ONE launch
+ * of the persistent path kernel, replayed from a captured CUDA graph.  The paths
+ * of all scenes form one index space (scene i's paths follow scene i-1's, each
+ * scene in gpss_render's order sample*npix + pixel) that the resident threads
+ * consume in chunks through one atomic cursor; each path carries the index of its
+ * scene in a device table of (scene, camera, options, film pointers).  Scene i's
+ * paths and random numbers are exactly those of gpss_render(scenes[i], cams[i],
+ * opts[i]): the images agree with separate renders up to the order of the film's
+ * float additions.  No counterpart in the paper (an execution-model feature).
+ *
+ *   scenes, cams, opts: n entries each (copied; the scenes must stay alive and
+ *     unchanged in layout while the batch exists, and live on the current device;
+ *     a scene may appear several times).  opts[i].flags must be 0.
+ *   n: 1..4096.
+ *   block_size: 0 = autotune: block size (64/128/256 threads) x shading threshold
+ *     x chunk size, each candidate timed on this batch with its spp reduced so
+ *     that one launch traces at most ~8M paths (takes up to a few seconds; the
+ *     scratch films are freed before return).  64, 128 or 256: that block size
+ *     with the default threshold (24) and chunk (256), no tuning.
+ *   stream: the stream tuning runs on (the graph is captured on a private one).
+ * INVALID_ARG on a bad argument, UNSUPPORTED for scenes on another device. */
 gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_camera* cams, const gpss_render_opts* opts,
                               int n, int block_size, gpss_stream stream, gpss_batch* out);
-/* images[i]: device H_i*W_i*3 floats (overwritten). */
-gpss_status gpss_batch_render(gpss_batch b, float* const* images, gpss_stream stream);
+/* Renders the batch on `stream` (one graph launch: counter clear, film clear, the
+ * persistent kernel).  images[i]: device buffer of H_i*W_i*3 floats, overwritten
+ * with the mean radiance.  sqsums: NULL, or n entries each NULL or a device buffer
+ * of H_i*W_i*3 floats receiving the per-pixel sum of squared path radiance.  The
+ * film pointers are written into the device table (one small host-to-device copy)
+ * only when they differ from the previous call's.  stats (host, nullable): sums
+ * over all scenes; stats->ms = device time of the graph launch (synchronises). */
+gpss_status gpss_batch_render(gpss_batch b, float* const* images, float* const* sqsums, gpss_stats* stats,
+                              gpss_stream stream);
+/* The launch shape in use: threads per block, shading threshold (lanes a warp
+ * gathers before shading), chunk (paths per cursor fetch) and grid (blocks).  Any
+ * output may be NULL. */
+gpss_status gpss_batch_config(gpss_batch b, int* block_size, int* shade_min, int* chunk, int* grid);
+/* Waits for the device to finish (graph launches may still be running on the
+ * caller's streams), then frees the batch.  NULL is a no-op. */
 gpss_status gpss_batch_destroy(gpss_batch b);
 
 /* ---------------------------------------------------------------- deterministic evaluators

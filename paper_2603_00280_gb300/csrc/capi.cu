@@ -397,21 +397,3 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
   }
   return GPSS_OK;
 }
-
-// ------------------------------------------------------------------ not yet available
-extern "C" gpss_status gpss_batch_create(const gpss_scene*, const gpss_camera*, const gpss_render_opts*, int, int,
-                                         gpss_stream, gpss_batch* out) {
-  if (out) *out = nullptr;
-  set_error("batches not built");
-  return GPSS_ERR_UNSUPPORTED;
-}
-
-extern "C" gpss_status gpss_batch_render(gpss_batch, float* const*, gpss_stream) {
-  set_error("batches not built");
-  return GPSS_ERR_UNSUPPORTED;
-}
-
-extern "C" gpss_status gpss_batch_destroy(gpss_batch) {
-  set_error("batches not built");
-  return GPSS_ERR_UNSUPPORTED;
-}

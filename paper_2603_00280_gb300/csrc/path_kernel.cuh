@@ -146,323 +146,374 @@ static __device__ __noinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_
   return dl;
 }
 
-template <bool ADJ>
-__global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5) k_path(const SceneDev S, const CameraDev C, const PathArgs P,
-                                                    float* __restrict__ image, float* __restrict__ sqsum,
-                                                    float* __restrict__ path_radiance, float* __restrict__ path_T,
-                                                    unsigned long long* __restrict__ counters, const AdjOut A) {
-  const unsigned FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
-  unsigned long long* cursor = counters + kCntNum;
-  const bool env = S.light.kind != kLightDirectional;
-
-  long long chunk_next = 0, chunk_end = 0;
-  bool exhausted = false;
-
-  bool active = false, waiting = false, begin = false;
-  long long pidx = 0;
-  uint32_t pixel = 0;
+// ---------------------------------------------------------------- per-lane path state
+struct Lane {
+  bool active, waiting, begin, vgrad, cont, walk_ok;
+  long long pidx;
+  uint32_t pixel;
+  int job;
   Rng rng;
-  V3 o{}, d{}, beta{}, L{}, pend{}, d_next{}, beta_next{};
-  float prev_pdf = -1.0f, T = 1.0f, pdf_next = 0.0f;
-  int bounce = 0, mode = kFlight;
-  bool cont = false, walk_ok = false;
-  uint32_t events = 0;
+  V3 o, d, beta, L, pend, d_next, beta_next;
+  float prev_pdf, T, pdf_next;
+  int bounce, mode;
+  uint32_t events;
   Walk w;
   // adjoint state
-  bool vgrad = false;
-  V3 Ltot{}, gpix{}, d_in{};
-  float Tfin = 0.0f, acc_l = 0.0f;
+  V3 Ltot, gpix, d_in;
+  float Tfin;
+};
 
-  uint32_t c_paths = 0, c_vert = 0, c_null = 0, c_shadow = 0, c_cells = 0, c_trunc = 0, c_abort = 0;
+struct LaneCounters {
+  uint32_t paths, vert, null_, shadow, cells, trunc, abort;
+  float acc_l;  // adjoint: length-scale gradient
+};
 
-  for (;;) {
-    // ------------------------------------------------ regeneration (warp-converged)
-    const unsigned need = __ballot_sync(FULL, !active);
-    if (need && !exhausted) {
-      const int n_need = __popc(need);
-      const int rank = __popc(need & ((1u << lane) - 1u));
-      long long avail = chunk_end - chunk_next;
-      long long mine = -1;
-      if (avail >= n_need) {
-        if (!active) mine = chunk_next + rank;
-        chunk_next += n_need;
-      } else {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)kChunk);
-        base = __shfl_sync(FULL, base, 0);
-        if (!active) mine = rank < avail ? chunk_next + rank : (long long)base + (rank - avail);
-        chunk_next = (long long)base + (n_need - avail);
-        chunk_end = (long long)base + kChunk;
-        if ((long long)base >= P.total) exhausted = true;
-      }
-      if (!active && mine >= 0 && mine < P.total) {
-        pidx = mine;
-        const int sample = (int)(mine / P.npix);
-        pixel = (uint32_t)(mine - (long long)sample * P.npix);
-        bool skip = false;
-        if constexpr (ADJ) {
-          gpix = v3(A.d_image[3 * pixel] * P.inv_spp, A.d_image[3 * pixel + 1] * P.inv_spp,
-                    A.d_image[3 * pixel + 2] * P.inv_spp);
-          Ltot = v3(A.L_path[3 * pidx], A.L_path[3 * pidx + 1], A.L_path[3 * pidx + 2]);
-          skip = gpix.x == 0.0f && gpix.y == 0.0f && gpix.z == 0.0f;  // no gradient flows through this pixel
-          vgrad = false;
-        }
-        if (!skip) {
-          rng.init(P.seed, pixel, (uint32_t)sample);
-          rng.start(0, kPurposeCamera);
-          const float jx = rng.next(), jy = rng.next();
-          camera_ray(C, (int)(pixel % (uint32_t)C.width), (int)(pixel / (uint32_t)C.width), jx, jy, o, d);
-          beta = v3(1.0f, 1.0f, 1.0f);
-          L = v3(0.0f, 0.0f, 0.0f);
-          prev_pdf = -1.0f;
-          bounce = 0;
-          mode = kFlight;
-          events = 0;
-          rng.start(0, kPurposeFlight);
-          begin = true;
-          waiting = false;
-          active = true;
-        }
-      }
-    }
-    const unsigned act = __ballot_sync(FULL, active);
-    if (act == 0) {
-      if (exhausted || chunk_next >= P.total) break;
-      continue;
-    }
+__device__ __forceinline__ void lane_init(Lane& s) {
+  s.active = s.waiting = s.begin = s.vgrad = s.cont = s.walk_ok = false;
+  s.pidx = 0;
+  s.pixel = 0;
+  s.job = 0;
+}
 
-    // ------------------------------------------------ deferred shading (and vertex gradients)
-    const unsigned wait_mask = __ballot_sync(FULL, waiting || vgrad);
-    if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act)) {
-      if constexpr (ADJ) {
-        if (vgrad) {
-          vgrad = false;
-          const ObjectDev& ob = S.obj[0];
-          const V3 Ck = v3(pend.x * Tfin, pend.y * Tfin, pend.z * Tfin);
-          const V3 after = Ltot - L - Ck;
-          const V3 F = fetch_albedo(ob, o);
-          const float Wnee = dot(gpix, Ck);
-          const float Wph = cont ? dot(gpix, after) : 0.0f;
-          const V3 ac = v3(F.x > 0.0f ? gpix.x * (Ck.x + (cont ? after.x : 0.0f)) / F.x : 0.0f,
-                           F.y > 0.0f ? gpix.y * (Ck.y + (cont ? after.y : 0.0f)) / F.y : 0.0f,
-                           F.z > 0.0f ? gpix.z * (Ck.z + (cont ? after.z : 0.0f)) / F.z : 0.0f);
-          acc_l += adj_vertex(ob, o, d_in, d, d_next, Wnee, Wph, ac, A);
-          L = L + Ck;
-          if (cont) {
-            mode = kFlight;
-            d = d_next;
-            beta = beta_next;
-            prev_pdf = pdf_next;
-            rng.start((uint32_t)bounce, kPurposeFlight);
-            begin = true;
-          } else {
-            walk_ok = false;  // treated below as an escaped flight that adds nothing
-            mode = kFlight;
-            begin = false;
-            beta = v3(0.0f, 0.0f, 0.0f);
-          }
-        }
-      }
-      if (waiting) {
-        waiting = false;
-        const V3 x = fma3(w.t, d, o);
-        Field f;
-        Local l;
-        int k = 0;
-        if (S.n_objs > 1) {
-          k = choose_object(S, x, d, rng.next(), f, l);
-        } else {
-          f = fetch(S.obj[0], x);
-          l = local_of(S.obj[0], f);
-        }
-        const V3 F = fetch_albedo(S.obj[k], x);
-        o = x;
-        cont = bounce + 1 < P.max_bounces;
-        if (cont) {
-          rng.start((uint32_t)bounce, kPurposePhase);
-          const float u0 = rng.next(), u1 = rng.next(), u2 = rng.next();
-          const PhaseSample ps = phase_sample_call(d, f, l.alpha, P.mix_R, u0, u1, u2);
-          if (ps.ok) {
-            d_next = ps.d2;
-            beta_next = v3(beta.x * F.x * ps.w_over_F, beta.y * F.y * ps.w_over_F, beta.z * F.z * ps.w_over_F);
-            pdf_next = ps.pdf;
-          } else {
-            cont = false;
-          }
-        } else {
-          ++c_trunc;
-        }
-        rng.start((uint32_t)bounce, kPurposeNee);
-        V3 wl, Le;
-        if (!env) {
-          wl = v3(S.light.dir[0], S.light.dir[1], S.light.dir[2]);
-          Le = v3(S.light.radiance[0], S.light.radiance[1], S.light.radiance[2]);
-        } else {
-          const float z = 1.0f - 2.0f * rng.next();
-          const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-          float sp, cp;
-          sincospif(2.0f * rng.next(), &sp, &cp);
-          wl = v3(r * cp, r * sp, z);
-          Le = env_radiance(S.light, wl);
-        }
-        const PhaseEval pe = phase_eval_call(d, wl, f, l.alpha, P.mix_R);
-        const float lw = env ? power_heuristic(kInv4Pi, pe.pdf) * (4.0f * kPi) : 1.0f;
-        const float scale = pe.p_over_F * lw;
-        pend = v3(beta.x * F.x * scale * Le.x, beta.y * F.y * scale * Le.y, beta.z * F.z * scale * Le.z);
-        if constexpr (ADJ) {
-          d_in = d;
-          Tfin = scale > 0.0f ? A.T_path[(size_t)pidx * P.max_bounces + bounce] : 0.0f;
-        } else {
-          if (path_T && !(scale > 0.0f)) path_T[(size_t)pidx * P.max_bounces + bounce] = 0.0f;
-        }
-        ++bounce;
-        if (scale > 0.0f) {
-          mode = kShadow;
-          d = wl;
-          T = 1.0f;
-          begin = true;
-        } else if (ADJ) {
-          d = wl;
-          vgrad = true;  // the vertex's phase-sampling factor still has a gradient
-        } else if (cont) {
-          mode = kFlight;
-          d = d_next;
-          beta = beta_next;
-          prev_pdf = pdf_next;
-          rng.start((uint32_t)bounce, kPurposeFlight);
-          begin = true;
-        } else {
-          // no shadow ray and no continuation: with walk_ok = false and beta = 0 the
-          // step below treats the lane as an escaped flight that adds nothing
-          mode = kFlight;
-          walk_ok = false;
-          begin = false;
-          beta = v3(0.0f, 0.0f, 0.0f);
-        }
-      }
-    }
-    if (!active || waiting || vgrad) continue;
+// Starts path `pidx` (= sample * npix + pixel) of a render; returns false when the
+// adjoint has nothing to do for it (no gradient flows through its pixel).
+template <bool ADJ>
+__device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const PathArgs& P, const AdjOut& A,
+                                           long long pidx) {
+  s.pidx = pidx;
+  const int sample = (int)(pidx / P.npix);
+  s.pixel = (uint32_t)(pidx - (long long)sample * P.npix);
+  if constexpr (ADJ) {
+    s.gpix = v3(A.d_image[3 * s.pixel] * P.inv_spp, A.d_image[3 * s.pixel + 1] * P.inv_spp,
+                A.d_image[3 * s.pixel + 2] * P.inv_spp);
+    s.Ltot = v3(A.L_path[3 * pidx], A.L_path[3 * pidx + 1], A.L_path[3 * pidx + 2]);
+    s.vgrad = false;
+    if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) return false;
+  }
+  s.rng.init(P.seed, s.pixel, (uint32_t)sample);
+  s.rng.start(0, kPurposeCamera);
+  const float jx = s.rng.next(), jy = s.rng.next();
+  camera_ray(C, (int)(s.pixel % (uint32_t)C.width), (int)(s.pixel / (uint32_t)C.width), jx, jy, s.o, s.d);
+  s.beta = v3(1.0f, 1.0f, 1.0f);
+  s.L = v3(0.0f, 0.0f, 0.0f);
+  s.prev_pdf = -1.0f;
+  s.bounce = 0;
+  s.mode = kFlight;
+  s.events = 0;
+  s.rng.start(0, kPurposeFlight);
+  s.begin = true;
+  s.waiting = false;
+  s.active = true;
+  return true;
+}
 
-    // ------------------------------------------------ one tentative collision
-    if (begin) {
-      walk_ok = walk_begin(S.mg, o, d, INFINITY, w);
-      begin = false;
+// Adjoint: the vertex gradient of the last real vertex, then the continuation.
+__device__ __forceinline__ void lane_vertex_grad(Lane& s, const SceneDev& S, const AdjOut& A, LaneCounters& c) {
+  s.vgrad = false;
+  const ObjectDev& ob = S.obj[0];
+  const V3 Ck = v3(s.pend.x * s.Tfin, s.pend.y * s.Tfin, s.pend.z * s.Tfin);
+  const V3 after = s.Ltot - s.L - Ck;
+  const V3 F = fetch_albedo(ob, s.o);
+  const float Wnee = dot(s.gpix, Ck);
+  const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
+  const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
+                   F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
+                   F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
+  c.acc_l += adj_vertex(ob, s.o, s.d_in, s.d, s.d_next, Wnee, Wph, ac, A);
+  s.L = s.L + Ck;
+  if (s.cont) {
+    s.mode = kFlight;
+    s.d = s.d_next;
+    s.beta = s.beta_next;
+    s.prev_pdf = s.pdf_next;
+    s.rng.start((uint32_t)s.bounce, kPurposeFlight);
+    s.begin = true;
+  } else {
+    s.walk_ok = false;  // treated below as an escaped flight that adds nothing
+    s.mode = kFlight;
+    s.begin = false;
+    s.beta = v3(0.0f, 0.0f, 0.0f);
+  }
+}
+
+// Shading of a real vertex: phase sampling, next-event estimation setup.
+template <bool ADJ>
+__device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
+                                           float* __restrict__ path_T, LaneCounters& c) {
+  const bool env = S.light.kind != kLightDirectional;
+  s.waiting = false;
+  const V3 x = fma3(s.w.t, s.d, s.o);
+  Field f;
+  Local l;
+  int k = 0;
+  if (S.n_objs > 1) {
+    k = choose_object(S, x, s.d, s.rng.next(), f, l);
+  } else {
+    f = fetch(S.obj[0], x);
+    l = local_of(S.obj[0], f);
+  }
+  const V3 F = fetch_albedo(S.obj[k], x);
+  s.o = x;
+  s.cont = s.bounce + 1 < P.max_bounces;
+  if (s.cont) {
+    s.rng.start((uint32_t)s.bounce, kPurposePhase);
+    const float u0 = s.rng.next(), u1 = s.rng.next(), u2 = s.rng.next();
+    const PhaseSample ps = phase_sample_call(s.d, f, l.alpha, P.mix_R, u0, u1, u2);
+    if (ps.ok) {
+      s.d_next = ps.d2;
+      s.beta_next = v3(s.beta.x * F.x * ps.w_over_F, s.beta.y * F.y * ps.w_over_F, s.beta.z * F.z * ps.w_over_F);
+      s.pdf_next = ps.pdf;
+    } else {
+      s.cont = false;
     }
-    bool hit = false;
-    if (walk_ok) hit = walk_advance(S.mg, o, d, w, -__logf(rng.next()), c_cells);
-    bool finish = false;
-    if (hit) {
-      ++events;
-      const V3 x = fma3(w.t, d, o);
-      float st;
-      DSig ds;
-      bool inobj = false;
-      if constexpr (ADJ) {
-        // extinction and its partials from one evaluation (the decision uses the same value)
-        inobj = inside(S.obj[0], x);
-        st = 0.0f;
-        if (inobj) {
-          const Field f = fetch(S.obj[0], x);
-          ds = dsigma_t(S.obj[0], f, d);
-          st = ds.st;
-        }
-      } else {
-        st = sigma_t_at(S, x, d);
-      }
-      if (mode == kFlight) {
-        const bool real = rng.next() * w.sbar < st;
-        if constexpr (ADJ) {
-          const float W = dot(gpix, Ltot - L);
-          if (W != 0.0f && inobj)
-            acc_l += adj_scatter_event(S.obj[0], x, ds, real ? W / st : -W / (w.sbar - st), A.d_mean, A.d_var);
-        }
-        if (real) {
-          ++c_vert;
-          waiting = true;  // real scattering vertex: shaded with the warp's other waiting lanes
-        } else {
-          ++c_null;
-        }
-      } else {
-        ++c_shadow;
-        if constexpr (ADJ) {
-          const float Wn = dot(gpix, pend) * Tfin;
-          if (Wn != 0.0f && inobj)
-            acc_l += adj_scatter_event(S.obj[0], x, ds, -Wn / (w.sbar - st), A.d_mean, A.d_var);
-        }
-        if (!ratio_step(T, st, w.sbar, rng)) walk_ok = false;  // T = 0: the shadow ray ends here
-      }
-      if (events >= kMaxEventsPerPath) {
-        ++c_abort;
-        finish = true;
-        waiting = false;
+  } else {
+    ++c.trunc;
+  }
+  s.rng.start((uint32_t)s.bounce, kPurposeNee);
+  V3 wl, Le;
+  if (!env) {
+    wl = v3(S.light.dir[0], S.light.dir[1], S.light.dir[2]);
+    Le = v3(S.light.radiance[0], S.light.radiance[1], S.light.radiance[2]);
+  } else {
+    const float z = 1.0f - 2.0f * s.rng.next();
+    const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincospif(2.0f * s.rng.next(), &sp, &cp);
+    wl = v3(r * cp, r * sp, z);
+    Le = env_radiance(S.light, wl);
+  }
+  const PhaseEval pe = phase_eval_call(s.d, wl, f, l.alpha, P.mix_R);
+  const float lw = env ? power_heuristic(kInv4Pi, pe.pdf) * (4.0f * kPi) : 1.0f;
+  const float scale = pe.p_over_F * lw;
+  s.pend = v3(s.beta.x * F.x * scale * Le.x, s.beta.y * F.y * scale * Le.y, s.beta.z * F.z * scale * Le.z);
+  if constexpr (ADJ) {
+    s.d_in = s.d;
+    s.Tfin = scale > 0.0f ? A.T_path[(size_t)s.pidx * P.max_bounces + s.bounce] : 0.0f;
+  } else {
+    if (path_T && !(scale > 0.0f)) path_T[(size_t)s.pidx * P.max_bounces + s.bounce] = 0.0f;
+  }
+  ++s.bounce;
+  if (scale > 0.0f) {
+    s.mode = kShadow;
+    s.d = wl;
+    s.T = 1.0f;
+    s.begin = true;
+  } else if (ADJ) {
+    s.d = wl;
+    s.vgrad = true;  // the vertex's phase-sampling factor still has a gradient
+  } else if (s.cont) {
+    s.mode = kFlight;
+    s.d = s.d_next;
+    s.beta = s.beta_next;
+    s.prev_pdf = s.pdf_next;
+    s.rng.start((uint32_t)s.bounce, kPurposeFlight);
+    s.begin = true;
+  } else {
+    // no shadow ray and no continuation: with walk_ok = false and beta = 0 the
+    // step treats the lane as an escaped flight that adds nothing
+    s.mode = kFlight;
+    s.walk_ok = false;
+    s.begin = false;
+    s.beta = v3(0.0f, 0.0f, 0.0f);
+  }
+}
+
+// One tentative collision of the lane's current ray; returns true when the path ends.
+template <bool ADJ>
+__device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
+                                          float* __restrict__ path_T, LaneCounters& c) {
+  const bool env = S.light.kind != kLightDirectional;
+  if (s.begin) {
+    s.walk_ok = walk_begin(S.mg, s.o, s.d, INFINITY, s.w);
+    s.begin = false;
+  }
+  bool hit = false;
+  if (s.walk_ok) hit = walk_advance(S.mg, s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
+  bool finish = false;
+  if (hit) {
+    ++s.events;
+    const V3 x = fma3(s.w.t, s.d, s.o);
+    float st;
+    DSig ds;
+    bool inobj = false;
+    if constexpr (ADJ) {
+      // extinction and its partials from one evaluation (the decision uses the same value)
+      inobj = inside(S.obj[0], x);
+      st = 0.0f;
+      if (inobj) {
+        const Field f = fetch(S.obj[0], x);
+        ds = dsigma_t(S.obj[0], f, s.d);
+        st = ds.st;
       }
     } else {
-      if (mode == kFlight) {
-        if (env) {
-          const V3 Le = env_radiance(S.light, d);
-          const float wm = prev_pdf < 0.0f ? 1.0f : power_heuristic(prev_pdf, kInv4Pi);
-          L = v3(fmaf(beta.x * Le.x, wm, L.x), fmaf(beta.y * Le.y, wm, L.y), fmaf(beta.z * Le.z, wm, L.z));
-        }
+      st = sigma_t_at(S, x, s.d);
+    }
+    if (s.mode == kFlight) {
+      const bool real = s.rng.next() * s.w.sbar < st;
+      if constexpr (ADJ) {
+        const float W = dot(s.gpix, s.Ltot - s.L);
+        if (W != 0.0f && inobj)
+          c.acc_l += adj_scatter_event(S.obj[0], x, ds, real ? W / st : -W / (s.w.sbar - st), A.d_mean, A.d_var);
+      }
+      if (real) {
+        ++c.vert;
+        s.waiting = true;  // real scattering vertex: shaded with the warp's other waiting lanes
+      } else {
+        ++c.null_;
+      }
+    } else {
+      ++c.shadow;
+      if constexpr (ADJ) {
+        const float Wn = dot(s.gpix, s.pend) * s.Tfin;
+        if (Wn != 0.0f && inobj)
+          c.acc_l += adj_scatter_event(S.obj[0], x, ds, -Wn / (s.w.sbar - st), A.d_mean, A.d_var);
+      }
+      if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;  // T = 0: the shadow ray ends here
+    }
+    if (s.events >= kMaxEventsPerPath) {
+      ++c.abort;
+      finish = true;
+      s.waiting = false;
+    }
+  } else {
+    if (s.mode == kFlight) {
+      if (env) {
+        const V3 Le = env_radiance(S.light, s.d);
+        const float wm = s.prev_pdf < 0.0f ? 1.0f : power_heuristic(s.prev_pdf, kInv4Pi);
+        s.L = v3(fmaf(s.beta.x * Le.x, wm, s.L.x), fmaf(s.beta.y * Le.y, wm, s.L.y), fmaf(s.beta.z * Le.z, wm, s.L.z));
+      }
+      finish = true;
+    } else if (ADJ) {
+      s.vgrad = true;  // shadow ray done: the vertex gradient is due
+    } else {
+      s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
+      if (path_T) path_T[(size_t)s.pidx * P.max_bounces + (s.bounce - 1)] = s.T;
+      if (s.cont) {
+        s.mode = kFlight;
+        s.d = s.d_next;
+        s.beta = s.beta_next;
+        s.prev_pdf = s.pdf_next;
+        s.rng.start((uint32_t)s.bounce, kPurposeFlight);
+        s.begin = true;
+      } else {
         finish = true;
-      } else if (ADJ) {
-        vgrad = true;  // shadow ray done: the vertex gradient is due
-      } else {
-        L = v3(fmaf(pend.x, T, L.x), fmaf(pend.y, T, L.y), fmaf(pend.z, T, L.z));
-        if (path_T) path_T[(size_t)pidx * P.max_bounces + (bounce - 1)] = T;
-        if (cont) {
-          mode = kFlight;
-          d = d_next;
-          beta = beta_next;
-          prev_pdf = pdf_next;
-          rng.start((uint32_t)bounce, kPurposeFlight);
-          begin = true;
-        } else {
-          finish = true;
-        }
       }
-    }
-    if (finish) {
-      if constexpr (!ADJ) {
-        float* px = image + 3 * (size_t)pixel;
-        atomicAdd(px + 0, L.x * P.inv_spp);
-        atomicAdd(px + 1, L.y * P.inv_spp);
-        atomicAdd(px + 2, L.z * P.inv_spp);
-        if (sqsum) {
-          float* q = sqsum + 3 * (size_t)pixel;
-          atomicAdd(q + 0, L.x * L.x);
-          atomicAdd(q + 1, L.y * L.y);
-          atomicAdd(q + 2, L.z * L.z);
-        }
-        if (path_radiance) {
-          float* pr = path_radiance + 3 * pidx;
-          pr[0] = L.x;
-          pr[1] = L.y;
-          pr[2] = L.z;
-        }
-      } else {
-        // the replay must reproduce the forward path; count any that does not
-        const V3 e = L - Ltot;
-        const float tol = 1e-3f * (fabsf(Ltot.x) + fabsf(Ltot.y) + fabsf(Ltot.z)) + 1e-6f;
-        if (fabsf(e.x) + fabsf(e.y) + fabsf(e.z) > tol) ++c_abort;
-      }
-      ++c_paths;
-      active = false;
     }
   }
+  return finish;
+}
 
-  // ------------------------------------------------ counters: warp reduce, one atomic per warp
-  if constexpr (ADJ) {
-    for (int off = 16; off > 0; off >>= 1) acc_l += __shfl_down_sync(FULL, acc_l, off);
-    if (lane == 0 && A.d_l && acc_l != 0.0f) atomicAdd(A.d_l, acc_l);
+// Film accumulation (forward) or the replay check (adjoint) of a finished path.
+template <bool ADJ>
+__device__ __forceinline__ void lane_finish(Lane& s, const PathArgs& P, float* __restrict__ image,
+                                            float* __restrict__ sqsum, float* __restrict__ path_radiance,
+                                            LaneCounters& c) {
+  if constexpr (!ADJ) {
+    float* px = image + 3 * (size_t)s.pixel;
+    atomicAdd(px + 0, s.L.x * P.inv_spp);
+    atomicAdd(px + 1, s.L.y * P.inv_spp);
+    atomicAdd(px + 2, s.L.z * P.inv_spp);
+    if (sqsum) {
+      float* q = sqsum + 3 * (size_t)s.pixel;
+      atomicAdd(q + 0, s.L.x * s.L.x);
+      atomicAdd(q + 1, s.L.y * s.L.y);
+      atomicAdd(q + 2, s.L.z * s.L.z);
+    }
+    if (path_radiance) {
+      float* pr = path_radiance + 3 * s.pidx;
+      pr[0] = s.L.x;
+      pr[1] = s.L.y;
+      pr[2] = s.L.z;
+    }
+  } else {
+    // the replay must reproduce the forward path; count any that does not
+    const V3 e = s.L - s.Ltot;
+    const float tol = 1e-3f * (fabsf(s.Ltot.x) + fabsf(s.Ltot.y) + fabsf(s.Ltot.z)) + 1e-6f;
+    if (fabsf(e.x) + fabsf(e.y) + fabsf(e.z) > tol) ++c.abort;
   }
-  uint32_t vals[7] = {c_paths, c_vert, c_null, c_shadow, c_cells, c_trunc, c_abort};
+  ++c.paths;
+  s.active = false;
+}
+
+// Warp-converged chunked work distribution: lanes without a path take the next
+// indices of the warp's chunk of the global cursor (one atomic per `chunk`).
+struct WarpCursor {
+  long long next, end;
+  bool exhausted;
+};
+
+__device__ __forceinline__ long long warp_take(WarpCursor& wc, bool want, unsigned need, int lane,
+                                               unsigned long long* cursor, long long total, int chunk) {
+  const int n_need = __popc(need);
+  const int rank = __popc(need & ((1u << lane) - 1u));
+  const long long avail = wc.end - wc.next;
+  long long mine = -1;
+  if (avail >= n_need) {
+    if (want) mine = wc.next + rank;
+    wc.next += n_need;
+  } else {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)chunk);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (want) mine = rank < avail ? wc.next + rank : (long long)base + (rank - avail);
+    wc.next = (long long)base + (n_need - avail);
+    wc.end = (long long)base + chunk;
+    if ((long long)base >= total) wc.exhausted = true;
+  }
+  return mine;
+}
+
+__device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned long long* counters, float* d_l) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  if (d_l) {
+    float a = c.acc_l;
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(FULL, a, off);
+    if (lane == 0 && a != 0.0f) atomicAdd(d_l, a);
+  }
+  const uint32_t vals[7] = {c.paths, c.vert, c.null_, c.shadow, c.cells, c.trunc, c.abort};
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     unsigned long long v = vals[i];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
     if (lane == 0 && v) atomicAdd(counters + i, v);
   }
+}
+
+// ---------------------------------------------------------------- single-render kernel
+template <bool ADJ>
+__global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
+    k_path(const __grid_constant__ SceneDev S, const __grid_constant__ CameraDev C, const __grid_constant__ PathArgs P,
+           float* __restrict__ image, float* __restrict__ sqsum, float* __restrict__ path_radiance,
+           float* __restrict__ path_T, unsigned long long* __restrict__ counters, const __grid_constant__ AdjOut A) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  WarpCursor wc{0, 0, false};
+  Lane s;
+  lane_init(s);
+  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0.0f};
+  for (;;) {
+    const unsigned need = __ballot_sync(FULL, !s.active);
+    if (need && !wc.exhausted) {
+      const long long mine = warp_take(wc, !s.active, need, lane, counters + kCntNum, P.total, kChunk);
+      if (!s.active && mine >= 0 && mine < P.total) lane_start<ADJ>(s, C, P, A, mine);
+    }
+    const unsigned act = __ballot_sync(FULL, s.active);
+    if (act == 0) {
+      if (wc.exhausted || wc.next >= P.total) break;
+      continue;
+    }
+    const unsigned wait_mask = __ballot_sync(FULL, s.waiting || s.vgrad);
+    if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act)) {
+      if constexpr (ADJ) {
+        if (s.vgrad) lane_vertex_grad(s, S, A, c);
+      }
+      if (s.waiting) lane_shade<ADJ>(s, S, P, A, path_T, c);
+    }
+    if (!s.active || s.waiting || s.vgrad) continue;
+    if (lane_step<ADJ>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
+  }
+  flush_counters(c, counters, ADJ ? A.d_l : nullptr);
 }
 
 }  // namespace gpss

@@ -78,7 +78,8 @@ _SIGS = {
                             ctypes.POINTER(Stats), _VP],
     "gpss_batch_create": [ctypes.POINTER(_VP), ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _I, _I, _VP,
                           ctypes.POINTER(_VP)],
-    "gpss_batch_render": [_VP, ctypes.POINTER(_VP), _VP],
+    "gpss_batch_render": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(Stats), _VP],
+    "gpss_batch_config": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "gpss_batch_destroy": [_VP],
     "gpss_eval_sigma_t": [_VP, _I, _VP, _VP, _VP, _VP],
     "gpss_eval_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP],
@@ -292,6 +293,65 @@ def render_adjoint(scene: Scene, camera: dict, opts: dict, d_image, d_mean=None,
           _ptr(d_variance), _ptr(d_albedo), _ptr(d_length_scale), ctypes.byref(st) if st is not None else None,
           _stream(stream))
     return st.as_dict() if st is not None else None
+
+
+class Batch:
+    """Many (scene, camera, options) jobs rendered by one graph-replayed persistent
+    launch (gpss_batch_*).  block_size 0 autotunes the launch shape at creation."""
+
+    def __init__(self, scenes, cameras, opts, block_size: int = 0, stream=None):
+        n = len(scenes)
+        if not (len(cameras) == n and len(opts) == n):
+            raise ValueError("scenes, cameras and opts must have the same length")
+        self.scenes = list(scenes)  # keeps the scenes alive as long as the batch
+        self.shapes = [(int(c["height"]), int(c["width"]), 3) for c in cameras]
+        sh = (_VP * n)(*[sc.handle for sc in self.scenes])
+        cams = (Camera * n)(*[camera_desc(c) for c in cameras])
+        ops = (RenderOpts * n)(*[render_opts(o) for o in opts])
+        h = _VP()
+        _call("gpss_batch_create", sh, cams, ops, n, int(block_size), _stream(stream), ctypes.byref(h))
+        self.handle = h
+
+    @property
+    def config(self):
+        b, s, c, g = _I(), _I(), _I(), _I()
+        _call("gpss_batch_config", self.handle, ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(g))
+        return {"block_size": b.value, "shade_min": s.value, "chunk": c.value, "grid": g.value}
+
+    def render(self, images=None, sqsums=None, want_sqsum=False, stats=True, stream=None):
+        """Renders every job.  images / sqsums: lists of CUDA tensors (H, W, 3) or None
+        (allocated here).  Returns (images, sqsums or None, stats dict or None)."""
+        torch = _torch()
+        n = len(self.shapes)
+        if images is None:
+            images = [torch.empty(sh, device="cuda", dtype=torch.float32) for sh in self.shapes]
+        if sqsums is None and want_sqsum:
+            sqsums = [torch.empty(sh, device="cuda", dtype=torch.float32) for sh in self.shapes]
+        for i, im in enumerate(images):
+            if tuple(im.shape) != self.shapes[i] or not im.is_cuda or im.dtype != torch.float32:
+                raise ValueError("image %d must be a float32 CUDA tensor of shape %s" % (i, self.shapes[i]))
+        ip = (_VP * n)(*[im.data_ptr() for im in images])
+        sp = (_VP * n)(*[(q.data_ptr() if q is not None else None) for q in sqsums]) if sqsums is not None else None
+        st = Stats() if stats else None
+        _call("gpss_batch_render", self.handle, ip, sp, ctypes.byref(st) if st is not None else None, _stream(stream))
+        return images, sqsums, (st.as_dict() if st is not None else None)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _call("gpss_batch_destroy", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def _dev(x):

@@ -42,8 +42,7 @@ def value_noise(points: np.ndarray, seed: int, freqs=(8, 16, 32), amps=(1.0, 0.5
     p = np.asarray(points, dtype=np.float64)
     out = np.zeros(p.shape[:-1])
     for octave, (f, a) in enumerate(zip(freqs, amps)):
-        n = int(math.ceil(3.0 * f)) + 3
-        lat = 2.0 * np.random.default_rng([seed, octave]).random((n, n, n)) - 1.0
+        n, lat = _lattice(seed, octave, f)
         g = (p - _NOISE_LO) * f
         i = np.clip(np.floor(g).astype(np.int64), 0, n - 2)
         w = np.clip(g - i, 0.0, 1.0)
@@ -55,6 +54,36 @@ def value_noise(points: np.ndarray, seed: int, freqs=(8, 16, 32), amps=(1.0, 0.5
                   * (w[..., 2] if cz else 1 - w[..., 2]))
             acc += wt * lat[i[..., 0] + cx, i[..., 1] + cy, i[..., 2] + cz]
         out += a * acc
+    return out / float(sum(amps))
+
+
+def _lattice(seed: int, octave: int, f: float):
+    n = int(math.ceil(3.0 * f)) + 3
+    return n, 2.0 * np.random.default_rng([seed, octave]).random((n, n, n)) - 1.0
+
+
+def value_noise_grid(bmin, bmax, n, seed: int, freqs=(8, 16, 32), amps=(1.0, 0.5, 0.25)) -> np.ndarray:
+    """``value_noise`` at the nodes of a node-centred grid (``node_coords``), shape
+    (nz, ny, nx).  The interpolation weights factor per axis, so each octave is
+    three one-dimensional interpolations of the lattice (x, then y, then z) instead
+    of eight corner lookups per node; the values equal ``value_noise`` up to the
+    order of the floating-point additions."""
+    axes = [np.linspace(bmin[a], bmax[a], n[a]) for a in range(3)]
+    out = np.zeros((n[2], n[1], n[0]))
+    for octave, (f, a) in enumerate(zip(freqs, amps)):
+        m, lat = _lattice(seed, octave, f)
+        idx, wts = [], []
+        for c in axes:
+            g = (c - _NOISE_LO) * f
+            i = np.clip(np.floor(g).astype(np.int64), 0, m - 2)
+            w = np.clip(g - i, 0.0, 1.0)
+            idx.append(i)
+            wts.append(w * w * (3.0 - 2.0 * w))
+        (ix, iy, iz), (wx, wy, wz) = idx, wts
+        A = (1 - wx)[:, None, None] * lat[ix] + wx[:, None, None] * lat[ix + 1]                    # (nx, m, m)
+        B = (1 - wy)[None, :, None] * A[:, iy, :] + wy[None, :, None] * A[:, iy + 1, :]            # (nx, ny, m)
+        C = (1 - wz)[None, None, :] * B[:, :, iz] + wz[None, None, :] * B[:, :, iz + 1]            # (nx, ny, nz)
+        out += a * C.transpose(2, 1, 0)
     return out / float(sum(amps))
 
 
@@ -150,7 +179,7 @@ def heterogeneous(n=128, width=512, height=512, spp=64, max_bounces=32, seed=0, 
     perspective camera, procedural sky."""
     bmin, bmax = (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5)
     p = node_coords(bmin, bmax, (n, n, n))
-    mean = sdf_sphere(p, (0.0, 0.0, 0.0), 0.3) + 0.02 * value_noise(p, noise_seed)
+    mean = sdf_sphere(p, (0.0, 0.0, 0.0), 0.3) + 0.02 * value_noise_grid(bmin, bmax, (n, n, n), noise_seed)
     var = 1e-4 + (0.01 - 1e-4) * (p[..., 0] + 0.5)
     obj = make_object(mean, var, albedo, bmin, bmax, length_scale)
     return {"name": "heterogeneous_%d" % n,
@@ -198,11 +227,11 @@ def differentiable(n=64, width=256, height=256, spp=64, max_bounces=32, seed=123
     0.6, l = 0.012)."""
     bmin, bmax = (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5)
     p = node_coords(bmin, bmax, (n, n, n))
-    mean = sdf_sphere(p, (0.0, 0.0, 0.0), 0.3) + 0.02 * value_noise(p, 1)
+    mean = sdf_sphere(p, (0.0, 0.0, 0.0), 0.3) + 0.02 * value_noise_grid(bmin, bmax, (n, n, n), 1)
     var = 1e-4 + (0.01 - 1e-4) * (p[..., 0] + 0.5)
     albedo, l = 0.8, 0.01
     if start:
-        mean = mean + 0.01 * value_noise(p, 2)
+        mean = mean + 0.01 * value_noise_grid(bmin, bmax, (n, n, n), 2)
         var = 2.0 * var
         albedo, l = 0.6, 0.012
     obj = make_object(mean, var, albedo, bmin, bmax, l)
@@ -233,7 +262,7 @@ def batched_scene(s: int, size_scale: float = 1.0):
         mean = p[..., 2] - rng.uniform(-0.2, 0.2)
     else:
         mean = sdf_box(p, (0, 0, 0), (rng.uniform(0.15, 0.3),) * 3)
-    mean = mean + 0.02 * value_noise(p, 100 + s)
+    mean = mean + 0.02 * value_noise_grid(bmin, bmax, (n, n, n), 100 + s)
     var = 1e-6 * (5e4) ** rng.random()
     obj = make_object(mean, var, 0.8, bmin, bmax, 0.01)
     return {"name": "batched_%02d" % s,

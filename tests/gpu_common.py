@@ -91,3 +91,17 @@ def check_image_parity(gm, gse, om, ose, frac4=0.01, block=4):
     out["total_z"] = float((gm.sum() - om.sum()) / np.sqrt(np.sum(gse ** 2) + np.sum(ose ** 2)))
     ok = out["frac_z4"] <= frac4 and out["block_frac_z3"] <= 0.03 and abs(out["total_z"]) < 4
     return ok, out
+
+
+def two_spheres_rgb():
+    """Two overlapping GPSS spheres on their own dyadic grids, RGB albedo: the
+    extinctions add and the scattering object is chosen by extinction."""
+    objs = []
+    rng = np.random.default_rng(4)
+    for c, r, v, lo, hi in [((-0.1, 0, 0), 0.25, 4e-3, (-0.5, -0.375, -0.375), (0.25, 0.375, 0.375)),
+                            ((0.15, 0.05, 0), 0.2, 1e-2, (-0.125, -0.25, -0.25), (0.5, 0.375, 0.375))]:
+        n = (int(round((hi[0] - lo[0]) * 32)) + 1, int(round((hi[1] - lo[1]) * 32)) + 1, int(round((hi[2] - lo[2]) * 32)) + 1)
+        p = W.node_coords(lo, hi, n)
+        alb = rng.uniform(0.3, 0.95, size=(3, n[2], n[1], n[0])).astype(np.float32)
+        objs.append(W.make_object(W.sdf_sphere(p, c, r), v, alb, lo, hi, 0.05))
+    return {"objects": objs, "light": W.sky_light()}

@@ -88,3 +88,20 @@ def test_option_validation_messages():
                                 "width": 4, "height": 4})
         assert L.gpss_render(ctypes.c_void_p(8), ctypes.byref(cam), ctypes.byref(o), ctypes.c_void_p(8), None,
                              None, None) == 1
+
+
+def test_batch_calls_reject_bad_arguments_on_the_host():
+    L = gpss.load()
+    h = ctypes.c_void_p(7)
+    cam = (gpss.Camera * 1)()
+    opts = (gpss.RenderOpts * 1)()
+    scenes = (ctypes.c_void_p * 1)(None)
+    assert L.gpss_batch_create(scenes, cam, opts, 0, 0, None, ctypes.byref(h)) == 1      # empty batch
+    assert not h.value
+    assert L.gpss_batch_create(scenes, cam, opts, 5000, 0, None, ctypes.byref(h)) == 1   # too many jobs
+    assert L.gpss_batch_create(scenes, cam, opts, 1, 96, None, ctypes.byref(h)) == 1     # no such block size
+    assert L.gpss_batch_create(None, cam, opts, 1, 0, None, ctypes.byref(h)) == 1
+    assert L.gpss_batch_create(scenes, cam, opts, 1, 0, None, None) == 1
+    assert L.gpss_batch_render(None, None, None, None, None) == 1
+    assert L.gpss_batch_config(None, None, None, None, None) == 1
+    assert L.gpss_batch_destroy(None) == 0

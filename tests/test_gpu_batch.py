@@ -1,0 +1,168 @@
+"""Batched persistent launch (gpss_batch_*).  Each job of a batch traces exactly
+the paths of the separate gpss_render call with the same scene, camera and
+options (same path indices, same random numbers), so its image equals the
+separate render up to the order of the film's float additions, whatever the
+launch shape; per-pixel standard-error maps then agree as well."""
+import numpy as np
+import pytest
+
+from paper_2603_00280_gb300 import gpss
+from paper_2603_00280_gb300 import workloads as W
+from tests import gpu_common as C
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+# film sums of <= 64 terms per pixel in another order: a few float32 ulps of the sum
+ATOL, RTOL = 1e-6, 2e-5
+
+
+def _jobs(count=6, scale=0.125, bounces=8):
+    js = W.batched(count, size_scale=scale)
+    for j in js:
+        j["opts"]["max_bounces"] = bounces
+    return js
+
+
+def _mixed_jobs():
+    """Jobs that differ in every per-job input: lights, object counts, albedo
+    channels, camera kinds, image sizes, spp, bounce limits and seeds."""
+    js = _jobs(4)
+    ts = W.tiny_slab(width=24, height=20, spp=8, max_bounces=6, seed=5)
+    js.append({"scene": ts["scene"], "camera": ts["camera"], "opts": ts["opts"]})
+    js.append({"scene": C.two_spheres_rgb(), "camera": W.perspective_camera(16, 12, eye=(0.0, -1.6, 0.6)),
+               "opts": {"spp": 12, "max_bounces": 5, "seed": 77, "mix_R": 0.5}})
+    js.append({"scene": H.dyadic_slab(albedo=1.0, mean=0.0625, light=W.uniform_light(1.0)),
+               "camera": W.ortho_camera_45(8, 8, film=0.5), "opts": {"spp": 33, "max_bounces": 40, "seed": 9}})
+    return js
+
+
+def _separate(scenes, js):
+    imgs, sqs, stats = [], [], []
+    for S, j in zip(scenes, js):
+        img, sq, st = gpss.render(S, j["camera"], j["opts"], want_sqsum=True)
+        imgs.append(img.cpu().numpy())
+        sqs.append(sq.cpu().numpy())
+        stats.append(st)
+    return imgs, sqs, stats
+
+
+def _assert_equal_images(a, b, what):
+    for i, (x, y) in enumerate(zip(a, b)):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        bad = np.abs(x - y) > ATOL + RTOL * np.maximum(np.abs(x), np.abs(y))
+        assert not bad.any(), (what, i, float(np.abs(x - y).max()), int(bad.sum()))
+
+
+def _sum_stats(stats):
+    keys = ("paths", "vertices", "null_collisions", "shadow_steps", "majorant_cells", "truncated", "aborted")
+    return {k: sum(s[k] for s in stats) for k in keys}
+
+
+@pytest.mark.parametrize("block", [64, 128, 256])
+def test_batch_equals_separate_renders(block):
+    js = _jobs()
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    ref_img, ref_sq, ref_st = _separate(scenes, js)
+    with gpss.Batch(scenes, [j["camera"] for j in js], [j["opts"] for j in js], block_size=block) as B:
+        cfg = B.config
+        assert cfg["block_size"] == block and cfg["grid"] > 0
+        imgs, sqs, st = B.render(want_sqsum=True)
+        _assert_equal_images([x.cpu().numpy() for x in imgs], ref_img, "image")
+        _assert_equal_images([x.cpu().numpy() for x in sqs], ref_sq, "sqsum")
+        want = _sum_stats(ref_st)
+        for k, v in want.items():
+            assert st[k] == v, (k, st[k], v)
+        assert st["paths"] == sum(j["camera"]["width"] * j["camera"]["height"] * j["opts"]["spp"] for j in js)
+
+
+def test_batch_mixed_jobs_and_repeated_scene():
+    js = _mixed_jobs()
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    # the same scene twice, with another seed and camera
+    js.append({"scene": None, "camera": W.perspective_camera(16, 16), "opts": dict(js[0]["opts"], seed=4242)})
+    scenes.append(scenes[0])
+    ref_img, ref_sq, ref_st = _separate(scenes, js)
+    with gpss.Batch(scenes, [j["camera"] for j in js], [j["opts"] for j in js], block_size=128) as B:
+        imgs, sqs, st = B.render(want_sqsum=True)
+        _assert_equal_images([x.cpu().numpy() for x in imgs], ref_img, "image")
+        _assert_equal_images([x.cpu().numpy() for x in sqs], ref_sq, "sqsum")
+        assert st["paths"] == _sum_stats(ref_st)["paths"] and st["aborted"] == 0
+
+
+def test_batch_rebinds_films_and_replays():
+    """New output buffers on the second call (table rewrite), no sqsum films, then
+    a third call into the first buffers: every call renders the same images."""
+    import torch
+    js = _jobs(5)
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    ref_img, _, _ = _separate(scenes, js)
+    with gpss.Batch(scenes, [j["camera"] for j in js], [j["opts"] for j in js], block_size=128) as B:
+        first, _, _ = B.render(want_sqsum=True)
+        second = [torch.full_like(x, 123.0) for x in first]
+        B.render(images=second, stats=False)
+        torch.cuda.synchronize()
+        _assert_equal_images([x.cpu().numpy() for x in second], ref_img, "second")
+        for x in first:
+            x.fill_(-7.0)
+        B.render(images=first, stats=False)
+        torch.cuda.synchronize()
+        _assert_equal_images([x.cpu().numpy() for x in first], ref_img, "third")
+
+
+def test_batch_on_side_stream():
+    import torch
+    js = _jobs(4)
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    ref_img, _, _ = _separate(scenes, js)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with gpss.Batch(scenes, [j["camera"] for j in js], [j["opts"] for j in js], block_size=64) as B:
+            imgs, _, _ = B.render(stats=False)
+            s.synchronize()
+            _assert_equal_images([x.cpu().numpy() for x in imgs], ref_img, "side stream")
+
+
+def test_batch_autotune_and_se_maps():
+    """Autotuned shape from the candidate sets; the batch's per-pixel standard
+    errors agree with those of separate renders (the equal-error condition of the
+    batch-vs-separate comparison)."""
+    js = _jobs(6, scale=0.25)
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    ref_img, ref_sq, _ = _separate(scenes, js)
+    with gpss.Batch(scenes, [j["camera"] for j in js], [j["opts"] for j in js], block_size=0) as B:
+        cfg = B.config
+        assert cfg["block_size"] in (64, 128, 256)
+        assert cfg["shade_min"] in (8, 16, 24, 32)
+        assert cfg["chunk"] in (64, 128, 256, 512, 1024)
+        imgs, sqs, _ = B.render(want_sqsum=True)
+    for j, m, q, rm, rq in zip(js, imgs, sqs, ref_img, ref_sq):
+        spp = j["opts"]["spp"]
+        m = m.cpu().numpy().astype(np.float64)
+        q = q.cpu().numpy().astype(np.float64)
+        se = np.sqrt(np.maximum(q / spp - m * m, 0) / spp)
+        rse = np.sqrt(np.maximum(rq / spp - rm.astype(np.float64) ** 2, 0) / spp)
+        big = rse > 1e-4 * max(float(rse.max()), 1e-30)
+        if big.any():
+            assert np.median(np.abs(se[big] - rse[big]) / rse[big]) < 0.10
+
+
+def test_batch_rejects_bad_jobs():
+    js = _jobs(2)
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    cams = [j["camera"] for j in js]
+    with pytest.raises(gpss.GpssError):
+        gpss.Batch(scenes, cams, [dict(j["opts"], spp=0) for j in js], block_size=128)
+    with pytest.raises(gpss.GpssError):
+        gpss.Batch(scenes, cams, [j["opts"] for j in js], block_size=96)
+    # flags are not accepted in a batch
+    L = gpss.load()
+    import ctypes
+    n = 2
+    sh = (ctypes.c_void_p * n)(*[s.handle for s in scenes])
+    cs = (gpss.Camera * n)(*[gpss.camera_desc(c) for c in cams])
+    os_ = (gpss.RenderOpts * n)(*[gpss.render_opts(j["opts"], gpss.FLAG_KEEP_PATH_RADIANCE) for j in js])
+    h = ctypes.c_void_p()
+    assert L.gpss_batch_create(sh, cs, os_, n, 128, None, ctypes.byref(h)) == 1
+    assert not h.value

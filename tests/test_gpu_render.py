@@ -77,22 +77,8 @@ def test_heterogeneous_image_parity(brick):
     _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=64, gpu_spp=2048, brick=brick)
 
 
-def two_spheres_rgb():
-    """Two overlapping GPSS spheres on their own dyadic grids, RGB albedo: the
-    extinctions add and the scattering object is chosen by extinction."""
-    objs = []
-    rng = np.random.default_rng(4)
-    for c, r, v, lo, hi in [((-0.1, 0, 0), 0.25, 4e-3, (-0.5, -0.375, -0.375), (0.25, 0.375, 0.375)),
-                            ((0.15, 0.05, 0), 0.2, 1e-2, (-0.125, -0.25, -0.25), (0.5, 0.375, 0.375))]:
-        n = (int(round((hi[0] - lo[0]) * 32)) + 1, int(round((hi[1] - lo[1]) * 32)) + 1, int(round((hi[2] - lo[2]) * 32)) + 1)
-        p = W.node_coords(lo, hi, n)
-        alb = rng.uniform(0.3, 0.95, size=(3, n[2], n[1], n[0])).astype(np.float32)
-        objs.append(W.make_object(W.sdf_sphere(p, c, r), v, alb, lo, hi, 0.05))
-    return {"objects": objs, "light": W.sky_light()}
-
-
 def test_rgb_albedo_and_multiple_objects_parity():
-    sc = two_spheres_rgb()
+    sc = C.two_spheres_rgb()
     cam = W.perspective_camera(20, 20, eye=(0.0, -1.6, 0.6))
     _parity(sc, cam, {"spp": 16, "max_bounces": 8, "mix_R": 0.5}, orc_spp=48, gpu_spp=2048)
 
