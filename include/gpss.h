@@ -130,6 +130,17 @@ gpss_status gpss_scene_set_traversal(gpss_scene s, int skip_levels, float kappa,
  * real scattering vertex once at least `shade_min` (1..32) of them wait, or no
  * other lane can advance.  Default 24.  Results do not depend on it. */
 gpss_status gpss_scene_set_schedule(gpss_scene s, int shade_min);
+/* Local majorants for thin shells (single-object scenes; ignored otherwise): in a
+ * majorant cell whose grid majorant times the rest of the ray's segment in the
+ * cell exceeds `hot` expected tentative collisions, the traversal bounds sigma_t
+ * over shorter pieces computed from the field cell at the piece's start: along
+ * the ray the trilinear mean falls at most at a rate B fixed by the cell's edge
+ * differences, so sigma_t <= rho_ub(mu(x) - B l) (B + alpha/(2 sqrt(pi))) over a
+ * piece of length l (gpss_eval_local_majorant returns these bounds).  This keeps
+ * delta/ratio tracking near a surface-like shell (sigma much smaller than the
+ * grid spacing) at a few tentative collisions per crossing.  hot >= 0, 0
+ * disables; default 4.  Every choice is unbiased. */
+gpss_status gpss_scene_set_local_majorant(gpss_scene s, float hot);
 /* Frees the scene.  Call after the stream's work on it has completed. */
 gpss_status gpss_scene_destroy(gpss_scene s);
 /* Majorant grid geometry: dims[3] cells and their values (device copy, may be NULL). */
@@ -222,6 +233,13 @@ gpss_status gpss_batch_destroy(gpss_batch b);
 /* ---------------------------------------------------------------- deterministic evaluators
  * Per-query kernels used by the parity tests; all arrays are device memory. */
 
+/* The local majorant that the traversal uses on a ray piece starting at
+ * org + t0 dir (object 0; see gpss_scene_set_local_majorant): t_end[i] (piece end,
+ * at most t_max[i]; t_end <= t0 when the start is outside the object's box) and
+ * sbar[i], an upper bound of sigma_t on [t0, t_end].  All arrays device, n
+ * entries (org3, dir3: n*3; dir unit length). */
+gpss_status gpss_eval_local_majorant(gpss_scene s, int n, const float* org3, const float* dir3, const float* t0,
+                                     const float* t_max, float* t_end, float* sbar, gpss_stream stream);
 /* sigma_t(x, d) summed over objects (Eq. generalized_sigma_t); pos3, dir3: n*3. */
 gpss_status gpss_eval_sigma_t(gpss_scene s, int n, const float* pos3, const float* dir3, float* out,
                               gpss_stream stream);

@@ -17,6 +17,15 @@ __global__ void k_eval_sigma_t(const SceneDev S, int n, const float* pos, const 
   out[i] = scene_sigma_t(S, ld3(pos, i), ld3(dir, i));
 }
 
+__global__ void k_eval_local_majorant(const SceneDev S, int n, const float* org, const float* dir, const float* t0,
+                                      const float* tmax, float* t_end, float* sbar) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 pc = local_majorant(S.obj[0], ld3(org, i), ld3(dir, i), t0[i], tmax[i]);
+  t_end[i] = pc.x;
+  sbar[i] = pc.y;
+}
+
 __global__ void k_eval_phase(const SceneDev S, int k, int n, const float* pos, const float* din, const float* dout,
                              float R, float* p3, float* pdf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -190,7 +199,7 @@ __global__ void k_estimate_tr(const SceneDev S, int n, const float* org, const f
     Walk w;
     float T = 1.0f;
     if (walk_begin(S.mg, o, d, tmax[i], w)) {
-      while (walk_advance(S.mg, o, d, w, -__logf(rng.next()), cells)) {
+      while (walk_advance(S.mg, S.obj[0], o, d, w, -__logf(rng.next()), cells)) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
         if (!ratio_step(T, st, w.sbar, rng)) break;
@@ -215,7 +224,7 @@ __global__ void k_free_flight(const SceneDev S, int n, const float* org, const f
     Walk w;
     float t_hit = INFINITY;
     if (walk_begin(S.mg, o, d, INFINITY, w)) {
-      while (walk_advance(S.mg, o, d, w, -__logf(rng.next()), cells)) {
+      while (walk_advance(S.mg, S.obj[0], o, d, w, -__logf(rng.next()), cells)) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
         if (rng.next() * w.sbar < st) {
@@ -259,6 +268,16 @@ extern "C" gpss_status gpss_eval_sigma_t(gpss_scene s, int n, const float* pos3,
   k_eval_sigma_t<<<nb(n), 128, 0, (cudaStream_t)stream>>>(scene_dev(s), n, pos3, dir3, out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GPSS_OK : cuda_fail(e, "eval_sigma_t");
+}
+
+extern "C" gpss_status gpss_eval_local_majorant(gpss_scene s, int n, const float* org3, const float* dir3,
+                                                const float* t0, const float* t_max, float* t_end, float* sbar,
+                                                gpss_stream stream) {
+  if (!s || !org3 || !dir3 || !t0 || !t_max || !t_end || !sbar) { set_error("null argument"); return GPSS_ERR_INVALID_ARG; }
+  CHECK_N(n);
+  k_eval_local_majorant<<<nb(n), 128, 0, (cudaStream_t)stream>>>(scene_dev(s), n, org3, dir3, t0, t_max, t_end, sbar);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GPSS_OK : cuda_fail(e, "eval_local_majorant");
 }
 
 extern "C" gpss_status gpss_eval_phase(gpss_scene s, int object, int n, const float* pos3, const float* d_in3,

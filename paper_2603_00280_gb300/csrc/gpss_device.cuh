@@ -62,6 +62,11 @@ struct MajorantDev {
   int dims[3];             // cells per axis
   const float* maj;        // per-cell majorant
   const float2* skip;      // per-cell (M_r, r)
+  // Local majorants (single-object scenes; 0 = off): where the cell's majorant
+  // times the rest of the ray's segment in the cell exceeds `hot` (expected
+  // tentative collisions), the walk bounds sigma_t over shorter pieces from the
+  // field at the piece's start (local_majorant).
+  float hot;
 };
 
 enum LightKind : int { kLightDirectional = 0, kLightSky = 1, kLightUniform = 2 };
@@ -585,6 +590,79 @@ __device__ __forceinline__ float power_heuristic(float a, float b) {
   return a2 / (a2 + b2);
 }
 
+// ---------------------------------------------------------------- local majorant
+// Upper bound of sigma_t along the ray piece [t, t_end] that starts at x = o + t d,
+// from the 8 corners of the field cell of `ob` containing x (the piece ends at
+// that cell's exit at the latest).  In the cell the mean is trilinear, so:
+//   - each gradient component d_a * dmu/dx_a is a bilinear blend of the cell's
+//     4 edge differences along a, hence -d.grad mu <= B = sum_a max over those
+//     edges of (-d_a * diff_a / h_a), and along the piece mu >= mu(x) - B (t'-t);
+//   - the variance lies between the corner minimum and maximum;
+//   - sigma(d) = E[max(0, -d.g)] <= max(0, -d.grad mu) + E[max(0, -d.(g - grad mu))]
+//     = max(0, -d.grad mu) + alpha/(2 sqrt(pi)) (Eq. generalized_lambda with the
+//     slope distribution of the gradient);
+// with rho bounded as for the grid majorant (lambda decreasing).  The piece length
+// follows the distance to the shell: l = (mu(x) - 2 sigma_hi)/B, at least
+// sigma_lo/B, so a ray approaching a thin shell takes a few pieces with about one
+// tentative collision each instead of (cell size / sigma)^2 null collisions.  The
+// bound depends on x only (not on the piece's random numbers), so delta and ratio
+// tracking stay unbiased.  Returns (t_end, majorant), or t_end <= t when x is not
+// inside the object's box (the caller then keeps the cell majorant).
+static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, V3 d, float t, float t_max) {
+  const V3 x = fma3(t, d, o);
+  if (!inside(ob, x)) return make_float2(t, 0.0f);
+  const float xx[3] = {x.x, x.y, x.z}, dd[3] = {d.x, d.y, d.z};
+  float f[3];
+  int ii[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f[a] = (xx[a] - ob.bmin[a]) * ob.inv_h[a];
+    ii[a] = min(max((int)floorf(f[a]), 0), ob.n[a] - 2);
+  }
+  const int sy = ob.n[0], sz = ob.n[0] * ob.n[1];
+  const int b = ii[0] + sy * ii[1] + sz * ii[2];
+  float2 c[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c[k] = __ldg(ob.mv + b + (k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz);
+  const float wx = fminf(fmaxf(f[0] - (float)ii[0], 0.0f), 1.0f);
+  const float wy = fminf(fmaxf(f[1] - (float)ii[1], 0.0f), 1.0f);
+  const float wz = fminf(fmaxf(f[2] - (float)ii[2], 0.0f), 1.0f);
+  const float mu = lerpf(lerpf(lerpf(c[0].x, c[1].x, wx), lerpf(c[2].x, c[3].x, wx), wy),
+                         lerpf(lerpf(c[4].x, c[5].x, wx), lerpf(c[6].x, c[7].x, wx), wy), wz);
+  float v_lo = c[0].y, v_hi = c[0].y;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    v_lo = fminf(v_lo, c[k].y);
+    v_hi = fmaxf(v_hi, c[k].y);
+  }
+  // directional decrease-rate bound B (edges along x: corner pairs k, k+1; y: k, k+2; z: k, k+4)
+  float ex = -INFINITY, ey = -INFINITY, ez = -INFINITY;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!(k & 1)) ex = fmaxf(ex, -d.x * (c[k + 1].x - c[k].x));
+    if (!(k & 2)) ey = fmaxf(ey, -d.y * (c[k + 2].x - c[k].x));
+    if (!(k & 4)) ez = fmaxf(ez, -d.z * (c[k + 4].x - c[k].x));
+  }
+  const float B = fmaxf(0.0f, ex * ob.inv_h[0] + ey * ob.inv_h[1] + ez * ob.inv_h[2]);
+  // exit of the field cell
+  float l_max = t_max - t;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (dd[a] == 0.0f) continue;
+    const float frac = dd[a] > 0.0f ? (float)(ii[a] + 1) - f[a] : f[a] - (float)ii[a];
+    l_max = fminf(l_max, fmaxf(frac, 0.0f) / (fabsf(dd[a]) * ob.inv_h[a]));
+  }
+  const float s_lo = sqrtf(v_lo), s_hi = sqrtf(v_hi);
+  float l = l_max;
+  if (B > 0.0f) l = fminf(fmaxf((mu - 2.0f * s_hi) / B, s_lo / B), l_max);
+  float mu_b = mu - B * l;
+  mu_b -= 1e-6f * (fabsf(mu) + B * l) + 1e-7f * s_lo;  // rounding of mu and of the piece's end
+  const float u = mu_b >= 0.0f ? mu_b / s_hi : mu_b / s_lo;
+  const float rho_ub = inv_mills(u) / s_lo;
+  const float sbar = rho_ub * (B + s_hi * ob.alpha_scale * (0.5f * kInvSqrtPi)) * 1.001f;
+  return make_float2(t + l, sbar);
+}
+
 // ---------------------------------------------------------------- majorant traversal
 // Majorant traversal consuming an optical-depth budget tau: advances to the next
 // tentative collision (returns true, w.t and w.sbar set) or to the end of the ray
@@ -638,9 +716,11 @@ __device__ __forceinline__ float slab_exit(float lo, float hi, float o, float in
   return ((dcomp > 0.0f ? hi : lo) - o) * inv;
 }
 
-__device__ __forceinline__ bool walk_advance(const MajorantDev& g, V3 o, V3 d, Walk& w, float tau, uint32_t& steps) {
-  // Each step moves the cell index strictly past the face the ray left by; the
-  // cap only guards against non-finite input (the ray then counts as leaving).
+__device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectDev& lob, V3 o, V3 d, Walk& w, float tau,
+                                             uint32_t& steps) {
+  // Each step moves the cell index strictly past the face the ray left by (or, in
+  // a local piece, t strictly forward); the cap only guards against non-finite
+  // input (the ray then counts as leaving).
   for (int guard = 0; guard < (1 << 22); ++guard) {
     const float2 sk = __ldg(g.skip + w.cx + g.dims[0] * (w.cy + g.dims[1] * w.cz));
     const int r = (int)sk.y;
@@ -651,15 +731,24 @@ __device__ __forceinline__ bool walk_advance(const MajorantDev& g, V3 o, V3 d, W
     const float ey = slab_exit(g.gmin[1] + (float)ly * g.cell[1], g.gmin[1] + (float)(hy + 1) * g.cell[1], o.y, w.idy, d.y);
     const float ez = slab_exit(g.gmin[2] + (float)lz * g.cell[2], g.gmin[2] + (float)(hz + 1) * g.cell[2], o.z, w.idz, d.z);
     const float seg_end = fminf(fminf(ex, ey), fminf(ez, w.t_end));
-    const float need = sk.x * (seg_end - w.t);
+    float piece_end = seg_end, sbar = sk.x;
+    if (g.hot > 0.0f && sk.x * (seg_end - w.t) > g.hot) {
+      const float2 pc = local_majorant(lob, o, d, w.t, seg_end);
+      if (pc.x > w.t && pc.y < sk.x) {
+        piece_end = fminf(pc.x, seg_end);
+        sbar = pc.y;
+      }
+    }
+    const float need = sbar * (piece_end - w.t);
     ++steps;
     if (tau < need) {
-      w.t += tau / sk.x;
-      w.sbar = sk.x;
+      w.t += tau / sbar;
+      w.sbar = sbar;
       return true;
     }
     tau -= fmaxf(need, 0.0f);
-    w.t = fmaxf(w.t, seg_end);
+    w.t = fmaxf(w.t, piece_end);
+    if (piece_end < seg_end) continue;  // next piece in the same cell
     if (seg_end >= w.t_end) return false;
     // step to the cell beyond the exit face; after a cube jump the other axes are
     // re-derived from the exit point (rounding there only yields empty segments)

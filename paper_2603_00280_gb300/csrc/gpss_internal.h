@@ -47,6 +47,7 @@ struct gpss_scene_s {
   int skip_levels = 5;             // radii 1, 2, ..., 2^(levels-1)
   float kappa = 0.5f;              // expected majorant depth allowed per skip
   int shade_min = 24;              // lanes a warp gathers before shading real vertices
+  float hot = 4.0f;                // local-majorant threshold (0 = off; single-object scenes)
   int brick = 1;                   // majorant cell = brick x finest field cell
   // scratch owned by the scene
   unsigned long long* counters = nullptr;   // kCntNum u64 + work cursor

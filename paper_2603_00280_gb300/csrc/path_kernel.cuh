@@ -328,7 +328,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
     s.begin = false;
   }
   bool hit = false;
-  if (s.walk_ok) hit = walk_advance(S.mg, s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
+  if (s.walk_ok) hit = walk_advance(S.mg, S.obj[0], s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
   bool finish = false;
   if (hit) {
     ++s.events;

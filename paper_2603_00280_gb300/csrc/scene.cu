@@ -200,6 +200,7 @@ SceneDev scene_dev(const gpss_scene_s* s) {
   d.mg = s->mg;
   d.mg.maj = s->maj;
   d.mg.skip = s->skip;
+  d.mg.hot = s->n_objs == 1 ? s->hot : 0.0f;
   d.light = s->light;
   return d;
 }

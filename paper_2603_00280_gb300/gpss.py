@@ -71,6 +71,7 @@ _SIGS = {
     "gpss_scene_destroy": [_VP],
     "gpss_scene_set_traversal": [_VP, _I, _F, _VP],
     "gpss_scene_set_schedule": [_VP, _I],
+    "gpss_scene_set_local_majorant": [_VP, _F],
     "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
     "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
     "gpss_render_noalloc": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, ctypes.POINTER(Stats), _VP],
@@ -82,6 +83,7 @@ _SIGS = {
     "gpss_batch_config": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "gpss_batch_destroy": [_VP],
     "gpss_eval_sigma_t": [_VP, _I, _VP, _VP, _VP, _VP],
+    "gpss_eval_local_majorant": [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "gpss_eval_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP],
     "gpss_sample_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP],
     "gpss_eval_ndf": [_I, _VP, _F, _F, _F, _F, _VP, _VP],
@@ -237,6 +239,9 @@ class Scene:
     def set_schedule(self, shade_min: int = 24):
         _call("gpss_scene_set_schedule", self.handle, int(shade_min))
 
+    def set_local_majorant(self, hot: float = 4.0):
+        _call("gpss_scene_set_local_majorant", self.handle, float(hot))
+
     def set_traversal(self, skip_levels: int = 5, kappa: float = 0.5, stream=None):
         _call("gpss_scene_set_traversal", self.handle, int(skip_levels), float(kappa), _stream(stream))
 
@@ -366,6 +371,17 @@ def eval_sigma_t(scene: Scene, pos, dirs, stream=None):
     out = torch.empty(len(pos), device="cuda", dtype=torch.float32)
     _call("gpss_eval_sigma_t", scene.handle, len(pos), _ptr(pos), _ptr(dirs), _ptr(out), _stream(stream))
     return out
+
+
+def eval_local_majorant(scene: Scene, org, dirs, t0, tmax, stream=None):
+    """(t_end, sbar) of the local majorant piece starting at org + t0 dir."""
+    torch = _torch()
+    org, dirs, t0, tmax = _dev(org), _dev(dirs), _dev(t0), _dev(tmax)
+    t_end = torch.empty(len(org), device="cuda")
+    sbar = torch.empty(len(org), device="cuda")
+    _call("gpss_eval_local_majorant", scene.handle, len(org), _ptr(org), _ptr(dirs), _ptr(t0), _ptr(tmax),
+          _ptr(t_end), _ptr(sbar), _stream(stream))
+    return t_end, sbar
 
 
 def eval_phase(scene: Scene, k: int, pos, d_in, d_out, mix_R=0.5, stream=None):

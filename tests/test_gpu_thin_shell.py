@@ -1,0 +1,186 @@
+"""Surface-like GPSS shells (sigma much smaller than the grid spacing) and the
+local majorants of the traversal: the local bound holds along every piece, and
+ratio tracking, free-flight sampling and images stay unbiased (against the FP64
+oracle and against the grid-majorant traversal), with far fewer null collisions."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_00280_gb300 import gpss
+from paper_2603_00280_gb300 import workloads as W
+from tests import gpu_common as C
+
+pytestmark = pytest.mark.gpu
+
+BMIN, BMAX = (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5)
+
+
+def thin_scene(shape="plane", n=17, var=2.0 ** -20, l=0.01, light=None, albedo=0.8):
+    """sigma = 2^-10 on a grid of spacing 1/16 (h/sigma = 64): a noisy plane
+    z = 0.03 or a noisy sphere of radius 0.3."""
+    p = W.node_coords(BMIN, BMAX, (n, n, n))
+    if shape == "plane":
+        mean = p[..., 2] - 0.03
+    else:
+        mean = W.sdf_sphere(p, (0.0, 0.0, 0.0), 0.3)
+    mean = mean + 0.02 * W.value_noise_grid(BMIN, BMAX, (n, n, n), 11)
+    obj = W.make_object(mean, var, albedo, BMIN, BMAX, l)
+    return {"objects": [obj], "light": light or W.sky_light()}
+
+
+@pytest.fixture(scope="module")
+def plane():
+    sc = thin_scene("plane")
+    return sc, gpss.Scene(sc), oracle.Scene(sc)
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    sc = thin_scene("sphere", n=33, var=2.0 ** -18)
+    return sc, gpss.Scene(sc), oracle.Scene(sc)
+
+
+def _pieces_hold(G, o, d, t0, tmax, k=97):
+    """sigma_t <= sbar at k points of each piece [t0, t_end] (ends included)."""
+    te, sb = gpss.eval_local_majorant(G, o, d, t0, tmax)
+    te, sb = te.cpu().numpy(), sb.cpu().numpy()
+    n = len(o)
+    s = np.linspace(0.0, 1.0, k)
+    t = t0[:, None] + (np.maximum(te, t0) - t0)[:, None] * s[None, :]
+    pos = (o[:, None, :] + t[..., None] * d[:, None, :]).reshape(-1, 3).astype(np.float32)
+    dirs = np.repeat(d, k, axis=0).astype(np.float32)
+    st = gpss.eval_sigma_t(G, pos, dirs).cpu().numpy().reshape(n, k)
+    ok = te > t0
+    viol = (st > sb[:, None]) & ok[:, None]
+    return te, sb, st, ok, viol
+
+
+@pytest.mark.parametrize("which", ["plane", "sphere"])
+def test_local_majorant_bounds_sigma_t(which, request):
+    sc, G, _ = request.getfixturevalue(which)
+    n = 4096
+    rng = np.random.default_rng(3)
+    o = rng.uniform(-0.49, 0.49, size=(n, 3)).astype(np.float32)
+    if which == "plane":
+        o[:, 2] = rng.uniform(-0.1, 0.15, size=n)  # near the shell
+    d = C.unit_dirs(n, 4)
+    d[: n // 4, 2] *= 0.02  # grazing rays
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t0 = np.zeros(n, np.float32)
+    tmax = np.full(n, 2.0, np.float32)
+    te, sb, st, ok, viol = _pieces_hold(G, o, d, t0, tmax)
+    assert ok.mean() > 0.99
+    assert not viol.any(), (int(viol.sum()), float((st / sb[:, None])[viol].max()))
+    # pieces are short near the shell and long away from it
+    assert np.median(te[ok]) > 1e-3
+
+
+def test_local_majorant_along_approaching_rays(plane):
+    """Chains of pieces as the traversal takes them (t0 <- t_end) on rays that
+    run into the shell at steep and grazing angles: every piece bounds sigma_t,
+    and each chain leaves the box or reaches the dense inside (sigma_t > 1e4,
+    where a real collision is certain) within a few hundred pieces."""
+    sc, G, _ = plane
+    n = 512
+    rng = np.random.default_rng(5)
+    o = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.4, 0.4, n), np.full(n, 0.3)], 1).astype(np.float32)
+    ang = rng.uniform(0.02, 1.5, n)  # angle below the horizon
+    phi = rng.uniform(0, 2 * math.pi, n)
+    d = np.stack([np.cos(ang) * np.cos(phi), np.cos(ang) * np.sin(phi), -np.sin(ang)], 1).astype(np.float32)
+    t0 = np.zeros(n, np.float32)
+    tmax = np.full(n, 3.0, np.float32)
+    alive = np.ones(n, bool)
+    pieces = np.zeros(n, int)
+    for it in range(400):
+        idx = np.nonzero(alive)[0]
+        if len(idx) == 0:
+            break
+        te, sb, st, ok, viol = _pieces_hold(G, o[idx], d[idx], t0[idx], tmax[idx], k=33)
+        assert not viol.any(), (it, int(viol.sum()))
+        x = o[idx] + te[:, None] * d[idx]
+        in_box = np.all(np.abs(x) < 0.5, axis=1)
+        pieces[idx] += 1
+        t0[idx] = np.where(ok, te, t0[idx])
+        alive[idx] = ok & in_box & (te < tmax[idx]) & (st[:, -1] < 1e4)
+    assert not alive.any(), int(alive.sum())
+    assert np.median(pieces) < 60, np.median(pieces)
+
+
+def test_thin_shell_ratio_tracking_unbiased(plane):
+    sc, G, O = plane
+    n = 48
+    rng = np.random.default_rng(8)
+    o = np.stack([rng.uniform(-0.35, 0.35, n), rng.uniform(-0.35, 0.35, n), np.full(n, 0.25)], 1).astype(np.float32)
+    ang = np.concatenate([rng.uniform(0.05, 0.3, n // 2), rng.uniform(0.3, 1.4, n - n // 2)])
+    phi = rng.uniform(0, 2 * math.pi, n)
+    d = np.stack([np.cos(ang) * np.cos(phi), np.cos(ang) * np.sin(phi), -np.sin(ang)], 1).astype(np.float32)
+    # stop where the shell is crossed in part: the transmittance then lies inside (0, 1)
+    tmax = np.zeros(n, np.float32)
+    for i in range(n):
+        lo, hi = 0.0, 3.0
+        for _ in range(40):
+            mid = 0.5 * (lo + hi)
+            tr = oracle.transmittance(O, o[i].astype(np.float64), d[i].astype(np.float64), mid)
+            lo, hi = (mid, hi) if tr > 0.5 else (lo, mid)
+        tmax[i] = lo
+    ref = np.array([oracle.transmittance(O, o[i].astype(np.float64), d[i].astype(np.float64), float(tmax[i]))
+                    for i in range(n)])
+    N = 40000
+    for hot in (4.0, 0.0):
+        G.set_local_majorant(hot)
+        m = gpss.estimate_transmittance(G, o, d, tmax, N, seed=11).cpu().numpy().astype(np.float64)
+        se = np.sqrt(np.maximum(ref * (1 - ref), 1e-4) / N)
+        z = (m - ref) / se
+        assert np.mean(np.abs(z) > 4) < 0.05, (hot, z)
+        assert abs(np.sum(m - ref)) < 4 * np.sqrt(np.sum(se ** 2)), hot
+    G.set_local_majorant(4.0)
+
+
+def test_thin_shell_free_flight_distribution(sphere):
+    """P(t_hit <= s) = 1 - Tr(s) for a ray entering the thin sphere obliquely."""
+    sc, G, O = sphere
+    o = np.array([[-0.45, -0.2, 0.35]], np.float32)
+    tgt = np.array([0.0, 0.0, 0.0])
+    d = (tgt - o[0]) / np.linalg.norm(tgt - o[0])
+    d = d.astype(np.float32)[None]
+    n = 200000
+    t = gpss.sample_free_flight(G, o, d, n, seed=5).cpu().numpy()[0]
+    ts = np.quantile(t[np.isfinite(t)], [0.05, 0.2, 0.5, 0.8, 0.95])
+    for s in ts:
+        p = float(np.mean(t <= s))
+        ref = 1 - oracle.transmittance(O, o[0].astype(np.float64), d[0].astype(np.float64), float(s))
+        assert abs(p - ref) < 5 * math.sqrt(max(ref * (1 - ref), 1e-8) / n) + 1e-4, (s, p, ref)
+
+
+def _img(G, cam, opts):
+    img, sq, st = gpss.render(G, cam, opts, want_sqsum=True)
+    return img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64), st
+
+
+def test_thin_shell_images_local_vs_grid_majorant(plane):
+    sc, G, _ = plane
+    cam = W.perspective_camera(24, 24)
+    spp = 2048
+    G.set_local_majorant(4.0)
+    a, asq, sa = _img(G, cam, {"spp": spp, "max_bounces": 8, "seed": 21})
+    G.set_local_majorant(0.0)
+    b, bsq, sb_ = _img(G, cam, {"spp": spp, "max_bounces": 8, "seed": 22})
+    G.set_local_majorant(4.0)
+    z, gm, om, gse, ose = C.image_z(a, asq, spp, b * spp, bsq, spp)
+    ok, info = C.check_image_parity(gm, gse, om, ose)
+    assert ok, info
+    assert sa["null_collisions"] < 0.2 * sb_["null_collisions"], (sa["null_collisions"], sb_["null_collisions"])
+    assert sa["aborted"] == 0 and sb_["aborted"] == 0
+
+
+def test_thin_shell_image_parity_oracle(plane):
+    sc, G, O = plane
+    cam = W.perspective_camera(8, 8)
+    opts = {"max_bounces": 4, "mix_R": 0.5}
+    img, sq, st = _img(G, cam, dict(opts, spp=8192, seed=31))
+    s, s2, ost = oracle.render(O, cam, dict(opts, spp=32, seed=32))
+    z, gm, om, gse, ose = C.image_z(img, sq, 8192, s, s2, 32)
+    ok, info = C.check_image_parity(gm, gse, om, ose)
+    assert ok, info
