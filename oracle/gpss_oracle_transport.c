@@ -171,9 +171,28 @@ double orc_optical_depth(const orc_scene* s, const double o[3], const double d[3
   return tau;
 }
 
-/* Eq. sm2tr */
+/* Eq. sm2tr.  exp(-tau) is exactly 0 in double precision once tau > 745.2, so
+ * the integration stops when a low-order estimate of the optical depth so far
+ * exceeds 1e4 (far beyond any error of that estimate): the value returned is the
+ * same, and shadow rays into the dense interior of a surface-like shell do not
+ * integrate the whole interior. */
 double orc_transmittance(const orc_scene* s, const double o[3], const double d[3], double tmax) {
-  return exp(-orc_optical_depth(s, o, d, tmax));
+  double* pc = NULL;
+  int n = build_pieces(s, o, d, 0.0, tmax, &pc);
+  ray_ctx c = {s, o, d};
+  double rough = 0.0;
+  for (int i = 0; i < n; ++i) {
+    rough += orc_integrate_rough(sigt_along, &c, pc[2 * i], pc[2 * i + 1]);
+    if (rough > 1e4) {
+      free(pc);
+      return 0.0;
+    }
+  }
+  double tol = (1e-13 * fabs(rough) + 1e-16) / (n > 0 ? n : 1);
+  double tau = 0.0;
+  for (int i = 0; i < n; ++i) tau += orc_integrate(sigt_along, &c, pc[2 * i], pc[2 * i + 1], tol);
+  free(pc);
+  return exp(-tau);
 }
 
 /* Regular tracking: the distance t with tau(t) = target, if it lies before

@@ -109,9 +109,16 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   A.d_l = d_length_scale;
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true>, kPathBlock, 0);
+  const SceneDev S = scene_dev(s);
+  if (S.mg.hot > 0.0f)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, true>, kPathBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, false>, kPathBlock, 0);
   const int agrid = sms * (per_sm > 0 ? per_sm : 1);
-  k_path<true><<<agrid, kPathBlock, 0, cs>>>(scene_dev(s), C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+  if (S.mg.hot > 0.0f)
+    k_path<true, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+  else
+    k_path<true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   if (stats) {

@@ -19,9 +19,10 @@
 //
 // Autotuner.  Candidates: block size (64/128/256 threads; grid = SMs x resident
 // blocks), shading threshold (lanes a warp gathers before shading real vertices)
-// and chunk (paths per cursor fetch).  Coordinate descent from (128, 24, 256):
-// each candidate is timed (best of two, CUDA events) on a copy of the batch whose
-// spp is reduced so that one launch traces at most kTunePaths paths.
+// and chunk (paths per cursor fetch).  Coordinate descent from (128, 24, 256),
+// one axis after the other: each candidate is timed (CUDA events) on a copy of
+// the batch whose spp is reduced so that one launch traces about kTunePaths
+// paths, within a total budget of kTuneBudgetMs.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -39,7 +40,8 @@ struct JobDev {
 };
 
 constexpr int kBatchMaxJobs = 4096;
-constexpr long long kTunePaths = 1ll << 23;
+constexpr long long kTunePaths = 1ll << 22;     // paths per tuning launch (at most, roughly)
+constexpr float kTuneBudgetMs = 5000.0f;         // tuning stops once its launches took this long
 constexpr int kBatchDefaultShade = 24;
 constexpr int kBatchDefaultChunk = 256;
 
@@ -56,7 +58,7 @@ __device__ __forceinline__ int find_job(const long long* __restrict__ begins, in
 
 // The persistent kernel over all jobs: k_path's loop with per-lane job lookup.
 // Register cap 96 for every block size, so that 640 lanes per SM stay resident.
-template <int BLOCK>
+template <int BLOCK, bool LOCAL>
 __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const long long* __restrict__ begins,
                                         int n_jobs, long long total, int chunk, int shade_min,
                                         unsigned long long* __restrict__ counters) {
@@ -88,7 +90,7 @@ __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const l
       if (s.waiting) lane_shade<false>(s, J.S, J.P, A, nullptr, c);
     }
     if (!s.active || s.waiting) continue;
-    if (lane_step<false>(s, J.S, J.P, A, nullptr, c)) lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
+    if (lane_step<false, LOCAL>(s, J.S, J.P, A, nullptr, c)) lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
   }
   flush_counters(c, counters, nullptr);
 }
@@ -105,30 +107,39 @@ __global__ void k_zero_films(const JobDev* __restrict__ jobs) {
   }
 }
 
-template <int BLOCK>
+template <int BLOCK, bool LOCAL>
 static int batch_grid(int device) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK>, BLOCK, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK, LOCAL>, BLOCK, 0);
   return sms * std::max(per_sm, 1);
 }
 
-static int grid_for(int block, int device) {
+static int grid_for(int block, bool local, int device) {
   switch (block) {
-    case 64: return batch_grid<64>(device);
-    case 256: return batch_grid<256>(device);
-    default: return batch_grid<128>(device);
+    case 64: return local ? batch_grid<64, true>(device) : batch_grid<64, false>(device);
+    case 256: return local ? batch_grid<256, true>(device) : batch_grid<256, false>(device);
+    default: return local ? batch_grid<128, true>(device) : batch_grid<128, false>(device);
   }
 }
 
-static cudaError_t launch_batch(int block, int grid, const JobDev* jobs, const long long* begins, int n,
+template <bool LOCAL>
+static void launch_batch_t(int block, int grid, const JobDev* jobs, const long long* begins, int n, long long total,
+                           int chunk, int shade_min, unsigned long long* counters, cudaStream_t st) {
+  switch (block) {
+    case 64: k_batch<64, LOCAL><<<grid, 64, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    case 256: k_batch<256, LOCAL><<<grid, 256, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    default: k_batch<128, LOCAL><<<grid, 128, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+  }
+}
+
+static cudaError_t launch_batch(int block, bool local, int grid, const JobDev* jobs, const long long* begins, int n,
                                 long long total, int chunk, int shade_min, unsigned long long* counters,
                                 cudaStream_t st) {
-  switch (block) {
-    case 64: k_batch<64><<<grid, 64, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-    case 256: k_batch<256><<<grid, 256, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-    default: k_batch<128><<<grid, 128, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-  }
+  if (local)
+    launch_batch_t<true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+  else
+    launch_batch_t<false>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
   return cudaGetLastError();
 }
 
@@ -155,6 +166,7 @@ struct gpss_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool table_valid = false;
+  bool local = false;              // some job's scene uses local majorants
   int block = 128, shade_min = kBatchDefaultShade, chunk = kBatchDefaultChunk, grid = 0;
 };
 
@@ -185,27 +197,30 @@ static void fill_table(const gpss_batch_s* b, JobDev* out, float* const* images,
   }
 }
 
-// Times one launch shape on a tuning table (best of two launches after a warm-up).
-// Returns the time in ms, or -1 with *err set.
+// Times one launch shape on a tuning table: one launch (the paths and their random
+// numbers are fixed, so repeats differ only by scheduling noise), preceded by an
+// untimed one the first time a block size runs (module load).  Returns the time
+// in ms, or -1 with *err set.
 static float time_shape(gpss_batch b, int block, int shade_min, int chunk, const JobDev* jobs, const long long* begins,
-                        long long total, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, cudaError_t* err) {
-  const int grid = grid_for(block, b->device);
-  float best = 1e30f;
-  for (int rep = 0; rep < 3; ++rep) {
+                        long long total, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, bool warm,
+                        cudaError_t* err) {
+  const int grid = grid_for(block, b->local, b->device);
+  float ms = 0.0f;
+  for (int rep = warm ? 0 : 1; rep < 2; ++rep) {
     cudaMemsetAsync(b->counters, 0, 16 * sizeof(unsigned long long), st);
     cudaEventRecord(e0, st);
-    if ((*err = launch_batch(block, grid, jobs, begins, b->n, total, chunk, shade_min, b->counters, st)) != cudaSuccess)
+    if ((*err = launch_batch(block, b->local, grid, jobs, begins, b->n, total, chunk, shade_min, b->counters, st)) != cudaSuccess)
       return -1.0f;
     cudaEventRecord(e1, st);
     if ((*err = cudaEventSynchronize(e1)) != cudaSuccess) return -1.0f;
-    float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (rep > 0) best = std::min(best, ms);
   }
-  return best;
+  return ms;
 }
 
-// Coordinate descent over (block, shade_min, chunk) on a reduced-spp copy of the batch.
+// Coordinate descent over (block, shade_min, chunk) on a reduced-spp copy of the
+// batch; stops early (keeping the best shape so far) once the timed launches
+// have taken kTuneBudgetMs.
 static gpss_status autotune(gpss_batch b, cudaStream_t st) {
   int div = (int)std::min<long long>((b->total + kTunePaths - 1) / kTunePaths, 1 << 20);
   if (div < 1) div = 1;
@@ -247,30 +262,42 @@ static gpss_status autotune(gpss_batch b, cudaStream_t st) {
   cudaEventCreate(&e1);
   {
     const long long ttotal = tbeg[b->n];
-    int best_b = 128, best_s = kBatchDefaultShade, best_c = kBatchDefaultChunk;
-    float best = time_shape(b, best_b, best_s, best_c, tjobs, tbegins, ttotal, st, e0, e1, &e);
-    if (best < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
+    struct Cand { int block, shade, chunk; };
+    const Cand start{128, kBatchDefaultShade, kBatchDefaultChunk};
+    Cand best = start;
+    bool warmed[3] = {false, false, false};  // block 64 / 128 / 256
+    auto slot = [](int blk) { return blk == 64 ? 0 : blk == 128 ? 1 : 2; };
+    float spent = 0.0f;
+    float best_ms = time_shape(b, best.block, best.shade, best.chunk, tjobs, tbegins, ttotal, st, e0, e1, true, &e);
+    if (best_ms < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
+    warmed[1] = true;
+    spent += best_ms;
     const int blocks[] = {64, 256};
-    for (int v : blocks) {
-      const float t = time_shape(b, v, best_s, best_c, tjobs, tbegins, ttotal, st, e0, e1, &e);
-      if (t < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
-      if (t < best) { best = t; best_b = v; }
-    }
     const int shades[] = {8, 16, 32};
-    for (int v : shades) {
-      const float t = time_shape(b, best_b, v, best_c, tjobs, tbegins, ttotal, st, e0, e1, &e);
-      if (t < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
-      if (t < best) { best = t; best_s = v; }
-    }
     const int chunks[] = {64, 128, 512, 1024};
-    for (int v : chunks) {
-      const float t = time_shape(b, best_b, best_s, v, tjobs, tbegins, ttotal, st, e0, e1, &e);
-      if (t < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
-      if (t < best) { best = t; best_c = v; }
+    for (int axis = 0; axis < 3; ++axis) {
+      const int* vals = axis == 0 ? blocks : axis == 1 ? shades : chunks;
+      const int nv = axis == 0 ? 2 : axis == 1 ? 3 : 4;
+      const Cand base = best;
+      for (int v = 0; v < nv && spent < kTuneBudgetMs; ++v) {
+        Cand c = base;
+        if (axis == 0) c.block = vals[v];
+        else if (axis == 1) c.shade = vals[v];
+        else c.chunk = vals[v];
+        const bool warm = !warmed[slot(c.block)];
+        const float t = time_shape(b, c.block, c.shade, c.chunk, tjobs, tbegins, ttotal, st, e0, e1, warm, &e);
+        if (t < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
+        warmed[slot(c.block)] = true;
+        spent += warm ? 2.0f * t : t;
+        if (t < best_ms) {
+          best_ms = t;
+          best = c;
+        }
+      }
     }
-    b->block = best_b;
-    b->shade_min = best_s;
-    b->chunk = best_c;
+    b->block = best.block;
+    b->shade_min = best.shade;
+    b->chunk = best.chunk;
   }
 done:
   if (e0) cudaEventDestroy(e0);
@@ -288,7 +315,7 @@ static gpss_status capture_graph(gpss_batch b) {
     return cuda_fail(e, "begin capture");
   cudaMemsetAsync(b->counters, 0, 16 * sizeof(unsigned long long), b->capture);
   k_zero_films<<<dim3(64, b->n), 256, 0, b->capture>>>(b->table_dev);
-  cudaError_t le = launch_batch(b->block, b->grid, b->table_dev, b->begins_dev, b->n, b->total, b->chunk,
+  cudaError_t le = launch_batch(b->block, b->local, b->grid, b->table_dev, b->begins_dev, b->n, b->total, b->chunk,
                                 b->shade_min, b->counters, b->capture);
   e = cudaStreamEndCapture(b->capture, &b->graph);
   if (le != cudaSuccess) return cuda_fail(le, "batch launch (capture)");
@@ -329,6 +356,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
     if ((st = check_opts(&opts[i])) != GPSS_OK) { free_batch(b); return st; }
     if (opts[i].flags != 0) { set_error("batch job %d: flags must be 0", i); free_batch(b); return GPSS_ERR_INVALID_ARG; }
     if (!camera_dev(&cams[i], &b->cams[i])) { free_batch(b); return GPSS_ERR_INVALID_ARG; }
+    if (scene_dev(scenes[i]).mg.hot > 0.0f) b->local = true;
     PathArgs& P = b->args[i];
     P.spp = opts[i].spp;
     P.max_bounces = opts[i].max_bounces;
@@ -364,7 +392,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
   } else {
     b->block = block_size;
   }
-  b->grid = grid_for(b->block, dev);
+  b->grid = grid_for(b->block, b->local, dev);
   if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) { st = cuda_fail(e, "batch setup"); free_batch(b); return st; }
   if ((st = capture_graph(b)) != GPSS_OK) { free_batch(b); return st; }
   *out = b;

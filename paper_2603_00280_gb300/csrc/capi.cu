@@ -219,7 +219,7 @@ extern "C" gpss_status gpss_scene_create(const gpss_object_desc* objs, int n_obj
   }
   if ((e = cudaMalloc(&s->counters, 16 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&s->tmp_planes, 2 * max_nodes * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&s->flags, 4 * sizeof(int))) != cudaSuccess) {
+      (e = cudaMalloc(&s->flags, kSceneFlagWords * sizeof(int))) != cudaSuccess) {
     free_scene(s);
     return cuda_fail(e, "scratch allocation");
   }

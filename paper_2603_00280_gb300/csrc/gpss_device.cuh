@@ -716,6 +716,9 @@ __device__ __forceinline__ float slab_exit(float lo, float hi, float o, float in
   return ((dcomp > 0.0f ? hi : lo) - o) * inv;
 }
 
+// LOCAL = false compiles the local-majorant branch out (scenes without thin
+// objects: no register cost for it in the render kernels).
+template <bool LOCAL = true>
 __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectDev& lob, V3 o, V3 d, Walk& w, float tau,
                                              uint32_t& steps) {
   // Each step moves the cell index strictly past the face the ray left by (or, in
@@ -732,7 +735,7 @@ __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectD
     const float ez = slab_exit(g.gmin[2] + (float)lz * g.cell[2], g.gmin[2] + (float)(hz + 1) * g.cell[2], o.z, w.idz, d.z);
     const float seg_end = fminf(fminf(ex, ey), fminf(ez, w.t_end));
     float piece_end = seg_end, sbar = sk.x;
-    if (g.hot > 0.0f && sk.x * (seg_end - w.t) > g.hot) {
+    if (LOCAL && g.hot > 0.0f && sk.x * (seg_end - w.t) > g.hot) {
       const float2 pc = local_majorant(lob, o, d, w.t, seg_end);
       if (pc.x > w.t && pc.y < sk.x) {
         piece_end = fminf(pc.x, seg_end);

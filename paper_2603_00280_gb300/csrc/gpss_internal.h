@@ -31,7 +31,10 @@ struct ObjectHost {
   float2* mv = nullptr;      // device (mean, variance)
   float* albedo = nullptr;   // device planes
   size_t nodes = 0;
+  float sigma_min = 0.0f;    // smallest standard deviation over the nodes
 };
+
+constexpr int kSceneFlagWords = 1 + kMaxObjects;  // validation bits + per-object min variance
 
 }  // namespace gpss
 
@@ -48,6 +51,7 @@ struct gpss_scene_s {
   float kappa = 0.5f;              // expected majorant depth allowed per skip
   int shade_min = 24;              // lanes a warp gathers before shading real vertices
   float hot = 4.0f;                // local-majorant threshold (0 = off; single-object scenes)
+  bool thin = false;               // some object's sigma_min < its grid spacing (local majorants pay)
   int brick = 1;                   // majorant cell = brick x finest field cell
   // scratch owned by the scene
   unsigned long long* counters = nullptr;   // kCntNum u64 + work cursor

@@ -319,7 +319,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
 }
 
 // One tentative collision of the lane's current ray; returns true when the path ends.
-template <bool ADJ>
+template <bool ADJ, bool LOCAL>
 __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                           float* __restrict__ path_T, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
@@ -328,7 +328,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
     s.begin = false;
   }
   bool hit = false;
-  if (s.walk_ok) hit = walk_advance(S.mg, S.obj[0], s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
+  if (s.walk_ok) hit = walk_advance<LOCAL>(S.mg, S.obj[0], s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
   bool finish = false;
   if (hit) {
     ++s.events;
@@ -481,7 +481,8 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
 }
 
 // ---------------------------------------------------------------- single-render kernel
-template <bool ADJ>
+// LOCAL: the scene uses local majorants (MajorantDev::hot > 0).
+template <bool ADJ, bool LOCAL>
 __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
     k_path(const __grid_constant__ SceneDev S, const __grid_constant__ CameraDev C, const __grid_constant__ PathArgs P,
            float* __restrict__ image, float* __restrict__ sqsum, float* __restrict__ path_radiance,
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
       if (s.waiting) lane_shade<ADJ>(s, S, P, A, path_T, c);
     }
     if (!s.active || s.waiting || s.vgrad) continue;
-    if (lane_step<ADJ>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
+    if (lane_step<ADJ, LOCAL>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
   }
   flush_counters(c, counters, ADJ ? A.d_l : nullptr);
 }

@@ -9,7 +9,7 @@ int render_block_size() { return kPathBlock; }
 int render_grid_size(int device, int block) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<false, false>, block, 0);
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
 }
@@ -27,7 +27,10 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   P.inv_spp = 1.0f / (float)o.spp;
   P.shade_min = shade_min;
   AdjOut A{};
-  k_path<false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+  if (S.mg.hot > 0.0f)
+    k_path<false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+  else
+    k_path<false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 // (read only at real collisions).  The majorant grid is a separate float grid
 // over the union of the object boxes whose cells are `brick` x the finest field
 // cell; for one object it is aligned with the field cells.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -12,14 +13,20 @@
 
 namespace gpss {
 
+// Interleaves (mean, variance) per node, validates both, and lowers *vmin_bits
+// to the bits of the smallest variance (positive floats order like their bits).
 __global__ void k_interleave(const float* __restrict__ mean, const float* __restrict__ var, float2* __restrict__ mv,
-                             size_t n, int* flags) {
+                             size_t n, int* flags, unsigned* vmin_bits) {
+  float vmin = INFINITY;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float m = mean[i], v = var[i];
     if (!isfinite(m)) atomicOr(flags, 1);
     if (!(v > 0.0f) || !isfinite(v)) atomicOr(flags, 2);
+    else vmin = fminf(vmin, v);
     mv[i] = make_float2(m, v);
   }
+  for (int off = 16; off > 0; off >>= 1) vmin = fminf(vmin, __shfl_xor_sync(0xFFFFFFFFu, vmin, off));
+  if ((threadIdx.x & 31) == 0 && vmin < INFINITY) atomicMin(vmin_bits, __float_as_uint(vmin));
 }
 
 __global__ void k_check_albedo(const float* __restrict__ a, size_t n, int* flags) {
@@ -126,7 +133,10 @@ static int blocks_for(size_t n, int block) {
 }
 
 gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(s->flags, 0, sizeof(int), st);
+  // flags[0]: validation bits; flags[1 + k]: bits of object k's smallest variance
+  // (0x7f7f7f7f = 3.4e38 before the minimum)
+  cudaError_t e = cudaMemsetAsync(s->flags, 0x7f, kSceneFlagWords * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->flags, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset flags");
   for (int k = 0; k < n; ++k) {
     ObjectHost& o = s->obj[k];
@@ -135,21 +145,35 @@ gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cuda
     if (e != cudaSuccess) return cuda_fail(e, "copy mean");
     e = cudaMemcpyAsync(s->tmp_planes + nodes, objs[k].variance, nodes * sizeof(float), cudaMemcpyDefault, st);
     if (e != cudaSuccess) return cuda_fail(e, "copy variance");
-    k_interleave<<<blocks_for(nodes, 256), 256, 0, st>>>(s->tmp_planes, s->tmp_planes + nodes, o.mv, nodes, s->flags);
+    k_interleave<<<blocks_for(nodes, 256), 256, 0, st>>>(s->tmp_planes, s->tmp_planes + nodes, o.mv, nodes, s->flags,
+                                                         (unsigned*)(s->flags + 1 + k));
     e = cudaMemcpyAsync(o.albedo, objs[k].albedo, nodes * o.channels * sizeof(float), cudaMemcpyDefault, st);
     if (e != cudaSuccess) return cuda_fail(e, "copy albedo");
     k_check_albedo<<<blocks_for(nodes * o.channels, 256), 256, 0, st>>>(o.albedo, nodes * o.channels, s->flags);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "upload kernels");
-  int flags = 0;
-  e = cudaMemcpyAsync(&flags, s->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int fl[kSceneFlagWords];
+  e = cudaMemcpyAsync(fl, s->flags, sizeof(fl), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "read flags");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "upload");
+  const int flags = fl[0];
   if (flags & 1) { set_error("mean contains non-finite values"); return GPSS_ERR_INVALID_ARG; }
   if (flags & 2) { set_error("variance must be finite and > 0"); return GPSS_ERR_INVALID_ARG; }
   if (flags & 4) { set_error("albedo must lie in [0,1]"); return GPSS_ERR_INVALID_ARG; }
+  // thin: some object's smallest standard deviation lies below its grid spacing,
+  // where the grid majorant of the cells at its shell is loose
+  s->thin = false;
+  for (int k = 0; k < n; ++k) {
+    float vmin;
+    std::memcpy(&vmin, &fl[1 + k], sizeof(float));
+    ObjectHost& o = s->obj[k];
+    o.sigma_min = std::sqrt(vmin);
+    float h = INFINITY;
+    for (int a = 0; a < 3; ++a) h = std::fmin(h, (o.bmax[a] - o.bmin[a]) / (float)(o.n[a] - 1));
+    if (h > o.sigma_min) s->thin = true;
+  }
   return GPSS_OK;
 }
 
@@ -200,7 +224,7 @@ SceneDev scene_dev(const gpss_scene_s* s) {
   d.mg = s->mg;
   d.mg.maj = s->maj;
   d.mg.skip = s->skip;
-  d.mg.hot = s->n_objs == 1 ? s->hot : 0.0f;
+  d.mg.hot = (s->n_objs == 1 && s->thin) ? s->hot : 0.0f;
   d.light = s->light;
   return d;
 }
