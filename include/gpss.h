@@ -103,6 +103,7 @@ typedef struct {
 
 typedef struct {
   uint64_t paths, vertices, null_collisions, shadow_steps, majorant_cells, truncated, aborted;
+  uint64_t max_path_events;  /* most tentative collisions of one path (flight + shadow) */
   float ms;                /* device time of the render kernel                      */
 } gpss_stats;
 

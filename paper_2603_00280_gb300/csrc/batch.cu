@@ -67,7 +67,7 @@ __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const l
   WarpCursor wc{0, 0, false};
   Lane s;
   lane_init(s);
-  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0.0f};
+  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, 0.0f};
   const AdjOut A{};
   for (;;) {
     const unsigned need = __ballot_sync(FULL, !s.active);
@@ -431,13 +431,7 @@ extern "C" gpss_status gpss_batch_render(gpss_batch b, float* const* images, flo
     if ((e = cudaMemcpyAsync(c, b->counters, sizeof(c), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
       return cuda_fail(e, "stats copy");
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "batch render");
-    stats->paths = c[kCntPaths];
-    stats->vertices = c[kCntVertices];
-    stats->null_collisions = c[kCntNull];
-    stats->shadow_steps = c[kCntShadow];
-    stats->majorant_cells = c[kCntCells];
-    stats->truncated = c[kCntTruncated];
-    stats->aborted = c[kCntAborted];
+    fill_stats(stats, c, 0.0f);
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     stats->ms = ms;

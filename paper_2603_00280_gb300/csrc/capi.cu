@@ -18,6 +18,18 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+void fill_stats(gpss_stats* st, const unsigned long long* c, float ms) {
+  st->paths = c[kCntPaths];
+  st->vertices = c[kCntVertices];
+  st->null_collisions = c[kCntNull];
+  st->shadow_steps = c[kCntShadow];
+  st->majorant_cells = c[kCntCells];
+  st->truncated = c[kCntTruncated];
+  st->aborted = c[kCntAborted];
+  st->max_path_events = c[kCntMaxEvents];
+  st->ms = ms;
+}
+
 gpss_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return GPSS_ERR_OOM;
@@ -388,13 +400,7 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
       return cuda_fail(e, "stats copy");
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "render");
     if (stats) {
-      stats->paths = c[kCntPaths];
-      stats->vertices = c[kCntVertices];
-      stats->null_collisions = c[kCntNull];
-      stats->shadow_steps = c[kCntShadow];
-      stats->majorant_cells = c[kCntCells];
-      stats->truncated = c[kCntTruncated];
-      stats->aborted = c[kCntAborted];
+      fill_stats(stats, c, 0.0f);
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, ev0, ev1);
       stats->ms = ms;

@@ -20,8 +20,10 @@ enum Counter : int {
   kCntCells,
   kCntTruncated,
   kCntAborted,
+  kCntMaxEvents,   // max over paths (atomicMax)
   kCntNum
 };
+static_assert(kCntNum + 1 <= 16, "counters + cursor must fit the 16-word counter area");
 
 struct ObjectHost {
   int n[3];
@@ -71,6 +73,8 @@ struct gpss_scene_s {
 namespace gpss {
 
 void set_error(const char* fmt, ...);
+// Fills *st from the kCntNum device counters copied to the host.
+void fill_stats(gpss_stats* st, const unsigned long long* c, float ms);
 gpss_status cuda_fail(cudaError_t e, const char* what);
 
 gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cudaStream_t st);

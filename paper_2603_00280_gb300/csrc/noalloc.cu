@@ -102,13 +102,7 @@ extern "C" gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam,
     if ((e = cudaMemcpyAsync(c, counters, sizeof(c), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
       return cuda_fail(e, "stats copy");
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "render");
-    stats->paths = c[kCntPaths];
-    stats->vertices = c[kCntVertices];
-    stats->null_collisions = c[kCntNull];
-    stats->shadow_steps = c[kCntShadow];
-    stats->majorant_cells = c[kCntCells];
-    stats->truncated = c[kCntTruncated];
-    stats->aborted = c[kCntAborted];
+    fill_stats(stats, c, 0.0f);
     stats->ms = 0.0f;
   }
   return GPSS_OK;

@@ -165,6 +165,7 @@ struct Lane {
 
 struct LaneCounters {
   uint32_t paths, vert, null_, shadow, cells, trunc, abort;
+  uint32_t max_events;  // most tentative collisions of one path
   float acc_l;  // adjoint: length-scale gradient
 };
 
@@ -432,6 +433,7 @@ __device__ __forceinline__ void lane_finish(Lane& s, const PathArgs& P, float* _
     if (fabsf(e.x) + fabsf(e.y) + fabsf(e.z) > tol) ++c.abort;
   }
   ++c.paths;
+  c.max_events = max(c.max_events, s.events);
   s.active = false;
 }
 
@@ -478,6 +480,9 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
     if (lane == 0 && v) atomicAdd(counters + i, v);
   }
+  uint32_t me = c.max_events;
+  for (int off = 16; off > 0; off >>= 1) me = max(me, __shfl_down_sync(FULL, me, off));
+  if (lane == 0 && me) atomicMax(counters + kCntMaxEvents, (unsigned long long)me);
 }
 
 // ---------------------------------------------------------------- single-render kernel
@@ -492,7 +497,7 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
   WarpCursor wc{0, 0, false};
   Lane s;
   lane_init(s);
-  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0.0f};
+  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, 0.0f};
   for (;;) {
     const unsigned need = __ballot_sync(FULL, !s.active);
     if (need && !wc.exhausted) {
