@@ -139,14 +139,16 @@ def test_thin_shell_ratio_tracking_unbiased(plane):
     ref = np.array([oracle.transmittance(O, o[i].astype(np.float64), d[i].astype(np.float64), float(tmax[i]))
                     for i in range(n)])
     assert ((ref > 0.02) & (ref < 0.98)).mean() > 0.7, ref
-    N = 40000
-    for hot in (4.0, 0.0):
+    # local majorants on all rays; the grid majorant (about (h/sigma)^2 null collisions
+    # per shell crossing) on a subset with fewer samples
+    for hot, rays, N in ((4.0, slice(None), 40000), (0.0, slice(0, n, 4), 4000)):
         G.set_local_majorant(hot)
-        m = gpss.estimate_transmittance(G, o, d, tmax, N, seed=11).cpu().numpy().astype(np.float64)
-        se = np.sqrt(np.maximum(ref * (1 - ref), 1e-4) / N)
-        z = (m - ref) / se
+        m = gpss.estimate_transmittance(G, o[rays], d[rays], tmax[rays], N, seed=11).cpu().numpy().astype(np.float64)
+        r = ref[rays]
+        se = np.sqrt(np.maximum(r * (1 - r), 1e-4) / N)
+        z = (m - r) / se
         assert np.mean(np.abs(z) > 4) < 0.05, (hot, z)
-        assert abs(np.sum(m - ref)) < 4 * np.sqrt(np.sum(se ** 2)), hot
+        assert abs(np.sum(m - r)) < 4 * np.sqrt(np.sum(se ** 2)), hot
     G.set_local_majorant(4.0)
 
 
