@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "M path-vertices/s at 1 GB300 (fwd; fwd+adjoint) and fraction of FP32-issue roofline"
 UNIT = "M path-vertices/s"
-# Algorithmic FP32 work per unit: one extinction
+# Algorithmic FP32 work per unit (counted from the formulas, not the code): one extinction
 # evaluation (field fetch + sigma_t) per tentative collision, plus the shading of
 # each real vertex (phase sampling + NEE phase evaluation + MIS).
 OPS_PER_SIGMA_T = 130
@@ -197,6 +197,21 @@ def oracle_sample(wl, target_seconds, threads=0):
     desc = "%d pixels (rows %d:%d:%d, cols %d:%d) x %d spp, %d paths, %d vertices, %.1f s" % (
         n_rows * 16, rows[0], rows[1], rows[2], c0, c1, opts["spp"], st["paths"], st["vertices"], dt)
     return st["vertices"] / dt / 1e6, desc, cores, dt
+
+
+# ----------------------------------------------------------------- ranks
+def job_totals(total_ms, units, dist=None, device="cpu"):
+    """Whole-job totals over ranks: the slowest rank's time (max) and the units
+    all ranks processed (sum).  Weak scaling: every rank renders the full
+    workload with its own random numbers, so the ranks exchange nothing but these two
+    numbers (each rank keys its paths with seed + 1000 * rank)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
 
 
 # ----------------------------------------------------------------- forward + adjoint
@@ -365,14 +380,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms, float(verts)], dtype=torch.float64, device="cuda")
-    if dist:
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tmax[1:2], op=dist.ReduceOp.SUM)
-        t = tmax
-    total_ms, all_verts = float(t[0]), float(t[1])
+    total_ms, all_verts = job_totals(sum(step_ms), verts, dist, "cuda")
     value = all_verts / (total_ms / 1e3) / 1e6
 
     # e2e through the C-ABI with host buffers: upload the grids from pinned host
@@ -399,11 +407,8 @@ def run_ours(args):
             if i >= args.warmup:
                 e2e_ms.append(1e3 * (t1 - t0))
                 e2e_verts += st["vertices"]
-        et = torch.tensor([sum(e2e_ms), float(e2e_verts)], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(et[0:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(et[1:2], op=dist.ReduceOp.SUM)
-        e2e = {"value": float(et[1]) / (float(et[0]) / 1e3) / 1e6, "unit": UNIT,
+        e_ms, e_verts = job_totals(sum(e2e_ms), e2e_verts, dist, "cuda")
+        e2e = {"value": e_verts / (e_ms / 1e3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": H * W * 3 * 4}
 
     adj = None if args.no_adjoint else measure_adjoint(args, gpss, torch, flush, rank)

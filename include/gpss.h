@@ -13,7 +13,7 @@
  *   phase        p(d,d') = F D_d(m) / (4 |d.m|)            (Eq. phase, microfacet_vndf)
  * with per-pixel Monte Carlo path tracing ("null scattering", Sec. 5): delta
  * tracking, ratio-tracking next-event estimation, and the mixture sampler of
- * Sec. 4.2.2 (Beckmann visible normals with probability R, else uniform).
+ * Sec. 4.2 (Beckmann visible normals with probability R, else uniform).
  *
  * Conventions
  *  - d is the marching direction of a ray (the paper's omega_o for extinction;

@@ -14,7 +14,7 @@
  *  - A scene object is a GPSS f ~ GP(mu(x), kappa) with squared-exponential
  *    kernel (Eq. se_kernel).  mu and sigma^2 are node-centred grids, trilinearly
  *    interpolated; grad mu is the analytic gradient of that interpolant.
- *  - Under the independence assumption (Sec. 4.2.1) the gradient at a point is
+ *  - Under the independence assumption (Sec. 4.2) the gradient at a point is
  *    g ~ N(grad mu, (sigma/l)^2 I) independent of f ~ N(mu, sigma^2).
  *  - Extinction for a ray marching along d (omega_o in Eq. generalized_sigma_t):
  *      sigma_t(x,d) = rho(x) * sigma(d),
@@ -101,7 +101,7 @@ double orc_ndf_local(const double m[3], double G, double ax, double ay, double a
 double orc_sigma_t_object(const orc_object* o, const double x[3], const double d[3]);
 double orc_sigma_t(const orc_scene* s, const double x[3], const double d[3]);
 /* Phase function of object k at x: p (per channel, includes F) and the pdf
- * of the sampling mixture over outgoing directions (Sec. 4.2.2, end).     */
+ * of the sampling mixture over outgoing directions (end of Sec. 4.2).     */
 int orc_phase_eval(const orc_scene* s, int k, const double x[3], const double d[3],
                    const double d2[3], double R, double p_out[3], double* pdf_out);
 /* Samples d2 with three uniforms; returns weight p/pdf (per channel) and pdf. */

@@ -254,7 +254,7 @@ double orc_sigma_t(const orc_scene* s, const double x[3], const double d[3]) {
 /* ------------------------------------------------------------------------ */
 /* Phase function (Eq. phase with Eq. microfacet_vndf):                      */
 /*   p(d, d2) = F D(m) <-d, m> / (4 |d.m| sigma(d)),  m = (d2-d)/|d2-d|.      */
-/* Sampling mixture (Sec. 4.2.2, last paragraph): with probability R a       */
+/* Sampling mixture (end of Sec. 4.2): with probability R a       */
 /* Beckmann visible-normal sample (Heitz & d'Eon 2014), else m uniform on the */
 /* hemisphere around -d.  Beckmann frame and roughness: z = sign(-d.n) n and  */
 /* alpha_B = clamp(alpha/G, 1e-3, 16); z = -d when G < 1e-6.                  */

@@ -11,7 +11,7 @@
 //     form through moments M_k(q) = int_0^inf s^k exp(-s^2 + 2 q s) ds;
 //   - the conductor phase function (Eq. phase, Eq. microfacet_vndf) and the
 //     sampling mixture R * Beckmann-vNDF + (1-R) * uniform hemisphere (end of
-//     Sec. 4.2.2);
+//     Sec. 4.2);
 //   - Philox4x32-10 (Salmon et al., SC'11) keyed by (seed) with counter
 //     (pixel, sample, bounce | purpose << 16, draw);
 //   - Amanatides-Woo traversal of the majorant grid.

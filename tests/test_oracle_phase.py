@@ -1,5 +1,5 @@
 """Pins of the oracle's phase function and its sampling mixture (Eq. phase,
-Eq. microfacet_vndf and the mixture at the end of Sec. 4.2.2)."""
+Eq. microfacet_vndf and the mixture at the end of Sec. 4.2)."""
 import math
 
 import numpy as np
