@@ -1,6 +1,7 @@
 // adjoint.cu -- gradients of a rendered image with respect to the scene's grids
 // (mean, variance, albedo) and the kernel length scale: the adjoint instance of
 // the persistent path kernel (see path_kernel.cuh for the estimator).
+#include <algorithm>
 #include <cstring>
 
 #include "path_kernel.cuh"
@@ -27,6 +28,16 @@ uint64_t path_fingerprint(const gpss_camera* cam, const gpss_render_opts* o, uin
 }
 
 gpss_status check_opts(const gpss_render_opts* o);
+
+// Adds the interleaved accumulation buffer into the caller's gradient grids.
+__global__ void k_split_grad(const float2* __restrict__ mv, float* __restrict__ d_mean, float* __restrict__ d_var,
+                             size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 g = mv[i];
+    if (d_mean) d_mean[i] += g.x;
+    if (d_var) d_var[i] += g.y;
+  }
+}
 
 }  // namespace gpss
 
@@ -103,8 +114,20 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   A.d_image = d_image;
   A.L_path = s->path_radiance;
   A.T_path = s->path_T;
-  A.d_mean = d_mean;
-  A.d_var = d_variance;
+  const size_t nodes = s->obj[0].nodes;
+  A.d_mv = nullptr;
+  if (d_mean || d_variance) {
+    if (s->grad_capacity < nodes) {
+      cudaFree(s->grad_mv);
+      s->grad_mv = nullptr;
+      s->grad_capacity = 0;
+      if ((e = cudaMalloc(&s->grad_mv, nodes * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "gradient buffer");
+      s->grad_capacity = nodes;
+    }
+    if ((e = cudaMemsetAsync(s->grad_mv, 0, nodes * sizeof(float2), cs)) != cudaSuccess)
+      return cuda_fail(e, "clear gradient buffer");
+    A.d_mv = s->grad_mv;
+  }
   A.d_alb = d_albedo;
   A.d_l = d_length_scale;
   int sms = 0, per_sm = 0;
@@ -121,6 +144,11 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
     k_path<true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  if (A.d_mv) {
+    const int eb = (int)std::min<size_t>((nodes + 255) / 256, 4096);
+    k_split_grad<<<eb, 256, 0, cs>>>(A.d_mv, d_mean, d_variance, nodes);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gradient epilogue");
+  }
   if (stats) {
     cudaEventRecord(ev1, cs);
     unsigned long long c[16];

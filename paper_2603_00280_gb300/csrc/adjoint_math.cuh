@@ -16,22 +16,22 @@
 namespace gpss {
 
 // psi(a) and the two ratios erfc(a)/psi(a), (e^{-a^2}/(2 sqrt pi))/psi(a), without
-// underflow for large a (continued fraction as in psi()).
+// underflow for large a (continued fraction as in psi(); for a > 2 the ratios follow
+// from K alone and from erfcx).
 __device__ __forceinline__ void psi_ratios(float a, float& ps, float& ec_over, float& ea_over) {
+  const float ex = expf(-a * a);
+  const float E = erfcxf(fabsf(a));
+  const float ec = erfc_from(a, ex, E);
   if (a <= 2.0f) {
-    const float ec = erfcf(a);
-    const float ea = 0.5f * kInvSqrtPi * expf(-a * a);
+    const float ea = 0.5f * kInvSqrtPi * ex;
     ps = fmaf(-0.5f * a, ec, ea);
     ec_over = ec / ps;
     ea_over = ea / ps;
   } else {
-    const float y = kSqrt2 * a;
-    float r = 0.0f;
-#pragma unroll 1
-    for (int k = 20; k >= 1; --k) r = (float)k / (y + r);
-    ps = erfcf(a) * r * (0.5f * kInvSqrt2);
+    const float r = mills_cf(kSqrt2 * a);
+    ps = ec * r * (0.5f * kInvSqrt2);
     ec_over = 2.0f * kSqrt2 / r;
-    ea_over = kSqrt2 * kInvSqrtPi / (erfcxf(a) * r);
+    ea_over = kSqrt2 * kInvSqrtPi / (E * r);
   }
 }
 
@@ -89,9 +89,10 @@ static __device__ __noinline__ DPhase dlog_phase(V3 d, V3 m, Field f, float alph
   return r;
 }
 
-// Scatters c_mu * dmu/d(node) + c_g . d(grad mu)/d(node) and c_var * dvar/d(node).
+// Scatters c_mu * dmu/d(node) + c_g . d(grad mu)/d(node) and c_var * dvar/d(node) into the
+// interleaved (d mean, d variance) gradient buffer: one 8-byte atomic per node.
 static __device__ __noinline__ void scatter_field(const ObjectDev& o, V3 x, float cmu, V3 cg, float cvar,
-                                                  float* __restrict__ dmean, float* __restrict__ dvar) {
+                                                  float2* __restrict__ dmv) {
   float wx, wy, wz;
   const int b = cell_of(o, x, wx, wy, wz);
   const int sy = o.n[0], sz = o.n[0] * o.n[1];
@@ -103,8 +104,7 @@ static __device__ __noinline__ void scatter_field(const ObjectDev& o, V3 x, floa
     const float w = ax * ay * az;
     const float gx = sx * ay * az * o.inv_h[0], gy = ax * syy * az * o.inv_h[1], gz = ax * ay * szz * o.inv_h[2];
     const int idx = b + cx + sy * cy + sz * cz;
-    if (dmean) atomicAdd(dmean + idx, fmaf(cmu, w, fmaf(cg.x, gx, fmaf(cg.y, gy, cg.z * gz))));
-    if (dvar) atomicAdd(dvar + idx, cvar * w);
+    atomicAdd(dmv + idx, make_float2(fmaf(cmu, w, fmaf(cg.x, gx, fmaf(cg.y, gy, cg.z * gz))), cvar * w));
   }
 }
 

@@ -147,6 +147,7 @@ static void free_scene(gpss_scene s) {
   cudaFree(s->counters);
   cudaFree(s->tmp_planes);
   cudaFree(s->flags);
+  cudaFree(s->grad_mv);
   cudaFree(s->film);
   cudaFree(s->path_radiance);
   cudaFree(s->path_T);

@@ -166,17 +166,30 @@ struct Rng {
 // lambda(u) = phi(u)/Phi(u) = sqrt(2/pi) / erfcx(-u/sqrt2)   (inverse Mills ratio)
 __device__ __forceinline__ float inv_mills(float u) { return kSqrt2OverPi / erfcxf(-u * kInvSqrt2); }
 
-// psi(a) = exp(-a^2)/(2 sqrt(pi)) - (a/2) erfc(a) = E[max(0, Z/sqrt2 - a)] with Z ~ N(0,1),
-// so the projected area is sigma(d) = alpha * psi((d . grad mu)/alpha).  For a > 2 the
-// difference cancels; there psi = erfc(a) * K(sqrt2 a) / (2 sqrt2) with Laplace's continued
-// fraction K(y) = 1/(y + 2/(y + 3/(y + ...))) of the Mills ratio (20 terms).
-__device__ __forceinline__ float psi(float a) {
-  if (a <= 2.0f) return fmaf(-0.5f * a, erfcf(a), 0.5f * kInvSqrtPi * expf(-a * a));
-  const float y = kSqrt2 * a;
+// erfc(a) from one erfcx evaluation: erfcx(|a|) e^{-a^2} for a >= 0, 2 minus that for
+// a < 0 (ex = e^{-a^2} is passed in because the callers need it too).
+__device__ __forceinline__ float erfc_from(float a, float ex, float erfcx_abs) {
+  const float t = erfcx_abs * ex;
+  return a >= 0.0f ? t : 2.0f - t;
+}
+
+// Laplace's continued fraction K(y) = 1/(y + 2/(y + 3/(y + ...))) of the Mills ratio,
+// 20 terms, evaluated backward (y >= 2 sqrt2 at the call sites).
+__device__ __forceinline__ float mills_cf(float y) {
   float r = 0.0f;
 #pragma unroll 1
-  for (int k = 20; k >= 1; --k) r = (float)k / (y + r);
-  return erfcf(a) * r * (0.5f * kInvSqrt2);
+  for (int k = 20; k >= 1; --k) r = __fdividef((float)k, y + r);
+  return r;
+}
+
+// psi(a) = exp(-a^2)/(2 sqrt(pi)) - (a/2) erfc(a) = E[max(0, Z/sqrt2 - a)] with Z ~ N(0,1),
+// so the projected area is sigma(d) = alpha * psi((d . grad mu)/alpha).  For a > 2 the
+// difference cancels; there psi = erfc(a) * K(sqrt2 a) / (2 sqrt2).
+__device__ __forceinline__ float psi(float a) {
+  const float ex = expf(-a * a);
+  const float ec = erfc_from(a, ex, erfcxf(fabsf(a)));
+  if (a <= 2.0f) return fmaf(-0.5f * a, ec, 0.5f * kInvSqrtPi * ex);
+  return ec * mills_cf(kSqrt2 * a) * (0.5f * kInvSqrt2);
 }
 
 // ---------------------------------------------------------------- fields

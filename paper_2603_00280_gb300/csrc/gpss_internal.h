@@ -67,6 +67,8 @@ struct gpss_scene_s {
   float* path_T = nullptr;         // per-vertex final shadow transmittance kept for the adjoint
   size_t pathT_capacity = 0;
   uint64_t path_tag = 0;           // fingerprint of the render that filled path_radiance
+  float2* grad_mv = nullptr;       // adjoint: interleaved (d mean, d variance) accumulation
+  size_t grad_capacity = 0;
   uint64_t version = 1;            // incremented whenever the grids change
 };
 

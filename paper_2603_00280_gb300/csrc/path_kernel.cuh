@@ -67,8 +67,7 @@ struct AdjOut {
   const float* d_image;   // dLoss/dimage (H*W*3)
   const float* L_path;    // per-path radiance of the forward render (3 per path)
   const float* T_path;    // per-vertex final shadow transmittance (max_bounces per path)
-  float* d_mean;
-  float* d_var;
+  float2* d_mv;           // interleaved (d mean, d variance) accumulation buffer, or null
   float* d_alb;
   float* d_l;
 };
@@ -115,10 +114,9 @@ static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, 
 }
 
 // Adjoint: scatter the derivative of the extinction (partials ds) at x with weight k.
-__device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, const DSig& ds, float k, float* d_mean,
-                                                   float* d_var) {
+__device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, const DSig& ds, float k, float2* d_mv) {
   if (!isfinite(k) || k == 0.0f) return 0.0f;
-  scatter_field(ob, x, k * ds.dmu, k * ds.dg, k * ds.dvar, d_mean, d_var);
+  if (d_mv) scatter_field(ob, x, k * ds.dmu, k * ds.dg, k * ds.dvar, d_mv);
   return k * ds.dl;
 }
 
@@ -140,7 +138,7 @@ static __device__ __noinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_
     cvar += Wph * dp.dvar;
     dl += Wph * dp.dl;
   }
-  if ((A.d_mean || A.d_var) && (Wnee != 0.0f || Wph != 0.0f)) scatter_field(ob, x, 0.0f, cg, cvar, A.d_mean, A.d_var);
+  if (A.d_mv && (Wnee != 0.0f || Wph != 0.0f)) scatter_field(ob, x, 0.0f, cg, cvar, A.d_mv);
   if (A.d_alb && (albedo_coef.x != 0.0f || albedo_coef.y != 0.0f || albedo_coef.z != 0.0f))
     scatter_albedo(ob, x, albedo_coef, A.d_alb);
   return dl;
@@ -349,12 +347,12 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
     } else {
       st = sigma_t_at(S, x, s.d);
     }
+    float k_adj = 0.0f;  // adjoint: weight of this collision's extinction derivative
     if (s.mode == kFlight) {
       const bool real = s.rng.next() * s.w.sbar < st;
       if constexpr (ADJ) {
         const float W = dot(s.gpix, s.Ltot - s.L);
-        if (W != 0.0f && inobj)
-          c.acc_l += adj_scatter_event(S.obj[0], x, ds, real ? W / st : -W / (s.w.sbar - st), A.d_mean, A.d_var);
+        if (W != 0.0f) k_adj = real ? W / st : -W / (s.w.sbar - st);
       }
       if (real) {
         ++c.vert;
@@ -366,10 +364,12 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
       ++c.shadow;
       if constexpr (ADJ) {
         const float Wn = dot(s.gpix, s.pend) * s.Tfin;
-        if (Wn != 0.0f && inobj)
-          c.acc_l += adj_scatter_event(S.obj[0], x, ds, -Wn / (s.w.sbar - st), A.d_mean, A.d_var);
+        if (Wn != 0.0f) k_adj = -Wn / (s.w.sbar - st);
       }
       if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;  // T = 0: the shadow ray ends here
+    }
+    if constexpr (ADJ) {
+      if (inobj && k_adj != 0.0f) c.acc_l += adj_scatter_event(S.obj[0], x, ds, k_adj, A.d_mv);
     }
     if (s.events >= kMaxEventsPerPath) {
       ++c.abort;
