@@ -80,13 +80,13 @@ def test_ndf_and_projected_area_parity(G, ax, ay, az):
 def test_projected_area_relative_accuracy_across_a():
     """sigma(d) = alpha psi(a) to 1e-5 relative (no absolute floor) for a = d.grad mu/alpha
     from -8.5 to 8.5: both the direct form and the continued-fraction form (a > 2),
-    down to values of 1e-33."""
+    down to values of 1e-35."""
     alpha = 0.1
     z = np.linspace(-0.85, 0.85, 4001)
     w = np.stack([np.sqrt(1 - z * z), np.zeros_like(z), z], 1).astype(np.float32)
     ga = gpss.eval_projected_area(w, 1.0, alpha, alpha, alpha).cpu().numpy().astype(np.float64)
     oa = np.array([oracle.projected_area_local(v.astype(np.float64), 1.0, alpha, alpha, alpha) for v in w])
-    assert oa.min() > 1e-34
+    assert oa.min() > 1e-37  # normal FP32 numbers throughout
     err = np.abs(ga - oa) / oa
     assert err.max() < C.REL, (err.max(), float(w[np.argmax(err), 2]) / alpha)
 
