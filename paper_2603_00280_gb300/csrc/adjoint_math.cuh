@@ -9,6 +9,8 @@
 //   d ln D/d grad mu    = (2 M4/(alpha M3)) m - (2/alpha^2) grad mu
 //   d ln D/d alpha      = 1/alpha + 2|grad mu|^2/alpha^3 - 2 q M4/(alpha M3)
 //   d ln sigma(d)/d grad mu = -erfc(a)/(2 sigma(d)) d,   d ln sigma(d)/d alpha = e^{-a^2}/(2 sqrt pi sigma(d))
+// A vertex with incoming d contributes W_nee d ln(F D(m_nee)/sigma(d)) + W_ph d ln(F D(m_ph)/sigma(d)):
+// the sigma(d) part is shared, weighted by W_nee + W_ph.
 #pragma once
 
 #include "gpss_device.cuh"
@@ -61,31 +63,20 @@ __device__ __forceinline__ DSig dsigma_t(const ObjectDev& o, const Field& f, V3 
   return r;
 }
 
-// d ln(D(m)/sigma(d)) with respect to grad mu, the variance and l.
-struct DPhase {
+// d ln D(m) with respect to grad mu and alpha (the variance and l act through alpha).
+struct DLogNdf {
   V3 dg;
-  float dvar, dl;
+  float dalpha;
 };
 
-static __device__ __noinline__ DPhase dlog_phase(V3 d, V3 m, Field f, float alpha_scale) {
-  const float sig = sqrtf(f.var);
-  const float alpha = sig * alpha_scale;
+static __device__ __noinline__ DLogNdf dlog_ndf(V3 m, Field f, float alpha) {
   float r4;
   ndf_iso(m, f.g, alpha, &r4);
-  const float q = dot(m, f.g) / alpha;
-  const float G2 = dot(f.g, f.g);
   const float inv_a = 1.0f / alpha;
-  V3 dg = fma3(-2.0f * inv_a * inv_a, f.g, (2.0f * r4 * inv_a) * m);
-  float dalpha = inv_a + 2.0f * G2 * inv_a * inv_a * inv_a - 2.0f * r4 * q * inv_a;
-  float ps, ec_over, ea_over;
-  psi_ratios(dot(d, f.g) * inv_a, ps, ec_over, ea_over);
-  // sigma(d) = alpha psi: d ln/d grad mu = -erfc/(2 alpha psi) d, d ln/d alpha = ea/(alpha psi)
-  dg = fma3(0.5f * ec_over * inv_a, d, dg);
-  dalpha -= ea_over * inv_a;
-  DPhase r;
-  r.dg = dg;
-  r.dvar = dalpha * alpha / (2.0f * f.var);
-  r.dl = -dalpha * alpha * (alpha_scale * kInvSqrt2);
+  const float q = dot(m, f.g) * inv_a;
+  DLogNdf r;
+  r.dg = fma3(-2.0f * inv_a * inv_a, f.g, (2.0f * r4 * inv_a) * m);
+  r.dalpha = inv_a + 2.0f * dot(f.g, f.g) * inv_a * inv_a * inv_a - 2.0f * r4 * q * inv_a;
   return r;
 }
 

@@ -16,8 +16,8 @@
 // Execution model: one persistent thread per resident lane.  Each iteration of the
 // main loop advances every active lane by ONE tentative collision of its current
 // ray (free-flight or shadow ray), so the lanes of a warp run the same traversal +
-// extinction code together.  Lanes that reach a real vertex (or, in the adjoint, a
-// vertex whose gradient is due) wait; the warp serves its waiting lanes together
+// extinction code together.  Lanes that reach a real vertex wait; the warp serves
+// its waiting lanes together
 // once at least `shade_min` of them wait or no lane can step, so the long shading
 // code runs with many lanes active.  Shading code and the Philox block are out of
 // line, keeping the traversal loop small in the instruction cache.  A finished
@@ -39,7 +39,8 @@
 //     the ray's final transmittance, recorded per vertex by the forward render;
 //   - vertex: d ln(F D(m_L)/sigma(d)) with weight <g, C_k> (C_k = pend T) and
 //     d ln(F D(m)/sigma(d)) of the sampled direction with weight <g, radiance after
-//     the vertex's NEE>;
+//     the vertex's NEE>, both known when the vertex is shaded (T is the forward's),
+//     so the vertex gradient is taken in the shading step;
 // where g = dLoss/dpixel / spp.  Each evaluation scatters to the 8 grid nodes it
 // interpolates (float atomics); the length-scale gradient is reduced per warp.
 #pragma once
@@ -120,33 +121,46 @@ __device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, co
   return k * ds.dl;
 }
 
-// Adjoint: gradient of the vertex factors at x (incoming direction d_in).
+// Adjoint: gradient of the vertex factors at x (incoming direction d_in): the NEE
+// factor F D(m_nee)/sigma(d_in) with weight Wnee and the sampled direction's factor
+// F D(m_ph)/sigma(d_in) with weight Wph (the sigma(d_in) part is shared).
 static __device__ __noinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, V3 wl, V3 d_next, float Wnee,
                                                 float Wph, V3 albedo_coef, const AdjOut A) {
   const Field f = fetch(ob, x);
+  const float sig = sqrtf(f.var);
+  const float alpha = sig * ob.alpha_scale;
   V3 cg = v3(0, 0, 0);
-  float cvar = 0.0f, dl = 0.0f;
+  float dalpha = 0.0f;
   if (Wnee != 0.0f) {
-    const DPhase dp = dlog_phase(d_in, normalize(wl - d_in), f, ob.alpha_scale);
-    cg = fma3(Wnee, dp.dg, cg);
-    cvar += Wnee * dp.dvar;
-    dl += Wnee * dp.dl;
+    const DLogNdf dn = dlog_ndf(normalize(wl - d_in), f, alpha);
+    cg = fma3(Wnee, dn.dg, cg);
+    dalpha = fmaf(Wnee, dn.dalpha, dalpha);
   }
   if (Wph != 0.0f) {
-    const DPhase dp = dlog_phase(d_in, normalize(d_next - d_in), f, ob.alpha_scale);
-    cg = fma3(Wph, dp.dg, cg);
-    cvar += Wph * dp.dvar;
-    dl += Wph * dp.dl;
+    const DLogNdf dn = dlog_ndf(normalize(d_next - d_in), f, alpha);
+    cg = fma3(Wph, dn.dg, cg);
+    dalpha = fmaf(Wph, dn.dalpha, dalpha);
   }
+  const float W = Wnee + Wph;
+  if (W != 0.0f) {
+    // -W d ln sigma(d_in): sigma(d) = alpha psi(a), d ln/d grad mu = -erfc(a)/(2 alpha psi) d,
+    // d ln/d alpha = e^{-a^2}/(2 sqrt(pi) alpha psi)
+    const float inv_a = 1.0f / alpha;
+    float ps, ec_over, ea_over;
+    psi_ratios(dot(d_in, f.g) * inv_a, ps, ec_over, ea_over);
+    cg = fma3(W * 0.5f * ec_over * inv_a, d_in, cg);
+    dalpha = fmaf(-W, ea_over * inv_a, dalpha);
+  }
+  const float cvar = dalpha * alpha / (2.0f * f.var);
   if (A.d_mv && (Wnee != 0.0f || Wph != 0.0f)) scatter_field(ob, x, 0.0f, cg, cvar, A.d_mv);
   if (A.d_alb && (albedo_coef.x != 0.0f || albedo_coef.y != 0.0f || albedo_coef.z != 0.0f))
     scatter_albedo(ob, x, albedo_coef, A.d_alb);
-  return dl;
+  return -dalpha * alpha * (ob.alpha_scale * kInvSqrt2);  // d/dl through alpha = sqrt2 sigma/l
 }
 
 // ---------------------------------------------------------------- per-lane path state
 struct Lane {
-  bool active, waiting, begin, vgrad, cont, walk_ok;
+  bool active, waiting, begin, cont, walk_ok;
   long long pidx;
   uint32_t pixel;
   int job;
@@ -157,7 +171,7 @@ struct Lane {
   uint32_t events;
   Walk w;
   // adjoint state
-  V3 Ltot, gpix, d_in;
+  V3 Ltot, gpix;
   float Tfin;
 };
 
@@ -168,7 +182,7 @@ struct LaneCounters {
 };
 
 __device__ __forceinline__ void lane_init(Lane& s) {
-  s.active = s.waiting = s.begin = s.vgrad = s.cont = s.walk_ok = false;
+  s.active = s.waiting = s.begin = s.cont = s.walk_ok = false;
   s.pidx = 0;
   s.pixel = 0;
   s.job = 0;
@@ -186,7 +200,6 @@ __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const Pa
     s.gpix = v3(A.d_image[3 * s.pixel] * P.inv_spp, A.d_image[3 * s.pixel + 1] * P.inv_spp,
                 A.d_image[3 * s.pixel + 2] * P.inv_spp);
     s.Ltot = v3(A.L_path[3 * pidx], A.L_path[3 * pidx + 1], A.L_path[3 * pidx + 2]);
-    s.vgrad = false;
     if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) return false;
   }
   s.rng.init(P.seed, s.pixel, (uint32_t)sample);
@@ -204,35 +217,6 @@ __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const Pa
   s.waiting = false;
   s.active = true;
   return true;
-}
-
-// Adjoint: the vertex gradient of the last real vertex, then the continuation.
-__device__ __forceinline__ void lane_vertex_grad(Lane& s, const SceneDev& S, const AdjOut& A, LaneCounters& c) {
-  s.vgrad = false;
-  const ObjectDev& ob = S.obj[0];
-  const V3 Ck = v3(s.pend.x * s.Tfin, s.pend.y * s.Tfin, s.pend.z * s.Tfin);
-  const V3 after = s.Ltot - s.L - Ck;
-  const V3 F = fetch_albedo(ob, s.o);
-  const float Wnee = dot(s.gpix, Ck);
-  const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
-  const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
-                   F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
-                   F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
-  c.acc_l += adj_vertex(ob, s.o, s.d_in, s.d, s.d_next, Wnee, Wph, ac, A);
-  s.L = s.L + Ck;
-  if (s.cont) {
-    s.mode = kFlight;
-    s.d = s.d_next;
-    s.beta = s.beta_next;
-    s.prev_pdf = s.pdf_next;
-    s.rng.start((uint32_t)s.bounce, kPurposeFlight);
-    s.begin = true;
-  } else {
-    s.walk_ok = false;  // treated below as an escaped flight that adds nothing
-    s.mode = kFlight;
-    s.begin = false;
-    s.beta = v3(0.0f, 0.0f, 0.0f);
-  }
 }
 
 // Shading of a real vertex: phase sampling, next-event estimation setup.
@@ -286,8 +270,18 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   const float scale = pe.p_over_F * lw;
   s.pend = v3(s.beta.x * F.x * scale * Le.x, s.beta.y * F.y * scale * Le.y, s.beta.z * F.z * scale * Le.z);
   if constexpr (ADJ) {
-    s.d_in = s.d;
+    // the vertex's gradient, now: its NEE contribution C = pend T (T = the forward's
+    // final shadow transmittance) and the radiance after it are already known
     s.Tfin = scale > 0.0f ? A.T_path[(size_t)s.pidx * P.max_bounces + s.bounce] : 0.0f;
+    const V3 Ck = v3(s.pend.x * s.Tfin, s.pend.y * s.Tfin, s.pend.z * s.Tfin);
+    const V3 after = s.Ltot - s.L - Ck;
+    const float Wnee = dot(s.gpix, Ck);
+    const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
+    const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
+                     F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
+                     F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
+    c.acc_l += adj_vertex(S.obj[0], x, s.d, wl, s.d_next, Wnee, Wph, ac, A);
+    s.L = s.L + Ck;
   } else {
     if (path_T && !(scale > 0.0f)) path_T[(size_t)s.pidx * P.max_bounces + s.bounce] = 0.0f;
   }
@@ -297,9 +291,6 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     s.d = wl;
     s.T = 1.0f;
     s.begin = true;
-  } else if (ADJ) {
-    s.d = wl;
-    s.vgrad = true;  // the vertex's phase-sampling factor still has a gradient
   } else if (s.cont) {
     s.mode = kFlight;
     s.d = s.d_next;
@@ -384,11 +375,12 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
         s.L = v3(fmaf(s.beta.x * Le.x, wm, s.L.x), fmaf(s.beta.y * Le.y, wm, s.L.y), fmaf(s.beta.z * Le.z, wm, s.L.z));
       }
       finish = true;
-    } else if (ADJ) {
-      s.vgrad = true;  // shadow ray done: the vertex gradient is due
     } else {
-      s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
-      if (path_T) path_T[(size_t)s.pidx * P.max_bounces + (s.bounce - 1)] = s.T;
+      // shadow ray done (the adjoint added the vertex's contribution when shading it)
+      if constexpr (!ADJ) {
+        s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
+        if (path_T) path_T[(size_t)s.pidx * P.max_bounces + (s.bounce - 1)] = s.T;
+      }
       if (s.cont) {
         s.mode = kFlight;
         s.d = s.d_next;
@@ -509,14 +501,11 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
       if (wc.exhausted || wc.next >= P.total) break;
       continue;
     }
-    const unsigned wait_mask = __ballot_sync(FULL, s.waiting || s.vgrad);
+    const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
     if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act)) {
-      if constexpr (ADJ) {
-        if (s.vgrad) lane_vertex_grad(s, S, A, c);
-      }
       if (s.waiting) lane_shade<ADJ>(s, S, P, A, path_T, c);
     }
-    if (!s.active || s.waiting || s.vgrad) continue;
+    if (!s.active || s.waiting) continue;
     if (lane_step<ADJ, LOCAL>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
   }
   flush_counters(c, counters, ADJ ? A.d_l : nullptr);
