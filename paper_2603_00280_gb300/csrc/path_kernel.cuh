@@ -17,9 +17,8 @@
 // main loop advances every active lane by ONE tentative collision of its current
 // ray (free-flight or shadow ray), so the lanes of a warp run the same traversal +
 // extinction code together.  Lanes that reach a real vertex wait; the warp serves
-// its waiting lanes together
-// once at least `shade_min` of them wait or no lane can step, so the long shading
-// code runs with many lanes active.  Shading code and the Philox block are out of
+// its waiting lanes together once at least `shade_min` of them wait or no lane can
+// step, so the long shading code runs with many lanes active.  Shading code and the Philox block are out of
 // line, keeping the traversal loop small in the instruction cache.  A finished
 // lane takes the next (sample, pixel) index from a warp-private chunk of the
 // global work cursor (one atomic per chunk; ranks from __ballot_sync/__popc).  Path
