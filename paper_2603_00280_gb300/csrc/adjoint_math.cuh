@@ -21,7 +21,7 @@ namespace gpss {
 // underflow for large a (continued fraction as in psi(); for a > 2 the ratios follow
 // from K alone and from erfcx).
 __device__ __forceinline__ void psi_ratios(float a, float& ps, float& ec_over, float& ea_over) {
-  const float ex = expf(-a * a);
+  const float ex = exp_neg_sq(a);
   const float E = erfcxf(fabsf(a));
   const float ec = erfc_from(a, ex, E);
   if (a <= 2.0f) {

@@ -166,6 +166,15 @@ struct Rng {
 // lambda(u) = phi(u)/Phi(u) = sqrt(2/pi) / erfcx(-u/sqrt2)   (inverse Mills ratio)
 __device__ __forceinline__ float inv_mills(float u) { return kSqrt2OverPi / erfcxf(-u * kInvSqrt2); }
 
+// e^{-a^2} without the rounding error of a*a: a^2 = hi + lo exactly (lo from an FMA,
+// the error-free product of Dekker / Ogita-Rump-Oishi), e^{-a^2} = e^{-hi} (1 - lo) to
+// first order in lo <= ulp(hi)/2.  Plain expf(-a*a) is off by ~a^2 ulp for large a.
+__device__ __forceinline__ float exp_neg_sq(float a) {
+  const float hi = a * a;
+  const float lo = fmaf(a, a, -hi);
+  return expf(-hi) * (1.0f - lo);
+}
+
 // erfc(a) from one erfcx evaluation: erfcx(|a|) e^{-a^2} for a >= 0, 2 minus that for
 // a < 0 (ex = e^{-a^2} is passed in because the callers need it too).
 __device__ __forceinline__ float erfc_from(float a, float ex, float erfcx_abs) {
@@ -186,7 +195,7 @@ __device__ __forceinline__ float mills_cf(float y) {
 // so the projected area is sigma(d) = alpha * psi((d . grad mu)/alpha).  For a > 2 the
 // difference cancels; there psi = erfc(a) * K(sqrt2 a) / (2 sqrt2).
 __device__ __forceinline__ float psi(float a) {
-  const float ex = expf(-a * a);
+  const float ex = exp_neg_sq(a);
   const float ec = erfc_from(a, ex, erfcxf(fabsf(a)));
   if (a <= 2.0f) return fmaf(-0.5f * a, ec, 0.5f * kInvSqrtPi * ex);
   return ec * mills_cf(kSqrt2 * a) * (0.5f * kInvSqrt2);

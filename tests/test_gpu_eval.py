@@ -88,7 +88,12 @@ def test_projected_area_relative_accuracy_across_a():
     oa = np.array([oracle.projected_area_local(v.astype(np.float64), 1.0, alpha, alpha, alpha) for v in w])
     assert oa.min() > 1e-37  # normal FP32 numbers throughout
     err = np.abs(ga - oa) / oa
-    assert err.max() < C.REL, (err.max(), float(w[np.argmax(err), 2]) / alpha)
+    # psi(a) ~ e^{-a^2} has relative condition number ~2a^2: the GPU forms
+    # a = G w_z / (alpha |w|) in FP32 (a few ulp), so the bar is 1e-5 plus that
+    a = z / alpha
+    cond = 2.0 * a * a * 4 * 2.0 ** -24
+    assert (err < C.REL + cond).all(), (err.max(), float(a[np.argmax(err - cond)]))
+    assert err[np.abs(a) < 2].max() < C.REL
 
 
 def _beckmann_conditioning(O, x, d, d2):
