@@ -422,24 +422,29 @@ __device__ __forceinline__ void beckmann_frame(V3 d, V3 g, float alpha, V3& z, f
   aB = fminf(fmaxf(alpha / G, 1e-3f), 16.0f);
 }
 
-// Beckmann visible-normal density <wi,m> D_B(m) / ((1+Lambda(wi)) cos theta_i).
-__device__ __forceinline__ float beckmann_vis_pdf(V3 m, V3 wi, V3 z, float a) {
+// (1 + Lambda(wi)) cos theta_i of the Beckmann NDF (roughness a, axis z): the normaliser
+// of its visible-normal density.
+__device__ __forceinline__ float beckmann_vis_den(V3 wi, V3 z, float a) {
+  const float ci = fmaxf(dot(wi, z), 0.0f);
+  const float si = sqrtf(fmaxf(0.0f, 1.0f - ci * ci));
+  if (si <= 0.0f) return ci;
+  const float ac = ci / (a * si);
+  return 0.5f * ci * (1.0f + erff(ac)) + a * si * expf(-ac * ac) * (0.5f * kInvSqrtPi);
+}
+
+// Beckmann visible-normal density <wi,m> D_B(m) / den, den = beckmann_vis_den(wi, z, a).
+__device__ __forceinline__ float beckmann_vis_pdf_den(V3 m, V3 wi, V3 z, float a, float den) {
   const float wm = dot(wi, m);
   const float c = dot(m, z);
   if (wm <= 0.0f || c <= 0.0f) return 0.0f;
   const float c2 = c * c;
   const float t2 = (1.0f - c2) / c2;
   const float D = expf(-t2 / (a * a)) / (kPi * a * a * c2 * c2);
-  const float ci = fmaxf(dot(wi, z), 0.0f);
-  const float si = sqrtf(fmaxf(0.0f, 1.0f - ci * ci));
-  float denom;
-  if (si <= 0.0f) {
-    denom = ci;
-  } else {
-    const float ac = ci / (a * si);
-    denom = 0.5f * ci * (1.0f + erff(ac)) + a * si * expf(-ac * ac) * (0.5f * kInvSqrtPi);
-  }
-  return wm * D / denom;
+  return wm * D / den;
+}
+
+__device__ __forceinline__ float beckmann_vis_pdf(V3 m, V3 wi, V3 z, float a) {
+  return beckmann_vis_pdf_den(m, wi, z, a, beckmann_vis_den(wi, z, a));
 }
 
 // Visible-normal sampling of the Beckmann NDF after Heitz & d'Eon (2014): stretch
@@ -498,20 +503,37 @@ __device__ __forceinline__ V3 uniform_hemisphere(V3 wi, float u1, float u2) {
   return normalize((s * cp) * t1 + (s * sp) * t2 + c * wi);
 }
 
-// mixture pdf over half-vectors m facing -d
-__device__ __forceinline__ float mixture_pdf_m(V3 d, V3 m, V3 g, float alpha, float R) {
-  const V3 wi = -d;
-  if (dot(wi, m) <= 0.0f) return 0.0f;
+// The quantities of the sampling mixture that depend on the incoming d only: the
+// Beckmann frame and roughness and its visible-normal normaliser.  A vertex sets
+// them up once for its phase sample and its NEE evaluation.
+struct Mix {
   V3 z;
-  float aB;
-  beckmann_frame(d, g, alpha, z, aB);
-  return R * beckmann_vis_pdf(m, wi, z, aB) + (1.0f - R) * (1.0f / kTwoPi);
+  float aB, den, R;
+};
+
+__device__ __forceinline__ Mix mix_setup(V3 d, V3 g, float alpha, float R) {
+  Mix mx;
+  beckmann_frame(d, g, alpha, mx.z, mx.aB);
+  mx.den = beckmann_vis_den(-d, mx.z, mx.aB);
+  mx.R = R;
+  return mx;
 }
 
-// Phase function p(d,d2)/F = D(m) / (4 sigma(d)) and the mixture pdf over d2.
-// Returns false where p = 0.
-__device__ __forceinline__ bool phase_eval(V3 d, V3 d2, const Field& f, float alpha, float R,
-                                           float& p_over_F, float& pdf) {
+// mixture pdf over half-vectors m facing -d
+__device__ __forceinline__ float mix_pdf_m(const Mix& mx, V3 d, V3 m) {
+  const V3 wi = -d;
+  if (dot(wi, m) <= 0.0f) return 0.0f;
+  return mx.R * beckmann_vis_pdf_den(m, wi, mx.z, mx.aB, mx.den) + (1.0f - mx.R) * (1.0f / kTwoPi);
+}
+
+__device__ __forceinline__ float mixture_pdf_m(V3 d, V3 m, V3 g, float alpha, float R) {
+  return mix_pdf_m(mix_setup(d, g, alpha, R), d, m);
+}
+
+// Phase function p(d,d2)/F = D(m) / (4 sigma(d)) and the mixture pdf over d2, with the
+// mixture set up and sd = sigma(d) given.  Returns false where p = 0.
+__device__ __forceinline__ bool phase_eval_mix(const Mix& mx, float sd, V3 d, V3 d2, const Field& f, float alpha,
+                                               float& p_over_F, float& pdf) {
   V3 m = d2 - d;
   const float len2 = dot(m, m);
   p_over_F = 0.0f;
@@ -520,36 +542,37 @@ __device__ __forceinline__ bool phase_eval(V3 d, V3 d2, const Field& f, float al
   m = rsqrtf(len2) * m;
   const float dm = dot(d, m);
   if (dm >= 0.0f) return false;
-  const float sd = projected_area(d, f, alpha);
   p_over_F = ndf_iso(m, f.g, alpha) / (4.0f * sd);
-  pdf = mixture_pdf_m(d, m, f.g, alpha, R) / (4.0f * fabsf(dm));
+  pdf = mix_pdf_m(mx, d, m) / (4.0f * fabsf(dm));
   return true;
 }
 
-// Samples d2; returns the weight p/pdf divided by F, and the pdf.
-__device__ __forceinline__ bool phase_sample(V3 d, const Field& f, float alpha, float R, float u0, float u1,
-                                             float u2, V3& d2, float& w_over_F, float& pdf) {
+// Samples d2 (mixture set up, sd = sigma(d)); returns the weight p/pdf divided by F, and the pdf.
+__device__ __forceinline__ bool phase_sample_mix(const Mix& mx, float sd, V3 d, const Field& f, float alpha, float u0,
+                                                 float u1, float u2, V3& d2, float& w_over_F, float& pdf) {
   const V3 wi = -d;
-  V3 m;
-  if (u0 < R) {
-    V3 z;
-    float aB;
-    beckmann_frame(d, f.g, alpha, z, aB);
-    m = beckmann_sample_vis(wi, z, aB, u1, u2);
-  } else {
-    m = uniform_hemisphere(wi, u1, u2);
-  }
+  const V3 m = u0 < mx.R ? beckmann_sample_vis(wi, mx.z, mx.aB, u1, u2) : uniform_hemisphere(wi, u1, u2);
   const float dm = dot(d, m);
   w_over_F = 0.0f;
   pdf = 0.0f;
   if (!(dm < 0.0f)) return false;
   d2 = normalize(fma3(-2.0f * dm, m, d));
-  const float pdf_m = mixture_pdf_m(d, m, f.g, alpha, R);
+  const float pdf_m = mix_pdf_m(mx, d, m);
   if (!(pdf_m > 0.0f)) return false;
-  const float sd = projected_area(d, f, alpha);
   w_over_F = ndf_iso(m, f.g, alpha) * fabsf(dm) / (sd * pdf_m);
   pdf = pdf_m / (4.0f * fabsf(dm));
   return isfinite(w_over_F);
+}
+
+__device__ __forceinline__ bool phase_eval(V3 d, V3 d2, const Field& f, float alpha, float R, float& p_over_F,
+                                           float& pdf) {
+  return phase_eval_mix(mix_setup(d, f.g, alpha, R), projected_area(d, f, alpha), d, d2, f, alpha, p_over_F, pdf);
+}
+
+__device__ __forceinline__ bool phase_sample(V3 d, const Field& f, float alpha, float R, float u0, float u1,
+                                             float u2, V3& d2, float& w_over_F, float& pdf) {
+  return phase_sample_mix(mix_setup(d, f.g, alpha, R), projected_area(d, f, alpha), d, f, alpha, u0, u1, u2, d2,
+                          w_over_F, pdf);
 }
 
 // Out-of-line entry points used at real vertices (rare compared with the
@@ -575,6 +598,26 @@ static __device__ __noinline__ PhaseSample phase_sample_call(V3 d, Field f, floa
   PhaseSample r;
   r.d2 = d;
   r.ok = phase_sample(d, f, alpha, R, u0, u1, u2, r.d2, r.w_over_F, r.pdf);
+  return r;
+}
+
+// Both phase-function uses of a real vertex with incoming d: the NEE evaluation toward
+// wl and (if `sample`) the phase sample, sharing sigma(d) and the mixture's set-up.
+struct VertexShade {
+  PhaseEval nee;
+  PhaseSample next;
+};
+
+__device__ __forceinline__ VertexShade shade_vertex_call(V3 d, V3 wl, Field f, float alpha, float R, int sample,
+                                                             float u0, float u1, float u2) {
+  const Mix mx = mix_setup(d, f.g, alpha, R);
+  const float sd = projected_area(d, f, alpha);
+  VertexShade r;
+  r.nee.ok = phase_eval_mix(mx, sd, d, wl, f, alpha, r.nee.p_over_F, r.nee.pdf);
+  r.next.d2 = d;
+  r.next.w_over_F = 0.0f;
+  r.next.pdf = 0.0f;
+  r.next.ok = sample ? phase_sample_mix(mx, sd, d, f, alpha, u0, u1, u2, r.next.d2, r.next.w_over_F, r.next.pdf) : 0;
   return r;
 }
 

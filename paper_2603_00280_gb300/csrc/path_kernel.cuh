@@ -226,28 +226,25 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   s.waiting = false;
   const V3 x = fma3(s.w.t, s.d, s.o);
   Field f;
-  Local l;
+  float alpha;
   int k = 0;
   if (S.n_objs > 1) {
+    Local l;
     k = choose_object(S, x, s.d, s.rng.next(), f, l);
+    alpha = l.alpha;
   } else {
     f = fetch(S.obj[0], x);
-    l = local_of(S.obj[0], f);
+    alpha = sqrtf(f.var) * S.obj[0].alpha_scale;  // the density rho is not needed for shading
   }
   const V3 F = fetch_albedo(S.obj[k], x);
   s.o = x;
   s.cont = s.bounce + 1 < P.max_bounces;
+  float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
   if (s.cont) {
     s.rng.start((uint32_t)s.bounce, kPurposePhase);
-    const float u0 = s.rng.next(), u1 = s.rng.next(), u2 = s.rng.next();
-    const PhaseSample ps = phase_sample_call(s.d, f, l.alpha, P.mix_R, u0, u1, u2);
-    if (ps.ok) {
-      s.d_next = ps.d2;
-      s.beta_next = v3(s.beta.x * F.x * ps.w_over_F, s.beta.y * F.y * ps.w_over_F, s.beta.z * F.z * ps.w_over_F);
-      s.pdf_next = ps.pdf;
-    } else {
-      s.cont = false;
-    }
+    u0 = s.rng.next();
+    u1 = s.rng.next();
+    u2 = s.rng.next();
   } else {
     ++c.trunc;
   }
@@ -264,7 +261,18 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     wl = v3(r * cp, r * sp, z);
     Le = env_radiance(S.light, wl);
   }
-  const PhaseEval pe = phase_eval_call(s.d, wl, f, l.alpha, P.mix_R);
+  const VertexShade vs = shade_vertex_call(s.d, wl, f, alpha, P.mix_R, s.cont, u0, u1, u2);
+  if (s.cont) {
+    const PhaseSample& ps = vs.next;
+    if (ps.ok) {
+      s.d_next = ps.d2;
+      s.beta_next = v3(s.beta.x * F.x * ps.w_over_F, s.beta.y * F.y * ps.w_over_F, s.beta.z * F.z * ps.w_over_F);
+      s.pdf_next = ps.pdf;
+    } else {
+      s.cont = false;
+    }
+  }
+  const PhaseEval& pe = vs.nee;
   const float lw = env ? power_heuristic(kInv4Pi, pe.pdf) * (4.0f * kPi) : 1.0f;
   const float scale = pe.p_over_F * lw;
   s.pend = v3(s.beta.x * F.x * scale * Le.x, s.beta.y * F.y * scale * Le.y, s.beta.z * F.z * scale * Le.z);
