@@ -123,7 +123,7 @@ __device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, co
 // Adjoint: gradient of the vertex factors at x (incoming direction d_in): the NEE
 // factor F D(m_nee)/sigma(d_in) with weight Wnee and the sampled direction's factor
 // F D(m_ph)/sigma(d_in) with weight Wph (the sigma(d_in) part is shared).
-static __device__ __noinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, V3 wl, V3 d_next, float Wnee,
+__device__ __forceinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, V3 wl, V3 d_next, float Wnee,
                                                 float Wph, V3 albedo_coef, const AdjOut A) {
   const Field f = fetch(ob, x);
   const float sig = sqrtf(f.var);
