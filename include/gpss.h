@@ -92,6 +92,11 @@ typedef struct {
 
 /* flags */
 #define GPSS_FLAG_KEEP_PATH_RADIANCE 1u /* keep per-path radiance for a later adjoint */
+/* Sample the phase function exactly from the GPSS visible-normal distribution
+ * max(0,-d.m) D(m)/sigma(d) (slope g ~ max(0,-d.g) N(grad mu, (sigma/l)^2 I),
+ * m = g/|g|): weight p/pdf = F exactly, pdf = p/F.  The paper leaves this sampling
+ * open (end of Sec. 4.2) and uses the Beckmann/uniform mixture, the default. */
+#define GPSS_FLAG_EXACT_VNDF 2u
 
 typedef struct {
   int spp;                 /* samples per pixel, >= 1                               */
@@ -203,7 +208,7 @@ gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss
  *
  *   scenes, cams, opts: n entries each (copied; the scenes must stay alive and
  *     unchanged in layout while the batch exists, and live on the current device;
- *     a scene may appear several times).  opts[i].flags must be 0.
+ *     a scene may appear several times).  opts[i].flags: 0 or GPSS_FLAG_EXACT_VNDF.
  *   n: 1..4096.
  *   block_size: 0 = autotune: block size (64/128/256 threads) x shading threshold
  *     x chunk size, each candidate timed on this batch with its spp reduced so
@@ -241,6 +246,11 @@ gpss_status gpss_batch_destroy(gpss_batch b);
  * entries (org3, dir3: n*3; dir unit length). */
 gpss_status gpss_eval_local_majorant(gpss_scene s, int n, const float* org3, const float* dir3, const float* t0,
                                      const float* t_max, float* t_end, float* sbar, gpss_stream stream);
+/* Exact visible-normal sample of object k's phase function at x (see
+ * GPSS_FLAG_EXACT_VNDF): uniforms u3 (n*3) -> d_out3 (n*3), w3_out = F per channel
+ * (n*3; zero where no sample), pdf_out = p/F over d_out (n). */
+gpss_status gpss_sample_phase_vndf(gpss_scene s, int object, int n, const float* pos3, const float* d_in3,
+                                   const float* u3, float* d_out3, float* w3_out, float* pdf_out, gpss_stream stream);
 /* sigma_t(x, d) summed over objects (Eq. generalized_sigma_t); pos3, dir3: n*3. */
 gpss_status gpss_eval_sigma_t(gpss_scene s, int n, const float* pos3, const float* dir3, float* out,
                               gpss_stream stream);

@@ -17,12 +17,13 @@ uint64_t path_fingerprint(const gpss_camera* cam, const gpss_render_opts* o, uin
     for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
   };
   gpss_render_opts oo = *o;
-  oo.flags = 0;
+  oo.flags &= ~GPSS_FLAG_KEEP_PATH_RADIANCE;
   mix(cam, sizeof(*cam));
   mix(&oo.spp, sizeof(oo.spp));
   mix(&oo.max_bounces, sizeof(oo.max_bounces));
   mix(&oo.seed, sizeof(oo.seed));
   mix(&oo.mix_R, sizeof(oo.mix_R));
+  mix(&oo.flags, sizeof(oo.flags));
   mix(&scene_version, sizeof(scene_version));
   return h | 1ull;
 }
@@ -110,6 +111,7 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   P.total = total;
   P.inv_spp = 1.0f / (float)opts->spp;
   P.shade_min = s->shade_min;
+  P.exact_vndf = (opts->flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
   AdjOut A;
   A.d_image = d_image;
   A.L_path = s->path_radiance;

@@ -354,7 +354,11 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
       return GPSS_ERR_UNSUPPORTED;
     }
     if ((st = check_opts(&opts[i])) != GPSS_OK) { free_batch(b); return st; }
-    if (opts[i].flags != 0) { set_error("batch job %d: flags must be 0", i); free_batch(b); return GPSS_ERR_INVALID_ARG; }
+    if (opts[i].flags & ~GPSS_FLAG_EXACT_VNDF) {
+      set_error("batch job %d: only GPSS_FLAG_EXACT_VNDF is accepted in a batch", i);
+      free_batch(b);
+      return GPSS_ERR_INVALID_ARG;
+    }
     if (!camera_dev(&cams[i], &b->cams[i])) { free_batch(b); return GPSS_ERR_INVALID_ARG; }
     if (scene_dev(scenes[i]).mg.hot > 0.0f) b->local = true;
     PathArgs& P = b->args[i];
@@ -366,6 +370,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
     P.total = (long long)P.npix * P.spp;
     P.inv_spp = 1.0f / (float)P.spp;
     P.shade_min = kBatchDefaultShade;
+    P.exact_vndf = (opts[i].flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
     b->begins[i + 1] = b->begins[i] + P.total;
   }
   b->total = b->begins[n];

@@ -132,6 +132,7 @@ gpss_status check_opts(const gpss_render_opts* o) {
   if (o->spp < 1) { set_error("spp must be >= 1"); return GPSS_ERR_INVALID_ARG; }
   if (o->max_bounces < 1 || o->max_bounces > 65535) { set_error("max_bounces must be in [1, 65535]"); return GPSS_ERR_INVALID_ARG; }
   if (!(o->mix_R > 0.0f && o->mix_R < 1.0f)) { set_error("mix_R must lie in (0,1)"); return GPSS_ERR_INVALID_ARG; }
+  if (o->flags & ~(GPSS_FLAG_KEEP_PATH_RADIANCE | GPSS_FLAG_EXACT_VNDF)) { set_error("unknown flags"); return GPSS_ERR_INVALID_ARG; }
   return GPSS_OK;
 }
 

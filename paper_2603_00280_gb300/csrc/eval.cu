@@ -46,6 +46,28 @@ __global__ void k_eval_phase(const SceneDev S, int k, int n, const float* pos, c
   pdf[i] = pd;
 }
 
+__global__ void k_sample_phase_vndf(const SceneDev S, int k, int n, const float* pos, const float* din,
+                                    const float* u3, float* dout, float* w3, float* pdf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const V3 x = ld3(pos, i);
+  const ObjectDev& o = S.obj[k];
+  V3 d2 = v3(0, 0, 0);
+  float wF = 0.0f, pd = 0.0f;
+  V3 F = v3(0, 0, 0);
+  if (inside(o, x)) {
+    const Field f = fetch(o, x);
+    const float alpha = sqrtf(f.var) * o.alpha_scale;
+    const V3 d = ld3(din, i);
+    const V3 u = ld3(u3, i);
+    if (!phase_sample_vndf(projected_area(d, f, alpha), d, f, alpha, u.x, u.y, u.z, d2, wF, pd)) wF = 0.0f;
+    F = fetch_albedo(o, x);
+  }
+  st3(dout, i, d2);
+  st3(w3, i, wF * F);
+  pdf[i] = pd;
+}
+
 __global__ void k_sample_phase(const SceneDev S, int k, int n, const float* pos, const float* din, const float* u3,
                                float R, float* dout, float* w3, float* pdf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -304,6 +326,18 @@ extern "C" gpss_status gpss_sample_phase(gpss_scene s, int object, int n, const 
                                                           w3_out, pdf_out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GPSS_OK : cuda_fail(e, "sample_phase");
+}
+
+extern "C" gpss_status gpss_sample_phase_vndf(gpss_scene s, int object, int n, const float* pos3,
+                                              const float* d_in3, const float* u3, float* d_out3, float* w3_out,
+                                              float* pdf_out, gpss_stream stream) {
+  if (!s || !pos3 || !d_in3 || !u3 || !d_out3 || !w3_out || !pdf_out) { set_error("null argument"); return GPSS_ERR_INVALID_ARG; }
+  if (object < 0 || object >= s->n_objs) { set_error("object index out of range"); return GPSS_ERR_INVALID_ARG; }
+  CHECK_N(n);
+  k_sample_phase_vndf<<<nb(n), 128, 0, (cudaStream_t)stream>>>(scene_dev(s), object, n, pos3, d_in3, u3, d_out3,
+                                                               w3_out, pdf_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GPSS_OK : cuda_fail(e, "sample_phase_vndf");
 }
 
 static bool positive_finite(float v) { return v > 0.0f && v < 3.0e38f; }

@@ -34,6 +34,8 @@ constexpr float kSqrt2 = 1.41421356237309504880f;
 constexpr float kInvSqrt2 = 0.70710678118654752440f;
 constexpr float kSqrt2OverPi = 0.79788456080286535588f;
 constexpr float kInvPi32 = 0.17958712212516656f;  // pi^(-3/2)
+constexpr float kSqrtPiOver2 = 1.25331413731550025121f;
+constexpr float kInvSqrt2Pi = 0.39894228040143267794f;
 
 // ---------------------------------------------------------------- layouts
 
@@ -575,6 +577,112 @@ __device__ __forceinline__ bool phase_sample(V3 d, const Field& f, float alpha, 
                           w_over_F, pdf);
 }
 
+// ---------------------------------------------------------------- exact visible-normal sampling
+// The GPSS visible-normal distribution max(0, -d.m) D(m)/sigma(d) is the direction
+// of a slope g drawn with density proportional to max(0, -d.g) N(g; grad mu, s^2 I),
+// s = alpha/sqrt2 (Eq. gdf_to_ndf: D(m) = int t^3 P(t m) dt, and dg = t^2 dt dm).  In
+// the frame of d, u = -d.g has density proportional to u N(u; -d.grad mu, s^2) on u > 0
+// and the two components orthogonal to d are independent N(grad mu_perp, s^2).  With
+// m = g/|g| and d2 = reflect(d, m) the sample's pdf is p(d,d2)/F and its weight p/pdf
+// is exactly F.  (The paper leaves this sampling open and uses the mixture above.)
+
+// Mills ratio R(x) = (1 - Phi(x))/phi(x) = sqrt(pi/2) erfcx(x/sqrt2).
+__device__ __forceinline__ float mills_ratio(float x) { return kSqrtPiOver2 * erfcxf(x * kInvSqrt2); }
+
+// q(x) = 1 - x R(x) for x >= 0, without cancellation: R(x) K(x) with Laplace's
+// continued fraction K (R = 1/(x + K)) for x >= 2.
+__device__ __forceinline__ float one_minus_x_mills(float x, float R) {
+  return x < 2.0f ? fmaf(-x, R, 1.0f) : R * mills_cf(x);
+}
+
+// Unnormalised CDF H(y) = int_0^y t phi(t - beta) dt of the visible slope y = u/s and its
+// derivative y phi(y - beta).  beta >= 0: direct form.  beta < 0 (B = -beta): both
+// scaled by 1/phi(beta), H = q(B) - E (q(y+B) + y R(y+B)), E = phi(y - beta)/phi(beta).
+__device__ __forceinline__ void visible_slope_cdf(float beta, float y, float& H, float& dH) {
+  if (beta >= 0.0f) {
+    const float t = y - beta;
+    const float pt = kInvSqrt2Pi * expf(-0.5f * t * t);
+    const float pb = kInvSqrt2Pi * expf(-0.5f * beta * beta);
+    const float Pt = 0.5f * erfcf(-t * kInvSqrt2), Pb = 0.5f * erfcf(beta * kInvSqrt2);  // Phi(t), Phi(-beta)
+    H = pb - pt + beta * (Pt - Pb);
+    dH = y * pt;
+  } else {
+    const float B = -beta;
+    const float E = expf(-y * (B + 0.5f * y));
+    const float x = y + B;
+    const float Rb = mills_ratio(B), Rx = mills_ratio(x);
+    H = one_minus_x_mills(B, Rb) - E * (one_minus_x_mills(x, Rx) + y * Rx);
+    dH = y * E;
+  }
+}
+
+// The visible slope y > 0 with density proportional to y exp(-(y - beta)^2/2) at CDF
+// value xi: Newton on H(y) = xi H(inf), safeguarded by bisection (at most 40 steps).
+__device__ __forceinline__ float sample_visible_slope(float beta, float xi) {
+  float Z;
+  if (beta >= 0.0f) {
+    Z = beta * 0.5f * erfcf(-beta * kInvSqrt2) + kInvSqrt2Pi * expf(-0.5f * beta * beta);
+  } else {
+    Z = one_minus_x_mills(-beta, mills_ratio(-beta));
+  }
+  const float target = xi * Z;
+  float lo = 0.0f, hi;
+  float y;
+  if (beta >= 0.0f) {
+    hi = beta + 9.0f;
+    y = fmaxf(beta + kSqrt2 * erfinvf(fminf(fmaxf(2.0f * xi - 1.0f, -0.999999f), 0.999999f)), 0.5f * beta);
+  } else {
+    // about Gamma(2, B) for large B: mean 2/B
+    hi = 9.0f + 40.0f / (1.0f - beta);
+    y = 2.0f * xi / (0.5f - beta);
+  }
+  y = fminf(fmaxf(y, 1e-7f), hi);
+#pragma unroll 1
+  for (int it = 0; it < 40; ++it) {
+    float H, dH;
+    visible_slope_cdf(beta, y, H, dH);
+    const float f = H - target;
+    if (f > 0.0f) hi = y; else lo = y;
+    if (fabsf(f) <= 1e-6f * Z || hi - lo <= 1e-7f * (1.0f + y)) break;
+    float yn = dH > 0.0f ? y - f / dH : 0.5f * (lo + hi);
+    if (!(yn > lo && yn < hi)) yn = 0.5f * (lo + hi);
+    y = yn;
+  }
+  return y;
+}
+
+// Exact visible-normal sample (uniforms u0: slope along -d, u1, u2: the orthogonal
+// slopes).  Returns false for the measure-zero case g = 0.
+__device__ __forceinline__ bool vndf_sample_exact(V3 d, V3 g, float alpha, float u0, float u1, float u2, V3& m) {
+  const float s = alpha * kInvSqrt2;
+  const float beta = -dot(d, g) / s;
+  const float y = sample_visible_slope(beta, u0);
+  V3 t1, t2;
+  onb(d, t1, t2);
+  const float n1 = kSqrt2 * erfinvf(fminf(fmaxf(2.0f * u1 - 1.0f, -0.99999994f), 0.99999994f));
+  const float n2 = kSqrt2 * erfinvf(fminf(fmaxf(2.0f * u2 - 1.0f, -0.99999994f), 0.99999994f));
+  const V3 gs = fma3(-s * y, d, fma3(fmaf(s, n1, dot(g, t1)), t1, fmaf(s, n2, dot(g, t2)) * t2));
+  const float len2 = dot(gs, gs);
+  if (!(len2 > 0.0f)) return false;
+  m = rsqrtf(len2) * gs;
+  return true;
+}
+
+// Exact-vNDF counterpart of phase_sample_mix: weight p/pdf/F = 1, pdf = p/F.
+__device__ __forceinline__ bool phase_sample_vndf(float sd, V3 d, const Field& f, float alpha, float u0, float u1,
+                                                  float u2, V3& d2, float& w_over_F, float& pdf) {
+  V3 m;
+  w_over_F = 0.0f;
+  pdf = 0.0f;
+  if (!vndf_sample_exact(d, f.g, alpha, u0, u1, u2, m)) return false;
+  const float dm = dot(d, m);
+  if (!(dm < 0.0f)) return false;
+  d2 = normalize(fma3(-2.0f * dm, m, d));
+  pdf = ndf_iso(m, f.g, alpha) / (4.0f * sd);
+  w_over_F = 1.0f;
+  return pdf > 0.0f && isfinite(pdf);
+}
+
 // Out-of-line entry points used at real vertices (rare compared with the
 // extinction evaluations of the traversal loop); results are returned by value.
 struct PhaseEval {
@@ -608,15 +716,34 @@ struct VertexShade {
   PhaseSample next;
 };
 
+// exact = true: the exact visible-normal sampler (its pdf is p/F, also for the NEE
+// direction's MIS weight) instead of the mixture.
 __device__ __forceinline__ VertexShade shade_vertex_call(V3 d, V3 wl, Field f, float alpha, float R, int sample,
-                                                             float u0, float u1, float u2) {
-  const Mix mx = mix_setup(d, f.g, alpha, R);
+                                                         bool exact, float u0, float u1, float u2) {
   const float sd = projected_area(d, f, alpha);
   VertexShade r;
-  r.nee.ok = phase_eval_mix(mx, sd, d, wl, f, alpha, r.nee.p_over_F, r.nee.pdf);
   r.next.d2 = d;
   r.next.w_over_F = 0.0f;
   r.next.pdf = 0.0f;
+  if (exact) {
+    V3 m = wl - d;
+    const float len2 = dot(m, m);
+    r.nee.ok = 0;
+    r.nee.p_over_F = 0.0f;
+    r.nee.pdf = 0.0f;
+    if (len2 > 0.0f) {
+      m = rsqrtf(len2) * m;
+      if (dot(d, m) < 0.0f) {
+        r.nee.p_over_F = ndf_iso(m, f.g, alpha) / (4.0f * sd);
+        r.nee.pdf = r.nee.p_over_F;
+        r.nee.ok = 1;
+      }
+    }
+    r.next.ok = sample ? phase_sample_vndf(sd, d, f, alpha, u0, u1, u2, r.next.d2, r.next.w_over_F, r.next.pdf) : 0;
+    return r;
+  }
+  const Mix mx = mix_setup(d, f.g, alpha, R);
+  r.nee.ok = phase_eval_mix(mx, sd, d, wl, f, alpha, r.nee.p_over_F, r.nee.pdf);
   r.next.ok = sample ? phase_sample_mix(mx, sd, d, f, alpha, u0, u1, u2, r.next.d2, r.next.w_over_F, r.next.pdf) : 0;
   return r;
 }

@@ -61,6 +61,7 @@ struct PathArgs {
   long long total;
   float inv_spp;
   int shade_min;
+  int exact_vndf;  // sample the phase function with the exact visible-normal sampler
 };
 
 struct AdjOut {
@@ -261,7 +262,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     wl = v3(r * cp, r * sp, z);
     Le = env_radiance(S.light, wl);
   }
-  const VertexShade vs = shade_vertex_call(s.d, wl, f, alpha, P.mix_R, s.cont, u0, u1, u2);
+  const VertexShade vs = shade_vertex_call(s.d, wl, f, alpha, P.mix_R, s.cont, P.exact_vndf != 0, u0, u1, u2);
   if (s.cont) {
     const PhaseSample& ps = vs.next;
     if (ps.ok) {

@@ -26,6 +26,7 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   P.total = (long long)P.npix * o.spp;
   P.inv_spp = 1.0f / (float)o.spp;
   P.shade_min = shade_min;
+  P.exact_vndf = (o.flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
   AdjOut A{};
   if (S.mg.hot > 0.0f)
     k_path<false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);

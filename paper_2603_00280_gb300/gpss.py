@@ -27,6 +27,7 @@ class GpssError(RuntimeError):
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "UNSUPPORTED"}
 FLAG_KEEP_PATH_RADIANCE = 1
+FLAG_EXACT_VNDF = 2
 
 
 class ObjectDesc(ctypes.Structure):
@@ -87,6 +88,7 @@ _SIGS = {
     "gpss_eval_local_majorant": [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "gpss_eval_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP],
     "gpss_sample_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP],
+    "gpss_sample_phase_vndf": [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "gpss_eval_ndf": [_I, _VP, _F, _F, _F, _F, _VP, _VP],
     "gpss_eval_projected_area": [_I, _VP, _F, _F, _F, _F, _VP, _VP],
     "gpss_eval_transmittance": [_VP, _I, _VP, _VP, _VP, _VP, _VP],
@@ -186,6 +188,11 @@ def render_opts(opts: dict, flags: int = 0) -> RenderOpts:
     o.seed = int(opts.get("seed", 0))
     o.mix_R = float(opts.get("mix_R", 0.5))
     o.flags = int(opts.get("flags", 0)) | flags
+    sampler = opts.get("sampler", "mixture")
+    if sampler == "vndf":
+        o.flags |= FLAG_EXACT_VNDF
+    elif sampler != "mixture":
+        raise ValueError("sampler must be 'mixture' (the paper's) or 'vndf' (exact visible normals)")
     return o
 
 
@@ -403,6 +410,19 @@ def sample_phase(scene: Scene, k: int, pos, d_in, u, mix_R=0.5, stream=None):
     pdf = torch.empty(len(pos), device="cuda", dtype=torch.float32)
     _call("gpss_sample_phase", scene.handle, int(k), len(pos), _ptr(pos), _ptr(d_in), _ptr(u), float(mix_R),
           _ptr(d_out), _ptr(w), _ptr(pdf), _stream(stream))
+    return d_out, w, pdf
+
+
+def sample_phase_vndf(scene: Scene, k: int, pos, d_in, u, stream=None):
+    """Exact visible-normal samples: (d_out, weight = F, pdf = p/F)."""
+    torch = _torch()
+    pos, d_in, u = _dev(pos), _dev(d_in), _dev(u)
+    n = len(pos)
+    d_out = torch.empty((n, 3), device="cuda")
+    w = torch.empty((n, 3), device="cuda")
+    pdf = torch.empty(n, device="cuda")
+    _call("gpss_sample_phase_vndf", scene.handle, int(k), n, _ptr(pos), _ptr(d_in), _ptr(u), _ptr(d_out), _ptr(w),
+          _ptr(pdf), _stream(stream))
     return d_out, w, pdf
 
 
