@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--spp", type=int, default=0, help="override samples per pixel (profiling of small cases)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-vndf", action="store_true", help="skip the exact visible-normal sampler comparison")
     ap.add_argument("--batch-count", type=int, default=64, help="scenes of the batched comparison")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="image/grid size scale of the batched scenes")
     return ap.parse_args()
@@ -249,6 +250,36 @@ def measure_adjoint(args, gpss, torch, flush, rank):
             "replay_mismatches": mism}
 
 
+# ----------------------------------------------------------------- exact visible-normal sampling
+def measure_vndf(args, gpss, torch, flush, wl, S, image):
+    """The heterogeneous workload with the exact GPSS visible-normal sampler instead of
+    the paper's mixture: throughput, and the summed per-pixel variance of the two
+    estimators (same scene, same spp) -- the efficiency ratio is
+    (var_mix t_mix) / (var_vndf t_vndf)."""
+    import numpy as np
+    cam = wl["camera"]
+    res = {}
+    for name, opts in (("mixture", wl["opts"]), ("vndf", dict(wl["opts"], sampler="vndf"))):
+        for _ in range(2):
+            gpss.render(S, cam, opts, image=image, stats=False)
+        ms, verts = [], 0
+        for _ in range(args.steps):
+            flush.zero_()
+            _, _, st = gpss.render(S, cam, opts, image=image, stats=True)
+            ms.append(st["ms"])
+            verts += st["vertices"]
+        img, sq, _ = gpss.render(S, cam, opts, want_sqsum=True, stats=False)
+        m = img.double().cpu().numpy()
+        v = np.maximum(sq.double().cpu().numpy() / opts["spp"] - m * m, 0.0)
+        res[name] = {"ms": sum(ms) / len(ms), "value": verts / (sum(ms) / 1e3) / 1e6, "var_sum": float(v.sum())}
+    mix, vn = res["mixture"], res["vndf"]
+    return {"workload": wl["name"], "unit": UNIT, "value_vndf": vn["value"], "value_mixture": mix["value"],
+            "ms_vndf": vn["ms"], "ms_mixture": mix["ms"],
+            "variance_ratio_vndf_over_mixture": vn["var_sum"] / mix["var_sum"],
+            "efficiency_ratio": (mix["var_sum"] * mix["ms"]) / (vn["var_sum"] * vn["ms"]),
+            "note": "per-pixel variance of one path's radiance summed over the image; same scene, spp and bounces"}
+
+
 # ----------------------------------------------------------------- batched launch
 def measure_batched(args, gpss, torch, flush):
     """The uneven 64-scene batch (images 64^2..512^2, grids 32^3..256^3, spp 4..64):
@@ -413,6 +444,7 @@ def run_ours(args):
 
     adj = None if args.no_adjoint else measure_adjoint(args, gpss, torch, flush, rank)
     batched = None if (args.no_batched or world > 1) else measure_batched(args, gpss, torch, flush)
+    vndf = None if (args.no_vndf or world > 1) else measure_vndf(args, gpss, torch, flush, wl, S, image)
 
     if rank != 0:
         if dist:
@@ -429,7 +461,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl, "flushed between steps (256 MB write)"),
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
-           "clocks": clk, "fwd_adjoint": adj, "batched": batched,
+           "clocks": clk, "fwd_adjoint": adj, "batched": batched, "exact_vndf": vndf,
            "work": {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
                     "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
                     "majorant_cells_per_step": stats["majorant_cells"],
