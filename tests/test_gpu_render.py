@@ -139,3 +139,30 @@ def test_full_size_workload_sampled_pixels():
     z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], 64, s[sel], s2[sel], orc_spp)
     ok, info = C.check_image_parity(gm, gse, om, ose, frac4=0.1, block=2)
     assert ok, info
+
+
+def test_full_size_surface_to_volume_sampled_pixels():
+    """The three-object surface-to-volume configuration at full size (torus, box and
+    sphere on 256^3 grids, variances 1e-6 / 2.24e-4 / 0.05, RGB albedo; 1024x1024,
+    256 spp, 64 bounces): every path completes, and sampled pixels over each object
+    agree with the oracle."""
+    wl = W.surface_to_volume()
+    S = gpss.Scene(wl["scene"])
+    img, sq, st = gpss.render(S, wl["camera"], wl["opts"], want_sqsum=True)
+    img, sq = img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64)
+    assert st["paths"] == 1024 * 1024 * 256 and st["aborted"] == 0
+    assert np.all(np.isfinite(img))
+    S.close()
+    O = oracle.Scene(wl["scene"])
+    gm_all, gse_all, om_all, ose_all = [], [], [], []
+    # torus (thin shell, slow in the oracle), box, sphere
+    for rows, cols, orc_spp in [((500, 502), (370, 372), 8), ((500, 504), (510, 514), 16), ((500, 504), (650, 654), 16)]:
+        s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=orc_spp, seed=9), rows=rows, cols=cols)
+        sel = (slice(*rows), slice(*cols))
+        z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], 256, s[sel], s2[sel], orc_spp)
+        assert om.max() > 0.0  # the region sees the object
+        for a, lst in ((gm, gm_all), (gse, gse_all), (om, om_all), (ose, ose_all)):
+            lst.append(a.reshape(-1, 3))
+    gm, gse, om, ose = (np.concatenate(l)[:, None, :] for l in (gm_all, gse_all, om_all, ose_all))
+    ok, info = C.check_image_parity(gm, gse, om, ose, frac4=0.1, block=1)
+    assert ok, info
