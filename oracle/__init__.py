@@ -50,7 +50,7 @@ class _Object(ctypes.Structure):
         ("bmin", ctypes.c_double * 3), ("bmax", ctypes.c_double * 3),
         ("mean", ctypes.POINTER(ctypes.c_float)), ("var", ctypes.POINTER(ctypes.c_float)),
         ("albedo", ctypes.POINTER(ctypes.c_float)), ("channels", ctypes.c_int),
-        ("length_scale", ctypes.c_double),
+        ("length_scale", ctypes.c_double), ("ndf", ctypes.c_int),
     ]
 
 
@@ -105,6 +105,10 @@ def lib():
             L.orc_projected_area_local.argtypes = [_PD, _D, _D, _D, _D]
             L.orc_ndf_local.restype = _D
             L.orc_ndf_local.argtypes = [_PD, _D, _D, _D, _D]
+            L.orc_ndf_hf.restype = _D
+            L.orc_ndf_hf.argtypes = [_PD, ctypes.c_int, _D]
+            L.orc_projected_area_hf.restype = _D
+            L.orc_projected_area_hf.argtypes = [_PD, ctypes.c_int, _D]
             L.orc_sigma_t.restype = _D
             L.orc_sigma_t.argtypes = [ctypes.POINTER(_Scene), _PD, _PD]
             L.orc_sigma_t_object.restype = _D
@@ -137,6 +141,9 @@ _LIGHT_TYPES = {"directional": 0, "sky": 1, "uniform": 2}
 _CAMERA_TYPES = {"ortho": 0, "perspective": 1}
 
 
+NDF_KINDS = {"gpss": 0, "beckmann": 1, "ggx": 2}
+
+
 class Scene:
     """ctypes view of a scene dictionary; keeps the float32 grids alive."""
 
@@ -164,6 +171,7 @@ class Scene:
             ob.albedo = alb.ctypes.data_as(fp)
             ob.channels = alb.shape[0]
             ob.length_scale = float(o["length_scale"])
+            ob.ndf = NDF_KINDS[o.get("ndf", "gpss")]
         self.s = _Scene()
         self.s.objs = ctypes.cast(self._objs, ctypes.POINTER(_Object))
         self.s.n_objs = len(objs)
@@ -222,6 +230,18 @@ def projected_area_local(w, G, ax, ay, az) -> float:
 def ndf_local(m, G, ax, ay, az) -> float:
     ma, mp = _vec(m)
     return lib().orc_ndf_local(mp, float(G), float(ax), float(ay), float(az))
+
+
+def ndf_hf(m, kind: str, alpha) -> float:
+    """Height-field macrofacet NDF (Sec. 4.1) in the frame n = z."""
+    ma, mp = _vec(m)
+    return lib().orc_ndf_hf(mp, NDF_KINDS[kind], float(alpha))
+
+
+def projected_area_hf(w, kind: str, alpha) -> float:
+    """Lambda(w) cos(theta) of a height-field macrofacet for the marching direction w."""
+    wa, wp = _vec(w)
+    return lib().orc_projected_area_hf(wp, NDF_KINDS[kind], float(alpha))
 
 
 # ---------------------------------------------------------------- scene queries

@@ -42,7 +42,16 @@ typedef struct {
   const float* albedo;       /* channels planes of nx*ny*nz, F in [0,1]      */
   int channels;              /* 1 or 3                                       */
   double length_scale;       /* isotropic SE correlation l (> 0)             */
+  int ndf;                   /* ORC_NDF_GPSS (Sec. 4.2) or a height-field     */
+                             /* macrofacet NDF (Sec. 4.1)                     */
 } orc_object;
+
+/* NDF of an object.  GPSS: the generalized macrofacet of Sec. 4.2 (default).
+ * Height-field macrofacets (Sec. 4.1): the same density rho with Lambda(w) cos(theta)
+ * and the phase function of a chosen microfacet NDF about n = grad mu/|grad mu|,
+ * roughness alpha = sqrt(2) sigma / l: Beckmann (the fully anisotropic GPSS with
+ * infinite correlation along n) or GGX (the paper's artist-friendly choice). */
+enum { ORC_NDF_GPSS = 0, ORC_NDF_BECKMANN = 1, ORC_NDF_GGX = 2 };
 
 enum { ORC_LIGHT_DIRECTIONAL = 0, ORC_LIGHT_SKY = 1, ORC_LIGHT_UNIFORM = 2 };
 
@@ -95,6 +104,11 @@ int orc_field(const orc_object* o, const double x[3], double* mu, double grad[3]
 /* Projected area sigma(w) in the paper's local frame: mean gradient (0,0,G),
  * roughness alpha_x, alpha_y, alpha_z (Eq. generalized_lambda times cos). */
 double orc_projected_area_local(const double w[3], double G, double ax, double ay, double az);
+/* Height-field macrofacet (Sec. 4.1), local frame with n = z: the NDF (zero for
+ * m_z <= 0) and the projected area Lambda(w) cos(theta) for the marching
+ * direction w, continued below the horizon by Lambda(-w) = -1 - Lambda(w). */
+double orc_ndf_hf(const double m[3], int ndf, double alpha);
+double orc_projected_area_hf(const double w[3], int ndf, double alpha);
 /* NDF by quadrature of its definition, local frame (Eq. gdf_to_ndf, gdf). */
 double orc_ndf_local(const double m[3], double G, double ax, double ay, double az);
 /* Extinction of one object / the whole scene (extinctions of objects add). */

@@ -19,6 +19,7 @@ typedef struct {
   double alpha;   /* sqrt(2) sigma / l  (Eq. roughness) */
   double G;       /* |grad mu|                          */
   double nhat[3]; /* grad mu / G (0 when G == 0)        */
+  int ndf;        /* the object's NDF kind              */
 } orc_fpt;
 
 int orc_point(const orc_object* o, const double x[3], orc_fpt* p);

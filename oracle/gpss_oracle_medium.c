@@ -154,6 +154,7 @@ int orc_point(const orc_object* o, const double x[3], orc_fpt* p) {
   p->alpha = ORC_SQRT2 * p->sigma / o->length_scale;  /* Eq. roughness */
   p->G = sqrt(p->g[0] * p->g[0] + p->g[1] * p->g[1] + p->g[2] * p->g[2]);
   for (int a = 0; a < 3; ++a) p->nhat[a] = p->G > 0.0 ? p->g[a] / p->G : 0.0;
+  p->ndf = o->ndf;
   return 1;
 }
 
@@ -172,8 +173,59 @@ double orc_projected_area_local(const double w[3], double G, double ax, double a
   return ae / (2.0 * ORC_SQRTPI) * exp(-a * a) - 0.5 * proj * erfc(a);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Height-field macrofacet (Sec. 4.1, Eq. macro_sigma_t): Smith's Lambda of   */
+/* the chosen NDF for a direction in the upper hemisphere (cos theta = c > 0):*/
+/*   Beckmann: a = c/(alpha sin theta), Lambda = (e^{-a^2}/(a sqrt pi) - erfc a)/2 */
+/*   GGX:      Lambda = (-1 + sqrt(1 + alpha^2 tan^2 theta))/2                */
+/* sigma(w) = Lambda(w) w_z for w_z >= 0 and (1 + Lambda(-w)) |w_z| below.    */
+/* ------------------------------------------------------------------------ */
+static double smith_lambda(double c, int ndf, double alpha) {
+  double s = sqrt(fmax(0.0, 1.0 - c * c));
+  if (ndf == ORC_NDF_GGX) {
+    if (c <= 0.0) return INFINITY;
+    double t = s / c;
+    return 0.5 * (-1.0 + sqrt(1.0 + alpha * alpha * t * t));
+  }
+  if (s == 0.0) return 0.0;
+  double a = c / (alpha * s);
+  if (a <= 0.0) return INFINITY;
+  return 0.5 * (exp(-a * a) / (a * ORC_SQRTPI) - erfc(a));
+}
+
+double orc_projected_area_hf(const double w[3], int ndf, double alpha) {
+  double c = w[2] / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double s = sqrt(fmax(0.0, 1.0 - c * c));
+  double cu = fabs(c);
+  if (cu < 1e-12) {
+    /* grazing: Lambda cos -> alpha/(2 sqrt pi) (Beckmann), alpha/2 (GGX) */
+    return ndf == ORC_NDF_GGX ? 0.5 * alpha * s : alpha * s / (2.0 * ORC_SQRTPI);
+  }
+  double lam = smith_lambda(cu, ndf, alpha);
+  return c >= 0.0 ? lam * cu : (1.0 + lam) * cu;
+}
+
+double orc_ndf_hf(const double m[3], int ndf, double alpha) {
+  double c = m[2] / sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  if (c <= 0.0) return 0.0;
+  double c2 = c * c, t2 = (1.0 - c2) / c2, a2 = alpha * alpha;
+  if (ndf == ORC_NDF_GGX) {
+    double q = a2 + t2;
+    return a2 / (ORC_PI * c2 * c2 * q * q);
+  }
+  return exp(-t2 / a2) / (ORC_PI * a2 * c2 * c2);
+}
+
+/* components of v in a frame with the unit vector n as its z axis */
+static void to_frame(const double v[3], const double n[3], double out[3]);
+
 /* World-frame isotropic form for a field point: the mean gradient is g. */
 double orc_projected_area_world(const double d[3], const orc_fpt* p) {
+  if (p->ndf != ORC_NDF_GPSS) {
+    double dl[3];
+    to_frame(d, p->nhat, dl);
+    return orc_projected_area_hf(dl, p->ndf, p->alpha);
+  }
   double dg = d[0] * p->g[0] + d[1] * p->g[1] + d[2] * p->g[2];
   double a = dg / p->alpha;
   return p->alpha / (2.0 * ORC_SQRTPI) * exp(-a * a) - 0.5 * dg * erfc(a);
@@ -222,6 +274,11 @@ double orc_ndf_local(const double m[3], double G, double ax, double ay, double a
 /* World-frame NDF for a field point (isotropic kernel): rotate m so that the
  * mean gradient is the local z axis; only m . nhat matters. */
 double orc_ndf_world(const double m[3], const orc_fpt* p) {
+  if (p->ndf != ORC_NDF_GPSS) {
+    double ml[3];
+    to_frame(m, p->nhat, ml);
+    return orc_ndf_hf(ml, p->ndf, p->alpha);
+  }
   double c = 1.0;
   if (p->G > 0.0) c = m[0] * p->nhat[0] + m[1] * p->nhat[1] + m[2] * p->nhat[2];
   if (c > 1.0) c = 1.0;
@@ -276,6 +333,14 @@ static void basis(const double z[3], double t1[3], double t2[3]) {
   t2[0] = z[1] * t1[2] - z[2] * t1[1];
   t2[1] = z[2] * t1[0] - z[0] * t1[2];
   t2[2] = z[0] * t1[1] - z[1] * t1[0];
+}
+
+static void to_frame(const double v[3], const double n[3], double out[3]) {
+  double t1[3], t2[3];
+  basis(n, t1, t2);
+  out[0] = dot3(v, t1);
+  out[1] = dot3(v, t2);
+  out[2] = dot3(v, n);
 }
 
 static void beck_frame(const orc_fpt* p, const double d[3], double z[3], double* aB) {
@@ -385,7 +450,9 @@ int orc_phase_eval_point(const orc_fpt* p, const double d[3], const double d2[3]
   double sd = orc_projected_area_world(d, p);
   double val = orc_ndf_world(m, p) / (4.0 * sd);
   for (int c = 0; c < 3; ++c) p_out[c] = p->F[c] * val;
-  if (pdf_out) *pdf_out = mixture_pdf_m(p, d, m, R) / (4.0 * fabs(dm));
+  /* the oracle samples height-field kinds uniformly on the hemisphere about -d */
+  double pdf_m = p->ndf == ORC_NDF_GPSS ? mixture_pdf_m(p, d, m, R) : 1.0 / (2.0 * ORC_PI);
+  if (pdf_out) *pdf_out = pdf_m / (4.0 * fabs(dm));
   return 1;
 }
 
@@ -404,7 +471,9 @@ int orc_phase_sample_point(const orc_fpt* p, const double d[3], double R, const 
                            double d2[3], double w_out[3], double* pdf_out) {
   double wi[3] = {-d[0], -d[1], -d[2]};
   double m[3];
-  if (u[0] < R) {
+  if (p->ndf != ORC_NDF_GPSS) {
+    uniform_hemi(wi, u[1], u[2], m);
+  } else if (u[0] < R) {
     double z[3], aB;
     beck_frame(p, d, z, &aB);
     beck_sample_vis(wi, z, aB, u[1], u[2], m);
@@ -417,7 +486,7 @@ int orc_phase_sample_point(const orc_fpt* p, const double d[3], double R, const 
   if (dm >= 0.0) return 0;
   for (int i = 0; i < 3; ++i) d2[i] = d[i] - 2.0 * dm * m[i];
   normalize3(d2);
-  double pdf_m = mixture_pdf_m(p, d, m, R);
+  double pdf_m = p->ndf == ORC_NDF_GPSS ? mixture_pdf_m(p, d, m, R) : 1.0 / (2.0 * ORC_PI);
   if (!(pdf_m > 0.0)) return 0;
   double sd = orc_projected_area_world(d, p);
   double w = orc_ndf_world(m, p) * fabs(dm) / (sd * pdf_m);
