@@ -63,7 +63,20 @@ typedef struct {
   const float* albedo;         /* albedo_channels planes of nx*ny*nz, F in [0,1]   */
   int albedo_channels;         /* 1 or 3                                           */
   float length_scale;          /* isotropic SE correlation l > 0 (Eq. roughness)   */
+  int ndf;                     /* gpss_ndf: the macrofacet's NDF                   */
 } gpss_object_desc;
+
+/* NDF of an object.  GPSS_NDF_GPSS: the generalized macrofacet of the GPSS
+ * (Sec. 4.2, Eq. generalized_sigma_t / macro_ndf).  The height-field macrofacets
+ * of Sec. 4.1 keep the density rho and take the projected area Lambda(w)cos(theta)
+ * (continued below the horizon by Lambda(-w) = -1 - Lambda(w)) and the phase
+ * function of a chosen microfacet NDF about n = grad mu/|grad mu| with roughness
+ * alpha = sqrt(2) sigma/l: GPSS_NDF_BECKMANN (the fully anisotropic GPSS with
+ * infinite correlation along n) or GPSS_NDF_GGX.  Height-field objects sample their
+ * visible normals exactly when the ray arrives from above n (weight F) and the
+ * hemisphere uniformly otherwise; mix_R does not apply to them.  The adjoint
+ * supports GPSS_NDF_GPSS only. */
+typedef enum { GPSS_NDF_GPSS = 0, GPSS_NDF_BECKMANN = 1, GPSS_NDF_GGX = 2 } gpss_ndf;
 
 typedef enum { GPSS_LIGHT_DIRECTIONAL = 0, GPSS_LIGHT_SKY = 1, GPSS_LIGHT_UNIFORM = 2 } gpss_light_type;
 

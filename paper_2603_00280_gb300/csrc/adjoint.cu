@@ -51,6 +51,10 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   gpss_status st = check_opts(opts);
   if (st != GPSS_OK) return st;
   if (s->n_objs != 1) { set_error("the adjoint supports single-object scenes"); return GPSS_ERR_UNSUPPORTED; }
+  if (s->obj[0].ndf != GPSS_NDF_GPSS) {
+    set_error("the adjoint supports the GPSS NDF only (not the height-field macrofacets)");
+    return GPSS_ERR_UNSUPPORTED;
+  }
   CameraDev C;
   if (!camera_dev(cam, &C)) return GPSS_ERR_INVALID_ARG;
   cudaStream_t cs = (cudaStream_t)stream;

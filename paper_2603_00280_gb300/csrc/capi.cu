@@ -112,6 +112,10 @@ static gpss_status check_objects(const gpss_object_desc* objs, int n) {
       set_error("object %d: length_scale must be finite and > 0", k);
       return GPSS_ERR_INVALID_ARG;
     }
+    if (o.ndf != GPSS_NDF_GPSS && o.ndf != GPSS_NDF_BECKMANN && o.ndf != GPSS_NDF_GGX) {
+      set_error("object %d: unknown ndf %d", k, o.ndf);
+      return GPSS_ERR_INVALID_ARG;
+    }
   }
   return GPSS_OK;
 }
@@ -223,6 +227,7 @@ extern "C" gpss_status gpss_scene_create(const gpss_object_desc* objs, int n_obj
     }
     o.channels = objs[k].albedo_channels;
     o.length_scale = objs[k].length_scale;
+    o.ndf = objs[k].ndf;
     o.nodes = (size_t)o.n[0] * o.n[1] * o.n[2];
     max_nodes = std::max(max_nodes, o.nodes);
     if ((e = cudaMalloc(&o.mv, o.nodes * sizeof(float2))) != cudaSuccess ||
@@ -276,6 +281,7 @@ extern "C" gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* o
         return GPSS_ERR_INVALID_ARG;
       }
     s->obj[k].length_scale = objs[k].length_scale;
+    s->obj[k].ndf = objs[k].ndf;
   }
   cudaStream_t cs = (cudaStream_t)stream;
   if ((st = scene_upload(s, objs, n_objs, cs)) != GPSS_OK) return st;

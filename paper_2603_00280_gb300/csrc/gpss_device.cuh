@@ -45,6 +45,7 @@ struct ObjectDev {
   float inv_h[3];          // (n-1)/(bmax-bmin)
   int n[3];
   int channels;            // albedo channels, 1 or 3
+  int ndf;                 // kNdfGpss or a height-field macrofacet NDF (gpss_ndf)
   float alpha_scale;       // sqrt(2)/l: alpha = sigma * alpha_scale (Eq. roughness)
   const float2* mv;        // (mean, variance) per node
   const float* albedo;     // channels planes
@@ -207,7 +208,10 @@ __device__ __forceinline__ float psi(float a) {
 struct Field {
   float mu, var;
   V3 g;        // gradient of the mean interpolant
+  int ndf;     // the object's NDF kind (gpss_ndf)
 };
+
+enum NdfKind : int { kNdfGpss = 0, kNdfBeckmann = 1, kNdfGgx = 2 };
 
 // Cell lookup + trilinear weights; returns the node index of the cell's corner 000.
 __device__ __forceinline__ int cell_of(const ObjectDev& o, V3 x, float& wx, float& wy, float& wz) {
@@ -244,6 +248,7 @@ __device__ __forceinline__ Field fetch(const ObjectDev& o, V3 x) {
   const float d00 = v100.x - v000.x, d10 = v110.x - v010.x, d01 = v101.x - v001.x, d11 = v111.x - v011.x;
   const float m0 = lerpf(m00, m10, wy), m1 = lerpf(m01, m11, wy);
   Field f;
+  f.ndf = o.ndf;
   f.mu = lerpf(m0, m1, wz);
   f.g.x = lerpf(lerpf(d00, d10, wy), lerpf(d01, d11, wy), wz) * o.inv_h[0];
   f.g.y = lerpf(m10 - m00, m11 - m01, wz) * o.inv_h[1];
@@ -289,7 +294,44 @@ __device__ __forceinline__ Local local_of(const ObjectDev& o, const Field& f) {
 }
 
 // sigma(d) = Lambda(d) cos(theta) = alpha psi(d . grad mu / alpha)
+// ---------------------------------------------------------------- height-field macrofacets
+// Sec. 4.1 (Eq. macro_sigma_t): the density rho times Lambda(w) cos(theta) of a chosen
+// microfacet NDF about n = grad mu/|grad mu|, roughness alpha.  For the marching
+// direction d (c = d.n, s = sin theta) and the continuation Lambda(-w) = -1 - Lambda(w)
+// both signs of c take one form:
+//   Beckmann: alpha s psi(c/(alpha s))   (the GPSS projected area with alpha_z = 0)
+//   GGX:      (sqrt(c^2 + alpha^2 s^2) - c)/2
+__device__ __forceinline__ V3 hf_normal(V3 g) {
+  const float G2 = dot(g, g);
+  return G2 > 1e-30f ? rsqrtf(G2) * g : v3(0.0f, 0.0f, 1.0f);
+}
+
+__device__ __forceinline__ float hf_projected_area(int ndf, V3 d, V3 n, float alpha) {
+  const float c = dot(d, n);
+  const float s2 = fmaxf(0.0f, 1.0f - c * c);
+  if (ndf == kNdfGgx) {
+    const float r = sqrtf(fmaf(alpha * alpha, s2, c * c));
+    return c > 0.0f ? 0.5f * alpha * alpha * s2 / (r + c) : 0.5f * (r - c);  // no cancellation
+  }
+  const float ae = alpha * sqrtf(s2);
+  if (!(ae > 0.0f)) return fmaxf(0.0f, -c);
+  return ae * psi(c / ae);
+}
+
+// Microfacet NDF about n, normalised by int D(m) (m.n) dm = 1; zero for m.n <= 0.
+__device__ __forceinline__ float hf_ndf(int ndf, V3 m, V3 n, float alpha) {
+  const float c = dot(m, n);
+  if (c <= 0.0f) return 0.0f;
+  const float c2 = c * c, a2 = alpha * alpha;
+  if (ndf == kNdfGgx) {
+    const float q = fmaf(c2, a2 - 1.0f, 1.0f);  // c^4 (a^2 + tan^2)^2 = (1 + c^2 (a^2 - 1))^2
+    return a2 / (kPi * q * q);
+  }
+  return expf(-(1.0f - c2) / (c2 * a2)) / (kPi * a2 * c2 * c2);
+}
+
 __device__ __forceinline__ float projected_area(V3 d, const Field& f, float alpha) {
+  if (f.ndf != kNdfGpss) return hf_projected_area(f.ndf, d, hf_normal(f.g), alpha);
   return alpha * psi(dot(d, f.g) / alpha);
 }
 
@@ -505,6 +547,53 @@ __device__ __forceinline__ V3 uniform_hemisphere(V3 wi, float u1, float u2) {
   return normalize((s * cp) * t1 + (s * sp) * t2 + c * wi);
 }
 
+// ---------------------------------------------------------------- height-field sampling
+// Visible-normal sampling of the GGX NDF (Heitz 2018, "Sampling the GGX distribution of
+// visible normals"): stretch the incident direction to unit roughness, sample the
+// projected hemisphere (a disk warped toward the incident direction), unstretch.
+// wi.n > 0 required.
+__device__ __forceinline__ V3 ggx_sample_vis(V3 wi, V3 n, float a, float u1, float u2) {
+  V3 b1, b2;
+  onb(n, b1, b2);
+  const V3 vh = normalize(v3(a * dot(wi, b1), a * dot(wi, b2), dot(wi, n)));
+  const float lensq = vh.x * vh.x + vh.y * vh.y;
+  const V3 T1 = lensq > 0.0f ? rsqrtf(lensq) * v3(-vh.y, vh.x, 0.0f) : v3(1.0f, 0.0f, 0.0f);
+  const V3 T2 = cross(vh, T1);
+  const float r = sqrtf(u1);
+  float sp, cp;
+  sincospif(2.0f * u2, &sp, &cp);
+  const float t1 = r * cp;
+  const float sh = 0.5f * (1.0f + vh.z);
+  const float t2 = (1.0f - sh) * sqrtf(fmaxf(0.0f, 1.0f - t1 * t1)) + sh * (r * sp);
+  const V3 nh = fma3(t1, T1, fma3(t2, T2, sqrtf(fmaxf(0.0f, 1.0f - t1 * t1 - t2 * t2)) * vh));
+  const V3 ne = normalize(v3(a * nh.x, a * nh.y, fmaxf(nh.z, 1e-7f)));
+  return normalize(fma3(ne.x, b1, fma3(ne.y, b2, ne.z * n)));
+}
+
+// NDF of a field sample's object (GPSS or height field).
+__device__ __forceinline__ float ndf_field(V3 m, const Field& f, float alpha) {
+  if (f.ndf != kNdfGpss) return hf_ndf(f.ndf, m, hf_normal(f.g), alpha);
+  return ndf_iso(m, f.g, alpha);
+}
+
+// Height-field objects: exact visible normals when the ray arrives from above n (pdf over
+// half vectors max(0, wi.m) D(m)/sigma(d)), otherwise m uniform on the hemisphere about wi.
+__device__ __forceinline__ float hf_pdf_m(V3 d, V3 m, const Field& f, float alpha, float sd) {
+  const V3 wi = -d;
+  const V3 n = hf_normal(f.g);
+  if (dot(wi, m) <= 0.0f) return 0.0f;
+  if (dot(wi, n) > 0.0f) return dot(wi, m) * hf_ndf(f.ndf, m, n, alpha) / sd;
+  return 1.0f / kTwoPi;
+}
+
+__device__ __forceinline__ V3 hf_sample_m(V3 d, const Field& f, float alpha, float u1, float u2) {
+  const V3 wi = -d;
+  const V3 n = hf_normal(f.g);
+  if (dot(wi, n) > 0.0f)
+    return f.ndf == kNdfGgx ? ggx_sample_vis(wi, n, alpha, u1, u2) : beckmann_sample_vis(wi, n, alpha, u1, u2);
+  return uniform_hemisphere(wi, u1, u2);
+}
+
 // The quantities of the sampling mixture that depend on the incoming d only: the
 // Beckmann frame and roughness and its visible-normal normaliser.  A vertex sets
 // them up once for its phase sample and its NEE evaluation.
@@ -544,8 +633,8 @@ __device__ __forceinline__ bool phase_eval_mix(const Mix& mx, float sd, V3 d, V3
   m = rsqrtf(len2) * m;
   const float dm = dot(d, m);
   if (dm >= 0.0f) return false;
-  p_over_F = ndf_iso(m, f.g, alpha) / (4.0f * sd);
-  pdf = mix_pdf_m(mx, d, m) / (4.0f * fabsf(dm));
+  p_over_F = ndf_field(m, f, alpha) / (4.0f * sd);
+  pdf = (f.ndf == kNdfGpss ? mix_pdf_m(mx, d, m) : hf_pdf_m(d, m, f, alpha, sd)) / (4.0f * fabsf(dm));
   return true;
 }
 
@@ -553,27 +642,42 @@ __device__ __forceinline__ bool phase_eval_mix(const Mix& mx, float sd, V3 d, V3
 __device__ __forceinline__ bool phase_sample_mix(const Mix& mx, float sd, V3 d, const Field& f, float alpha, float u0,
                                                  float u1, float u2, V3& d2, float& w_over_F, float& pdf) {
   const V3 wi = -d;
-  const V3 m = u0 < mx.R ? beckmann_sample_vis(wi, mx.z, mx.aB, u1, u2) : uniform_hemisphere(wi, u1, u2);
+  const bool hf = f.ndf != kNdfGpss;
+  const V3 m = hf ? hf_sample_m(d, f, alpha, u1, u2)
+                  : (u0 < mx.R ? beckmann_sample_vis(wi, mx.z, mx.aB, u1, u2) : uniform_hemisphere(wi, u1, u2));
   const float dm = dot(d, m);
   w_over_F = 0.0f;
   pdf = 0.0f;
   if (!(dm < 0.0f)) return false;
   d2 = normalize(fma3(-2.0f * dm, m, d));
-  const float pdf_m = mix_pdf_m(mx, d, m);
+  const float pdf_m = hf ? hf_pdf_m(d, m, f, alpha, sd) : mix_pdf_m(mx, d, m);
   if (!(pdf_m > 0.0f)) return false;
-  w_over_F = ndf_iso(m, f.g, alpha) * fabsf(dm) / (sd * pdf_m);
+  w_over_F = ndf_field(m, f, alpha) * fabsf(dm) / (sd * pdf_m);
   pdf = pdf_m / (4.0f * fabsf(dm));
   return isfinite(w_over_F);
 }
 
+// The mixture's set-up for a field sample (unused by height-field objects).
+__device__ __forceinline__ Mix mix_for(V3 d, const Field& f, float alpha, float R) {
+  if (f.ndf != kNdfGpss) {
+    Mix mx;
+    mx.z = -d;
+    mx.aB = 1.0f;
+    mx.den = 1.0f;
+    mx.R = R;
+    return mx;
+  }
+  return mix_setup(d, f.g, alpha, R);
+}
+
 __device__ __forceinline__ bool phase_eval(V3 d, V3 d2, const Field& f, float alpha, float R, float& p_over_F,
                                            float& pdf) {
-  return phase_eval_mix(mix_setup(d, f.g, alpha, R), projected_area(d, f, alpha), d, d2, f, alpha, p_over_F, pdf);
+  return phase_eval_mix(mix_for(d, f, alpha, R), projected_area(d, f, alpha), d, d2, f, alpha, p_over_F, pdf);
 }
 
 __device__ __forceinline__ bool phase_sample(V3 d, const Field& f, float alpha, float R, float u0, float u1,
                                              float u2, V3& d2, float& w_over_F, float& pdf) {
-  return phase_sample_mix(mix_setup(d, f.g, alpha, R), projected_area(d, f, alpha), d, f, alpha, u0, u1, u2, d2,
+  return phase_sample_mix(mix_for(d, f, alpha, R), projected_area(d, f, alpha), d, f, alpha, u0, u1, u2, d2,
                           w_over_F, pdf);
 }
 
@@ -671,6 +775,7 @@ __device__ __forceinline__ bool vndf_sample_exact(V3 d, V3 g, float alpha, float
 // Exact-vNDF counterpart of phase_sample_mix: weight p/pdf/F = 1, pdf = p/F.
 __device__ __forceinline__ bool phase_sample_vndf(float sd, V3 d, const Field& f, float alpha, float u0, float u1,
                                                   float u2, V3& d2, float& w_over_F, float& pdf) {
+  if (f.ndf != kNdfGpss) return phase_sample_mix(mix_for(d, f, alpha, 0.5f), sd, d, f, alpha, u0, u1, u2, d2, w_over_F, pdf);
   V3 m;
   w_over_F = 0.0f;
   pdf = 0.0f;
@@ -678,7 +783,7 @@ __device__ __forceinline__ bool phase_sample_vndf(float sd, V3 d, const Field& f
   const float dm = dot(d, m);
   if (!(dm < 0.0f)) return false;
   d2 = normalize(fma3(-2.0f * dm, m, d));
-  pdf = ndf_iso(m, f.g, alpha) / (4.0f * sd);
+  pdf = ndf_field(m, f, alpha) / (4.0f * sd);
   w_over_F = 1.0f;
   return pdf > 0.0f && isfinite(pdf);
 }
@@ -725,7 +830,7 @@ __device__ __forceinline__ VertexShade shade_vertex_call(V3 d, V3 wl, Field f, f
   r.next.d2 = d;
   r.next.w_over_F = 0.0f;
   r.next.pdf = 0.0f;
-  if (exact) {
+  if (exact && f.ndf == kNdfGpss) {
     V3 m = wl - d;
     const float len2 = dot(m, m);
     r.nee.ok = 0;
@@ -734,7 +839,7 @@ __device__ __forceinline__ VertexShade shade_vertex_call(V3 d, V3 wl, Field f, f
     if (len2 > 0.0f) {
       m = rsqrtf(len2) * m;
       if (dot(d, m) < 0.0f) {
-        r.nee.p_over_F = ndf_iso(m, f.g, alpha) / (4.0f * sd);
+        r.nee.p_over_F = ndf_field(m, f, alpha) / (4.0f * sd);
         r.nee.pdf = r.nee.p_over_F;
         r.nee.ok = 1;
       }
@@ -742,7 +847,7 @@ __device__ __forceinline__ VertexShade shade_vertex_call(V3 d, V3 wl, Field f, f
     r.next.ok = sample ? phase_sample_vndf(sd, d, f, alpha, u0, u1, u2, r.next.d2, r.next.w_over_F, r.next.pdf) : 0;
     return r;
   }
-  const Mix mx = mix_setup(d, f.g, alpha, R);
+  const Mix mx = mix_for(d, f, alpha, R);
   r.nee.ok = phase_eval_mix(mx, sd, d, wl, f, alpha, r.nee.p_over_F, r.nee.pdf);
   r.next.ok = sample ? phase_sample_mix(mx, sd, d, f, alpha, u0, u1, u2, r.next.d2, r.next.w_over_F, r.next.pdf) : 0;
   return r;
@@ -851,7 +956,9 @@ static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, 
   mu_b -= 1e-6f * (fabsf(mu) + B * l) + 1e-7f * s_lo;  // rounding of mu and of the piece's end
   const float u = mu_b >= 0.0f ? mu_b / s_hi : mu_b / s_lo;
   const float rho_ub = inv_mills(u) / s_lo;
-  const float sbar = rho_ub * (B + s_hi * ob.alpha_scale * (0.5f * kInvSqrtPi)) * 1.001f;
+  const float area_ub = ob.ndf == kNdfGpss ? B + s_hi * ob.alpha_scale * (0.5f * kInvSqrtPi)
+                      : 1.0f + s_hi * ob.alpha_scale * (ob.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
+  const float sbar = rho_ub * area_ub * 1.001f;
   return make_float2(t + l, sbar);
 }
 

@@ -34,6 +34,7 @@ struct ObjectHost {
   float* albedo = nullptr;   // device planes
   size_t nodes = 0;
   float sigma_min = 0.0f;    // smallest standard deviation over the nodes
+  int ndf = 0;               // gpss_ndf
 };
 
 constexpr int kSceneFlagWords = 1 + kMaxObjects;  // validation bits + per-object min variance

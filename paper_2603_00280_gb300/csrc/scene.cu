@@ -41,7 +41,8 @@ __global__ void k_check_albedo(const float* __restrict__ a, size_t n, int* flags
 //   the trilinear interpolant is a convex combination of edge differences / h);
 //   lambda is decreasing, so rho <= lambda(mu_lo/sigma_hi)/sigma_lo for mu_lo >= 0 and
 //   lambda(mu_lo/sigma_lo)/sigma_lo otherwise;  sigma(d) = E[max(0,-d.g)] <= G_hi +
-//   alpha_hi/(2 sqrt(pi)).  Objects' bounds add.  A 1e-3 relative margin covers FP32
+//   alpha_hi/(2 sqrt(pi)) (height-field NDFs: 1 + alpha_hi/(2 sqrt(pi)) or 1 + alpha_hi/2).
+//   Objects' bounds add.  A 1e-3 relative margin covers FP32
 //   rounding of the per-sample evaluation.
 __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
   const long long ncell = (long long)g.dims[0] * g.dims[1] * g.dims[2];
@@ -89,7 +90,10 @@ __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
       const float s_lo = sqrtf(v_lo), s_hi = sqrtf(v_hi);
       const float u = mu_lo >= 0.0f ? mu_lo / s_hi : mu_lo / s_lo;
       const float rho_ub = inv_mills(u) / s_lo;
-      const float area_ub = G_hi + s_hi * o.alpha_scale * (0.5f * kInvSqrtPi);
+      // height-field macrofacets: sigma(d) <= max(0, -d.n) + alpha/(2 sqrt pi) (Beckmann),
+      // <= max(0, -d.n) + alpha/2 (GGX), with |n| = 1
+      const float area_ub = o.ndf == kNdfGpss ? G_hi + s_hi * o.alpha_scale * (0.5f * kInvSqrtPi)
+                          : 1.0f + s_hi * o.alpha_scale * (o.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
       total += rho_ub * area_ub;
     }
     maj[c] = total * 1.001f;
@@ -217,6 +221,7 @@ SceneDev scene_dev(const gpss_scene_s* s) {
       o.inv_h[a] = (float)(h.n[a] - 1) / (h.bmax[a] - h.bmin[a]);
     }
     o.channels = h.channels;
+    o.ndf = h.ndf;
     o.alpha_scale = kSqrt2 / h.length_scale;
     o.mv = h.mv;
     o.albedo = h.albedo;

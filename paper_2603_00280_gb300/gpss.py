@@ -34,7 +34,10 @@ class ObjectDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("bbox_min", ctypes.c_float * 3), ("bbox_max", ctypes.c_float * 3),
                 ("mean", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
-                ("albedo_channels", ctypes.c_int), ("length_scale", ctypes.c_float)]
+                ("albedo_channels", ctypes.c_int), ("length_scale", ctypes.c_float), ("ndf", ctypes.c_int)]
+
+
+NDF_KINDS = {"gpss": 0, "beckmann": 1, "ggx": 2}
 
 
 class LightDesc(ctypes.Structure):
@@ -220,6 +223,7 @@ def _object_descs(objects, keep):
         D.albedo = _ptr(alb).value
         D.albedo_channels = 1 if alb.ndim == 3 else int(alb.shape[0])
         D.length_scale = float(o["length_scale"])
+        D.ndf = NDF_KINDS[o.get("ndf", "gpss")]
     return descs
 
 
