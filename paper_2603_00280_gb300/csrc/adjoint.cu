@@ -140,14 +140,14 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
   const SceneDev S = scene_dev(s);
   if (S.mg.hot > 0.0f)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, true>, kPathBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, true, false>, kPathBlock, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, false>, kPathBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, false, false>, kPathBlock, 0);
   const int agrid = sms * (per_sm > 0 ? per_sm : 1);
   if (S.mg.hot > 0.0f)
-    k_path<true, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+    k_path<true, true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
   else
-    k_path<true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+    k_path<true, false, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   if (A.d_mv) {

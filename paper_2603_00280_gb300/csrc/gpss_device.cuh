@@ -308,7 +308,8 @@ __device__ __forceinline__ V3 hf_normal(V3 g) {
 
 __device__ __forceinline__ float hf_projected_area(int ndf, V3 d, V3 n, float alpha) {
   const float c = dot(d, n);
-  const float s2 = fmaxf(0.0f, 1.0f - c * c);
+  const V3 dxn = cross(d, n);
+  const float s2 = dot(dxn, dxn);  // sin^2 theta without the cancellation of 1 - c^2 near the normal
   if (ndf == kNdfGgx) {
     const float r = sqrtf(fmaf(alpha * alpha, s2, c * c));
     return c > 0.0f ? 0.5f * alpha * alpha * s2 / (r + c) : 0.5f * (r - c);  // no cancellation

@@ -75,13 +75,30 @@ struct AdjOut {
 
 enum Mode : int { kFlight = 0, kShadow = 1 };
 
+// Whether a scene has a height-field object (selects the HF kernel instances).
+inline bool scene_has_heightfield(const SceneDev& S) {
+  for (int k = 0; k < S.n_objs; ++k)
+    if (S.obj[k].ndf != kNdfGpss) return true;
+  return false;
+}
+
+// HF = false: the scene has no height-field object (every object uses the GPSS NDF), so
+// a field sample's kind is the constant kNdfGpss and the kind dispatch folds away.
+template <bool HF>
+__device__ __forceinline__ Field fetch_k(const ObjectDev& o, V3 x) {
+  Field f = fetch(o, x);
+  if constexpr (!HF) f.ndf = kNdfGpss;
+  return f;
+}
+
 // Total extinction at x (single object fast path; several objects add).
+template <bool HF>
 __device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d) {
   if (S.n_objs == 1) {
     if (!inside(S.obj[0], x)) return 0.0f;
-    Field f;
-    Local l;
-    return sigma_t_object(S.obj[0], x, d, f, l);
+    const Field f = fetch_k<HF>(S.obj[0], x);
+    const Local l = local_of(S.obj[0], f);
+    return l.rho * projected_area(d, f, l.alpha);
   }
   return scene_sigma_t(S, x, d);
 }
@@ -220,7 +237,7 @@ __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const Pa
 }
 
 // Shading of a real vertex: phase sampling, next-event estimation setup.
-template <bool ADJ>
+template <bool ADJ, bool HF>
 __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                            float* __restrict__ path_T, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
@@ -234,7 +251,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     k = choose_object(S, x, s.d, s.rng.next(), f, l);
     alpha = l.alpha;
   } else {
-    f = fetch(S.obj[0], x);
+    f = fetch_k<HF>(S.obj[0], x);
     alpha = sqrtf(f.var) * S.obj[0].alpha_scale;  // the density rho is not needed for shading
   }
   const V3 F = fetch_albedo(S.obj[k], x);
@@ -317,7 +334,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
 }
 
 // One tentative collision of the lane's current ray; returns true when the path ends.
-template <bool ADJ, bool LOCAL>
+template <bool ADJ, bool LOCAL, bool HF>
 __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                           float* __restrict__ path_T, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
@@ -344,7 +361,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
         st = ds.st;
       }
     } else {
-      st = sigma_t_at(S, x, s.d);
+      st = sigma_t_at<HF>(S, x, s.d);
     }
     float k_adj = 0.0f;  // adjoint: weight of this collision's extinction derivative
     if (s.mode == kFlight) {
@@ -486,8 +503,9 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
 }
 
 // ---------------------------------------------------------------- single-render kernel
-// LOCAL: the scene uses local majorants (MajorantDev::hot > 0).
-template <bool ADJ, bool LOCAL>
+// LOCAL: the scene uses local majorants (MajorantDev::hot > 0).  HF: the scene has a
+// height-field object (the adjoint supports the GPSS NDF only: HF = false there).
+template <bool ADJ, bool LOCAL, bool HF>
 __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
     k_path(const __grid_constant__ SceneDev S, const __grid_constant__ CameraDev C, const __grid_constant__ PathArgs P,
            float* __restrict__ image, float* __restrict__ sqsum, float* __restrict__ path_radiance,
@@ -511,10 +529,10 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
     }
     const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
     if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act)) {
-      if (s.waiting) lane_shade<ADJ>(s, S, P, A, path_T, c);
+      if (s.waiting) lane_shade<ADJ, HF>(s, S, P, A, path_T, c);
     }
     if (!s.active || s.waiting) continue;
-    if (lane_step<ADJ, LOCAL>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
+    if (lane_step<ADJ, LOCAL, HF>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
   }
   flush_counters(c, counters, ADJ ? A.d_l : nullptr);
 }

@@ -9,7 +9,7 @@ int render_block_size() { return kPathBlock; }
 int render_grid_size(int device, int block) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<false, false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<false, false, false>, block, 0);
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
 }
@@ -28,10 +28,15 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   P.shade_min = shade_min;
   P.exact_vndf = (o.flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
   AdjOut A{};
-  if (S.mg.hot > 0.0f)
-    k_path<false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+  const bool local = S.mg.hot > 0.0f, hf = scene_has_heightfield(S);
+  if (local && hf)
+    k_path<false, true, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+  else if (local)
+    k_path<false, true, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+  else if (hf)
+    k_path<false, false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
   else
-    k_path<false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+    k_path<false, false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
   return cudaGetLastError();
 }
 
