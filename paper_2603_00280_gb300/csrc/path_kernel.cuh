@@ -100,7 +100,14 @@ __device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d) {
     const Local l = local_of(S.obj[0], f);
     return l.rho * projected_area(d, f, l.alpha);
   }
-  return scene_sigma_t(S, x, d);
+  float tot = 0.0f;
+  for (int k = 0; k < S.n_objs; ++k) {
+    if (!inside(S.obj[k], x)) continue;
+    const Field f = fetch_k<HF>(S.obj[k], x);
+    const Local l = local_of(S.obj[k], f);
+    tot += l.rho * projected_area(d, f, l.alpha);
+  }
+  return tot;
 }
 
 // The scattering object, chosen in proportion to its extinction (reading Q13),
@@ -254,6 +261,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     f = fetch_k<HF>(S.obj[0], x);
     alpha = sqrtf(f.var) * S.obj[0].alpha_scale;  // the density rho is not needed for shading
   }
+  if constexpr (!HF) f.ndf = kNdfGpss;  // also on the several-object path
   const V3 F = fetch_albedo(S.obj[k], x);
   s.o = x;
   s.cont = s.bounce + 1 < P.max_bounces;
