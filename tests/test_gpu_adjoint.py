@@ -196,3 +196,50 @@ def test_autograd_function_and_edge_cases():
     with pytest.raises(gpss.GpssError) as e:
         gpss.render_adjoint(gpss.Scene(two), wl["camera"], wl["opts"], torch.zeros((8, 8, 3), device="cuda"))
     assert e.value.status == 5
+
+
+def test_full_size_differentiable_voxels_against_finite_differences():
+    """The differentiable configuration at full size (64^3 grids, 256x256, 64 spp, 32
+    bounces, start field): the adjoint's gradient of a fixed linear image loss with
+    respect to the mean at 32 shell nodes (seed 3) against central differences
+    (eps = 1e-3) of the GPU forward render with common random numbers."""
+    import torch
+    wl = W.differentiable(start=True)
+    sc, cam, opts = wl["scene"], wl["camera"], wl["opts"]
+    obj = sc["objects"][0]
+    mean = obj["mean"]
+    sig = np.sqrt(obj["var"])
+    rng = np.random.default_rng(3)
+    shell = np.argwhere((np.abs(mean) < 3 * sig) & (np.abs(mean) < 0.05))
+    nodes = shell[rng.choice(len(shell), 32, replace=False)]
+    H_, W_ = cam["height"], cam["width"]
+    wimg = np.random.default_rng(4).random((H_, W_, 3)).astype(np.float32)  # a fixed linear loss
+    seeds = [101, 102, 103, 104]
+    res = _adjoint_runs(sc, cam, opts, wimg, seeds)
+    adj = np.array([[dm[tuple(n)] for n in nodes] for dm in res["dm"]])  # (seeds, nodes)
+    S = gpss.Scene(sc)
+    w = torch.as_tensor(wimg).cuda()
+    eps = 1e-3
+    fd = np.zeros((len(seeds), len(nodes)))
+    for j, n in enumerate(nodes):
+        vals = {}
+        for sign in (1, -1):
+            m = mean.copy()
+            m[tuple(n)] += sign * eps
+            S.update([dict(obj, mean=m)])
+            for i, sd in enumerate(seeds):
+                img, _, _ = gpss.render(S, cam, dict(opts, seed=sd), stats=False)
+                vals[(sign, i)] = float((img * w).double().sum())
+        for i in range(len(seeds)):
+            fd[i, j] = (vals[(1, i)] - vals[(-1, i)]) / (2 * eps)
+    a, ase = _mean_se(adj)
+    f, fse = _mean_se(fd)
+    z = (a - f) / np.sqrt(ase ** 2 + fse ** 2 + 1e-30)
+    tol = np.abs(z) < 4 + 0.05 * np.abs(f) / np.sqrt(ase ** 2 + fse ** 2 + 1e-30)
+    assert tol.mean() >= 0.9, (z, a, f)
+    # the check has power: most nodes have a gradient resolved to 30% or better
+    assert np.mean(np.abs(a) > 3 * ase) > 0.5, (a, ase)
+    # and the summed gradient over the 32 nodes agrees within 4 standard errors + 5%
+    sa, sase = _mean_se(adj.sum(axis=1))
+    sf, sfse = _mean_se(fd.sum(axis=1))
+    assert abs(sa - sf) < 4 * math.sqrt(sase ** 2 + sfse ** 2) + 0.05 * abs(sf), (sa, sase, sf, sfse)
