@@ -56,7 +56,9 @@ __device__ __forceinline__ DSig dsigma_t(const ObjectDev& o, const Field& f, V3 
   DSig r;
   r.st = rho * S;
   r.dmu = S * lamp / f.var;
-  r.dg = (-0.5f * rho * ps * ec_over * alpha) * d;  // rho erfc(a)/2 with erfc = ec_over psi
+  // sigma(d) = alpha psi(d.grad mu/alpha): the alpha cancels, d sigma(d)/d grad mu = psi'(a) d
+  // = -erfc(a)/2 d, with erfc(a) = ec_over psi
+  r.dg = (-0.5f * rho * ps * ec_over) * d;
   const float dsig = S * (-(lamp * u + lam) / f.var) + rho * ps * ea_over * alpha / sig;
   r.dvar = dsig / (2.0f * sig);
   r.dl = -rho * ps * ea_over * alpha * (o.alpha_scale * kInvSqrt2);  // 1/l = alpha_scale/sqrt2

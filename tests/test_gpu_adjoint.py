@@ -123,6 +123,25 @@ def test_gradients_match_oracle_finite_differences():
     blk_sum = np.array([dm[blk].sum() for dm in res["dm"]])
     m, se = _mean_se(blk_sum)
     assert abs(m - fd) < 4 * math.sqrt(se ** 2 + fd_se ** 2) + 0.02 * abs(fd), ("mean block", m, se, fd, fd_se)
+    # a linear ramp of the mean, mean += eps (p.e): it turns grad mu by eps e everywhere,
+    # which the block above (grad mu unchanged inside it) hardly exercises
+    ramp = _ramp(obj)
+    op, om = dict(obj), dict(obj)
+    op["mean"] = obj["mean"] + epsm * ramp
+    om["mean"] = obj["mean"] - epsm * ramp
+    Sp = oracle.Scene({"objects": [op], "light": sc["light"]})
+    Sm = oracle.Scene({"objects": [om], "light": sc["light"]})
+    s, s2, _ = oracle.render_diff(Sp, Sm, cam, dict(wl["opts"], spp=ospp, seed=7))
+    fd = s[..., 0].sum() / ospp / (2 * epsm)
+    fd_se = math.sqrt(max(np.sum(s2[..., 0] / ospp - (s[..., 0] / ospp) ** 2), 0) / ospp) / (2 * epsm)
+    m, se = _mean_se([(dm * ramp).sum() for dm in res["dm"]])
+    assert abs(m - fd) < 4 * math.sqrt(se ** 2 + fd_se ** 2) + 0.02 * abs(fd), ("mean ramp", m, se, fd, fd_se)
+
+
+def _ramp(obj, e=(0.6, -0.48, 0.64)):
+    """p.e at every node of the object's grid (the nodes' world coordinates)."""
+    p = W.node_coords(obj["bbox_min"], obj["bbox_max"], obj["mean"].shape[::-1])
+    return p @ np.asarray(e)
 
 
 def test_gradients_match_gpu_finite_differences_with_common_random_numbers():
@@ -137,7 +156,8 @@ def test_gradients_match_gpu_finite_differences_with_common_random_numbers():
     seeds = list(range(21, 29))
     res = _adjoint_runs(sc, cam, dict(wl["opts"], spp=4096), d_image, seeds=seeds)
     eps = 0.01
-    fds_l, fds_v = [], []
+    ramp = _ramp(obj)
+    fds_l, fds_v, fds_r = [], [], []
     for sd in seeds:
         vals = []
         for sign in (1, -1):
@@ -155,9 +175,18 @@ def test_gradients_match_gpu_finite_differences_with_common_random_numbers():
             img, _, _ = gpss.render(S, cam, dict(wl["opts"], spp=4096, seed=sd))
             vals.append(float(img[..., 0].double().sum()))
         fds_v.append((vals[0] - vals[1]) / (2 * eps))
-    # adjoint of the variance scale: sum_j var_j d/dvar_j
+        vals = []
+        for sign in (1, -1):
+            o = dict(obj)
+            o["mean"] = (obj["mean"] + sign * 2e-3 * ramp).astype(np.float32)
+            S = gpss.Scene({"objects": [o], "light": sc["light"]})
+            img, _, _ = gpss.render(S, cam, dict(wl["opts"], spp=4096, seed=sd))
+            vals.append(float(img[..., 0].double().sum()))
+        fds_r.append((vals[0] - vals[1]) / 4e-3)
+    # adjoint of the variance scale: sum_j var_j d/dvar_j; of the mean ramp: sum_j (p_j.e) d/dmean_j
     adj_v = np.array([(dv * obj["var"]).sum() for dv in res["dv"]])
-    for name, fd, adj in (("l", fds_l, res["l"]), ("var scale", fds_v, adj_v)):
+    adj_r = np.array([(dm * ramp).sum() for dm in res["dm"]])
+    for name, fd, adj in (("l", fds_l, res["l"]), ("var scale", fds_v, adj_v), ("mean ramp", fds_r, adj_r)):
         a, ase = _mean_se(adj)
         f, fse = _mean_se(fd)
         assert abs(a - f) < 4 * math.sqrt(ase ** 2 + fse ** 2) + 0.03 * abs(f), (name, a, ase, f, fse)
@@ -206,7 +235,7 @@ def test_full_size_differentiable_voxels_against_finite_differences():
     moved by +-eps together) with common random numbers.  eps = 2e-3 keeps the
     difference in the linear regime of the shell's density (a node moved by 1e-2
     shifts mu/sigma by up to ~0.7 there); the exact visible-normal sampler (21x less
-    path variance than the mixture on these scenes) and 256 seeds give the
+    path variance than the mixture on these scenes) and 2048 seeds give the
     difference the power to resolve the gradient at this size (the small-scene tests
     cover the mixture against the oracle)."""
     import torch
@@ -226,7 +255,7 @@ def test_full_size_differentiable_voxels_against_finite_differences():
     S = gpss.Scene(sc)
     w = torch.as_tensor(wimg).cuda()
     eps = 2e-3
-    seeds = list(range(1000, 1256))
+    seeds = list(range(1000, 3048))
     vals = {}
     for sign in (1, -1):
         m = mean.copy()
