@@ -53,8 +53,9 @@ typedef enum {
   GPSS_ERR_UNSUPPORTED = 5
 } gpss_status;
 
-/* One GPSS object.  mean/variance/albedo may be host or device memory (they are
- * copied by gpss_scene_create / gpss_scene_update with cudaMemcpyDefault). */
+/* One GPSS object.  mean/variance/albedo (and tangent, correlation_scale) may be
+ * host or device memory (they are copied by gpss_scene_create / gpss_scene_update
+ * with cudaMemcpyDefault). */
 typedef struct {
   int nx, ny, nz;              /* nodes per axis, each >= 2                        */
   float bbox_min[3], bbox_max[3];
@@ -62,8 +63,21 @@ typedef struct {
   const float* variance;       /* nx*ny*nz variance sigma^2, finite and > 0        */
   const float* albedo;         /* albedo_channels planes of nx*ny*nz, F in [0,1]   */
   int albedo_channels;         /* 1 or 3                                           */
-  float length_scale;          /* isotropic SE correlation l > 0 (Eq. roughness)   */
+  float length_scale;          /* SE correlation l_t > 0 (Eq. roughness)           */
   int ndf;                     /* gpss_ndf: the macrofacet's NDF                   */
+  /* Anisotropic and non-stationary kernels (optional; zero/NULL = the isotropic
+   * stationary kernel).  The gradient of the GPSS at x has the covariance
+   * sigma^2 diag(1/l_t^2, 1/l_b^2, 1/l_n^2) in the local frame (t, b, n) of Sec. 4.2
+   * (the paper's alpha_x, alpha_y, alpha_z = sqrt(2) sigma/l_t, /l_b, /l_n), where
+   * n = grad mu/|grad mu| (world z where grad mu = 0), t = the tangent field's
+   * component orthogonal to n (any unit vector orthogonal to n where it vanishes)
+   * and b = n x t.  Every l is multiplied by the correlation-scale factor s(x) > 0
+   * (a spatially varying correlation: with length_scale = 1 the grid is l(x)). */
+  float length_scale_b;        /* l_b > 0, or 0 for l_t; l_b != l_t needs tangent   */
+  float length_scale_n;        /* l_n > 0, or 0 for l_t                             */
+  const float* tangent;        /* NULL or 3 planes (x, y, z) of nx*ny*nz, finite;    */
+                               /* trilinearly interpolated                         */
+  const float* correlation_scale; /* NULL or nx*ny*nz factors s > 0, trilinear     */
 } gpss_object_desc;
 
 /* NDF of an object.  GPSS_NDF_GPSS: the generalized macrofacet of the GPSS
@@ -75,7 +89,8 @@ typedef struct {
  * infinite correlation along n) or GPSS_NDF_GGX.  Height-field objects sample their
  * visible normals exactly when the ray arrives from above n (weight F) and the
  * hemisphere uniformly otherwise; mix_R does not apply to them.  The adjoint
- * supports GPSS_NDF_GPSS only. */
+ * supports GPSS_NDF_GPSS only.  Height-field objects take the isotropic
+ * roughness (l_b = l_n = l_t, no tangent field; a correlation-scale grid is allowed). */
 typedef enum { GPSS_NDF_GPSS = 0, GPSS_NDF_BECKMANN = 1, GPSS_NDF_GGX = 2 } gpss_ndf;
 
 typedef enum { GPSS_LIGHT_DIRECTIONAL = 0, GPSS_LIGHT_SKY = 1, GPSS_LIGHT_UNIFORM = 2 } gpss_light_type;
@@ -133,10 +148,14 @@ typedef struct {
  * cell of `majorant_brick` x the finest field cell; 0 selects 1).  1 <= n_objs <= 4.
  * light may be NULL (directional light from +z, irradiance 1).  Synchronises
  * `stream` (device-side validation).  INVALID_ARG on bad sizes, non-positive or
- * non-finite variance, albedo outside [0,1], channels not 1/3, l <= 0. */
+ * non-finite variance, albedo outside [0,1], channels not 1/3, l <= 0, a
+ * correlation-scale factor <= 0 or non-finite, a non-finite tangent, l_b != l_t
+ * without a tangent field, or a height-field object with an anisotropic kernel. */
 gpss_status gpss_scene_create(const gpss_object_desc* objs, int n_objs, const gpss_light_desc* light,
                               int majorant_brick, gpss_stream stream, gpss_scene* out);
-/* Re-copies the grids (same sizes as at creation) and rebuilds the majorant. */
+/* Re-copies the grids (same sizes as at creation) and rebuilds the majorant.  The
+ * kernel description may change; an object that gains a tangent field or a
+ * correlation-scale grid gets its device copy allocated here. */
 gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* objs, int n_objs, gpss_stream stream);
 /* Empty-space skipping of the majorant traversal: each majorant cell stores the
  * largest radius r in {0, 1, 2, ..., 2^(skip_levels-1)} whose cube of (2r+1)^3
@@ -196,8 +215,11 @@ gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam, const gpss
 
 /* Path-replay adjoint (gradients of the image's expectation).  d_image: H*W*3
  * (dLoss/dimage, device).  Gradients are ACCUMULATED (+=) into d_mean, d_variance
- * (nx*ny*nz each), d_albedo (channels planes) and d_length_scale (1 float); any
- * output may be NULL.  Single-object scenes only (UNSUPPORTED otherwise).  The
+ * (nx*ny*nz each), d_albedo (channels planes), d_length_scale (1 float: the
+ * object's l_t) and d_correlation_scale (nx*ny*nz: the correlation-scale factors;
+ * only for an object that has them, INVALID_ARG otherwise); any output may be
+ * NULL.  Single-object scenes with the GPSS NDF and an isotropic kernel only
+ * (UNSUPPORTED otherwise; the correlation-scale grid is supported).  The
  * paths are those of gpss_render with equal camera and options: if the scene
  * kept their per-path radiance (GPSS_FLAG_KEEP_PATH_RADIANCE on that render, no
  * scene update since) it is reused, else the forward paths are traced first.
@@ -205,7 +227,8 @@ gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam, const gpss
  * radiance (expected 0). */
 gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts,
                                 const float* d_image, float* d_mean, float* d_variance, float* d_albedo,
-                                float* d_length_scale, gpss_stats* stats, gpss_stream stream);
+                                float* d_length_scale, float* d_correlation_scale, gpss_stats* stats,
+                                gpss_stream stream);
 
 /* ---------------------------------------------------------------- batches */
 

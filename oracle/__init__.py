@@ -51,6 +51,8 @@ class _Object(ctypes.Structure):
         ("mean", ctypes.POINTER(ctypes.c_float)), ("var", ctypes.POINTER(ctypes.c_float)),
         ("albedo", ctypes.POINTER(ctypes.c_float)), ("channels", ctypes.c_int),
         ("length_scale", ctypes.c_double), ("ndf", ctypes.c_int),
+        ("length_scale_b", ctypes.c_double), ("length_scale_n", ctypes.c_double),
+        ("tangent", ctypes.POINTER(ctypes.c_float)), ("cscale", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -172,6 +174,18 @@ class Scene:
             ob.channels = alb.shape[0]
             ob.length_scale = float(o["length_scale"])
             ob.ndf = NDF_KINDS[o.get("ndf", "gpss")]
+            ob.length_scale_b = float(o.get("length_scale_b", 0.0))
+            ob.length_scale_n = float(o.get("length_scale_n", 0.0))
+            if o.get("tangent") is not None:
+                t = np.ascontiguousarray(o["tangent"], dtype=np.float32)
+                assert t.shape == (3,) + mean.shape
+                self._keep.append(t)
+                ob.tangent = t.ctypes.data_as(fp)
+            if o.get("correlation_scale") is not None:
+                c = np.ascontiguousarray(o["correlation_scale"], dtype=np.float32)
+                assert c.shape == mean.shape and np.all(c > 0)
+                self._keep.append(c)
+                ob.cscale = c.ctypes.data_as(fp)
         self.s = _Scene()
         self.s.objs = ctypes.cast(self._objs, ctypes.POINTER(_Object))
         self.s.n_objs = len(objs)

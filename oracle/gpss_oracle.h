@@ -15,7 +15,10 @@
  *    kernel (Eq. se_kernel).  mu and sigma^2 are node-centred grids, trilinearly
  *    interpolated; grad mu is the analytic gradient of that interpolant.
  *  - Under the independence assumption (Sec. 4.2) the gradient at a point is
- *    g ~ N(grad mu, (sigma/l)^2 I) independent of f ~ N(mu, sigma^2).
+ *    g ~ N(grad mu, (sigma/l)^2 I) independent of f ~ N(mu, sigma^2); with an
+ *    anisotropic kernel its covariance is sigma^2 diag(1/l_t^2, 1/l_b^2, 1/l_n^2)
+ *    in the local frame of Sec. 4.2 (mean gradient along z), and a non-stationary
+ *    kernel scales every l by a factor grid s(x).
  *  - Extinction for a ray marching along d (omega_o in Eq. generalized_sigma_t):
  *      sigma_t(x,d) = rho(x) * sigma(d),
  *      rho   = phi(mu;0,sigma^2) / Phi(mu;0,sigma^2)      (Eq. macro_sigma_t)
@@ -41,9 +44,18 @@ typedef struct {
   const float* var;          /* nx*ny*nz variance sigma^2 (> 0)              */
   const float* albedo;       /* channels planes of nx*ny*nz, F in [0,1]      */
   int channels;              /* 1 or 3                                       */
-  double length_scale;       /* isotropic SE correlation l (> 0)             */
+  double length_scale;       /* SE correlation l_t (> 0)                      */
   int ndf;                   /* ORC_NDF_GPSS (Sec. 4.2) or a height-field     */
                              /* macrofacet NDF (Sec. 4.1)                     */
+  /* Anisotropic / non-stationary kernel (0 / NULL: isotropic, stationary).
+   * Gradient covariance sigma^2 diag(1/l_t^2, 1/l_b^2, 1/l_n^2) in the frame
+   * (t, b, n): n = grad mu/|grad mu| (world z where grad mu = 0), t = the tangent
+   * field minus its n component, normalised (any unit vector orthogonal to n where
+   * that vanishes), b = n x t.  Every l is multiplied by the factor s(x).           */
+  double length_scale_b;     /* l_b (0: l_t)                                  */
+  double length_scale_n;     /* l_n (0: l_t)                                  */
+  const float* tangent;      /* NULL or 3 planes of nx*ny*nz: t(x), trilinear  */
+  const float* cscale;       /* NULL or nx*ny*nz: s(x) > 0, trilinear         */
 } orc_object;
 
 /* NDF of an object.  GPSS: the generalized macrofacet of Sec. 4.2 (default).

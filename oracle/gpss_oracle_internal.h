@@ -20,6 +20,10 @@ typedef struct {
   double G;       /* |grad mu|                          */
   double nhat[3]; /* grad mu / G (0 when G == 0)        */
   int ndf;        /* the object's NDF kind              */
+  /* kernel: roughness per axis of the frame (t, b, n); aniso = not all equal */
+  double ax, ay, az;
+  double ft[3], fb[3], fn[3];
+  int aniso;
 } orc_fpt;
 
 int orc_point(const orc_object* o, const double x[3], orc_fpt* p);

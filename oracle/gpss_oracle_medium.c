@@ -148,14 +148,81 @@ int orc_field(const orc_object* o, const double x[3], double* mu, double grad[3]
   return 1;
 }
 
+/* Trilinear interpolation of a node grid (plane `c` of a multi-plane grid) at x,
+ * which lies in the box (same cell rule as orc_field). */
+static double interp_plane(const orc_object* o, const float* grid, int c, const double x[3]) {
+  const int n[3] = {o->nx, o->ny, o->nz};
+  int i[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    double h = (o->bmax[a] - o->bmin[a]) / (double)(n[a] - 1);
+    double f = (x[a] - o->bmin[a]) / h;
+    int ia = (int)floor(f);
+    if (ia < 0) ia = 0;
+    if (ia > n[a] - 2) ia = n[a] - 2;
+    double wa = f - ia;
+    i[a] = ia;
+    w[a] = wa < 0.0 ? 0.0 : (wa > 1.0 ? 1.0 : wa);
+  }
+  const size_t plane = (size_t)n[0] * n[1] * n[2];
+  double v = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    int cx = k & 1, cy = (k >> 1) & 1, cz = (k >> 2) & 1;
+    size_t idx = (size_t)(i[0] + cx) + (size_t)n[0] * ((size_t)(i[1] + cy) + (size_t)n[1] * (i[2] + cz));
+    double wt = (cx ? w[0] : 1.0 - w[0]) * (cy ? w[1] : 1.0 - w[1]) * (cz ? w[2] : 1.0 - w[2]);
+    v += wt * (double)grid[c * plane + idx];
+  }
+  return v;
+}
+
+static void basis(const double z[3], double t1[3], double t2[3]);
+
 int orc_point(const orc_object* o, const double x[3], orc_fpt* p) {
   if (!orc_field(o, x, &p->mu, p->g, &p->var, p->F)) return 0;
   p->sigma = sqrt(p->var);
-  p->alpha = ORC_SQRT2 * p->sigma / o->length_scale;  /* Eq. roughness */
   p->G = sqrt(p->g[0] * p->g[0] + p->g[1] * p->g[1] + p->g[2] * p->g[2]);
   for (int a = 0; a < 3; ++a) p->nhat[a] = p->G > 0.0 ? p->g[a] / p->G : 0.0;
   p->ndf = o->ndf;
+  /* correlation lengths at x: l_a s(x) (Eq. roughness per axis of the local frame) */
+  double s = o->cscale ? interp_plane(o, o->cscale, 0, x) : 1.0;
+  double lt = o->length_scale * s;
+  double lb = (o->length_scale_b > 0.0 ? o->length_scale_b : o->length_scale) * s;
+  double ln = (o->length_scale_n > 0.0 ? o->length_scale_n : o->length_scale) * s;
+  p->alpha = ORC_SQRT2 * p->sigma / lt;
+  p->ax = p->alpha;
+  p->ay = ORC_SQRT2 * p->sigma / lb;
+  p->az = ORC_SQRT2 * p->sigma / ln;
+  p->aniso = (lb != lt || ln != lt);
+  /* frame: n from the mean gradient, t from the tangent field */
+  if (p->G > 0.0) {
+    for (int a = 0; a < 3; ++a) p->fn[a] = p->nhat[a];
+  } else {
+    p->fn[0] = 0.0; p->fn[1] = 0.0; p->fn[2] = 1.0;
+  }
+  double t[3] = {0.0, 0.0, 0.0};
+  if (o->tangent)
+    for (int a = 0; a < 3; ++a) t[a] = interp_plane(o, o->tangent, a, x);
+  double tn = t[0] * p->fn[0] + t[1] * p->fn[1] + t[2] * p->fn[2];
+  double tp[3] = {t[0] - tn * p->fn[0], t[1] - tn * p->fn[1], t[2] - tn * p->fn[2]};
+  double l2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  if (l2 > 1e-12 * t2 && l2 > 0.0) {
+    double il = 1.0 / sqrt(l2);
+    for (int a = 0; a < 3; ++a) p->ft[a] = tp[a] * il;
+    p->fb[0] = p->fn[1] * p->ft[2] - p->fn[2] * p->ft[1];
+    p->fb[1] = p->fn[2] * p->ft[0] - p->fn[0] * p->ft[2];
+    p->fb[2] = p->fn[0] * p->ft[1] - p->fn[1] * p->ft[0];
+  } else {
+    basis(p->fn, p->ft, p->fb);
+  }
   return 1;
+}
+
+/* components of v in the kernel frame (t, b, n) */
+static void kernel_frame_coords(const orc_fpt* p, const double v[3], double out[3]) {
+  out[0] = v[0] * p->ft[0] + v[1] * p->ft[1] + v[2] * p->ft[2];
+  out[1] = v[0] * p->fb[0] + v[1] * p->fb[1] + v[2] * p->fb[2];
+  out[2] = v[0] * p->fn[0] + v[1] * p->fn[1] + v[2] * p->fn[2];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -226,6 +293,12 @@ double orc_projected_area_world(const double d[3], const orc_fpt* p) {
     to_frame(d, p->nhat, dl);
     return orc_projected_area_hf(dl, p->ndf, p->alpha);
   }
+  if (p->aniso) {
+    /* the paper's local frame: mean gradient (0, 0, G), roughness per axis */
+    double dl[3];
+    kernel_frame_coords(p, d, dl);
+    return orc_projected_area_local(dl, p->G, p->ax, p->ay, p->az);
+  }
   double dg = d[0] * p->g[0] + d[1] * p->g[1] + d[2] * p->g[2];
   double a = dg / p->alpha;
   return p->alpha / (2.0 * ORC_SQRTPI) * exp(-a * a) - 0.5 * dg * erfc(a);
@@ -278,6 +351,11 @@ double orc_ndf_world(const double m[3], const orc_fpt* p) {
     double ml[3];
     to_frame(m, p->nhat, ml);
     return orc_ndf_hf(ml, p->ndf, p->alpha);
+  }
+  if (p->aniso) {
+    double ml[3];
+    kernel_frame_coords(p, m, ml);
+    return orc_ndf_local(ml, p->G, p->ax, p->ay, p->az);
   }
   double c = 1.0;
   if (p->G > 0.0) c = m[0] * p->nhat[0] + m[1] * p->nhat[1] + m[2] * p->nhat[2];

@@ -46,7 +46,8 @@ using namespace gpss;
 
 extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts,
                                            const float* d_image, float* d_mean, float* d_variance, float* d_albedo,
-                                           float* d_length_scale, gpss_stats* stats, gpss_stream stream) {
+                                           float* d_length_scale, float* d_correlation_scale, gpss_stats* stats,
+                                           gpss_stream stream) {
   if (!s || !d_image) { set_error("null scene or d_image"); return GPSS_ERR_INVALID_ARG; }
   gpss_status st = check_opts(opts);
   if (st != GPSS_OK) return st;
@@ -54,6 +55,14 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   if (s->obj[0].ndf != GPSS_NDF_GPSS) {
     set_error("the adjoint supports the GPSS NDF only (not the height-field macrofacets)");
     return GPSS_ERR_UNSUPPORTED;
+  }
+  if (s->obj[0].anisotropic()) {
+    set_error("the adjoint supports isotropic kernels only (l_b = l_n = l_t, no tangent field)");
+    return GPSS_ERR_UNSUPPORTED;
+  }
+  if (d_correlation_scale && !s->obj[0].cscale) {
+    set_error("d_correlation_scale given for an object without a correlation-scale grid");
+    return GPSS_ERR_INVALID_ARG;
   }
   CameraDev C;
   if (!camera_dev(cam, &C)) return GPSS_ERR_INVALID_ARG;
@@ -136,18 +145,26 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   }
   A.d_alb = d_albedo;
   A.d_l = d_length_scale;
+  A.d_cs = d_correlation_scale;
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
   const SceneDev S = scene_dev(s);
-  if (S.mg.hot > 0.0f)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, true, false>, kPathBlock, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<true, false, false>, kPathBlock, 0);
+  // instances: local majorants or not; the general one where the object has a
+  // correlation-scale grid (the only general feature the adjoint accepts)
+  const bool local = S.mg.hot > 0.0f, gen = scene_general(S);
+  const void* fn = local ? (gen ? (const void*)k_path<true, true, true> : (const void*)k_path<true, true, false>)
+                         : (gen ? (const void*)k_path<true, false, true> : (const void*)k_path<true, false, false>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPathBlock, 0);
   const int agrid = sms * (per_sm > 0 ? per_sm : 1);
-  if (S.mg.hot > 0.0f)
-    k_path<true, true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+  float* const nf = nullptr;
+  if (local && gen)
+    k_path<true, true, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
+  else if (local)
+    k_path<true, true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
+  else if (gen)
+    k_path<true, false, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
   else
-    k_path<true, false, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nullptr, nullptr, nullptr, nullptr, s->counters, A);
+    k_path<true, false, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   if (A.d_mv) {

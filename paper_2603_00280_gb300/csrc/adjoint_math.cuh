@@ -45,7 +45,7 @@ struct DSig {
 
 __device__ __forceinline__ DSig dsigma_t(const ObjectDev& o, const Field& f, V3 d) {
   const float sig = sqrtf(f.var);
-  const float alpha = sig * o.alpha_scale;
+  const float alpha = sig * f.as;  // sqrt2 sigma/(s(x) l)
   const float u = f.mu / sig;
   const float lam = inv_mills(u);
   const float lamp = -lam * (u + lam);
@@ -61,7 +61,8 @@ __device__ __forceinline__ DSig dsigma_t(const ObjectDev& o, const Field& f, V3 
   r.dg = (-0.5f * rho * ps * ec_over) * d;
   const float dsig = S * (-(lamp * u + lam) / f.var) + rho * ps * ea_over * alpha / sig;
   r.dvar = dsig / (2.0f * sig);
-  r.dl = -rho * ps * ea_over * alpha * (o.alpha_scale * kInvSqrt2);  // 1/l = alpha_scale/sqrt2
+  // d/dl of the object's l (l(x) = s(x) l, alpha proportional to 1/l): 1/l = alpha_scale/sqrt2
+  r.dl = -rho * ps * ea_over * alpha * (o.alpha_scale * kInvSqrt2);
   return r;
 }
 
@@ -98,6 +99,19 @@ static __device__ __noinline__ void scatter_field(const ObjectDev& o, V3 x, floa
     const float gx = sx * ay * az * o.inv_h[0], gy = ax * syy * az * o.inv_h[1], gz = ax * ay * szz * o.inv_h[2];
     const int idx = b + cx + sy * cy + sz * cz;
     atomicAdd(dmv + idx, make_float2(fmaf(cmu, w, fmaf(cg.x, gx, fmaf(cg.y, gy, cg.z * gz))), cvar * w));
+  }
+}
+
+// Scatters c * d(value at x)/d(node) of a trilinearly interpolated scalar node grid.
+static __device__ __noinline__ void scatter_scalar(const ObjectDev& o, V3 x, float c, float* __restrict__ d) {
+  float wx, wy, wz;
+  const int b = cell_of(o, x, wx, wy, wz);
+  const int sy = o.n[0], sz = o.n[0] * o.n[1];
+#pragma unroll
+  for (int corner = 0; corner < 8; ++corner) {
+    const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+    const float w = (cx ? wx : 1.0f - wx) * (cy ? wy : 1.0f - wy) * (cz ? wz : 1.0f - wz);
+    atomicAdd(d + b + cx + sy * cy + sz * cz, c * w);
   }
 }
 

@@ -58,7 +58,7 @@ __device__ __forceinline__ int find_job(const long long* __restrict__ begins, in
 
 // The persistent kernel over all jobs: k_path's loop with per-lane job lookup.
 // Register cap 96 for every block size, so that 640 lanes per SM stay resident.
-template <int BLOCK, bool LOCAL, bool HF>
+template <int BLOCK, bool LOCAL, bool GEN>
 __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const long long* __restrict__ begins,
                                         int n_jobs, long long total, int chunk, int shade_min,
                                         unsigned long long* __restrict__ counters) {
@@ -87,10 +87,10 @@ __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const l
     const JobDev& J = jobs[s.job];
     const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
     if (wait_mask && (__popc(wait_mask) >= shade_min || wait_mask == act)) {
-      if (s.waiting) lane_shade<false, HF>(s, J.S, J.P, A, nullptr, c);
+      if (s.waiting) lane_shade<false, GEN>(s, J.S, J.P, A, nullptr, c);
     }
     if (!s.active || s.waiting) continue;
-    if (lane_step<false, LOCAL, HF>(s, J.S, J.P, A, nullptr, c)) lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
+    if (lane_step<false, LOCAL, GEN>(s, J.S, J.P, A, nullptr, c)) lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
   }
   flush_counters(c, counters, nullptr);
 }
@@ -107,46 +107,46 @@ __global__ void k_zero_films(const JobDev* __restrict__ jobs) {
   }
 }
 
-template <int BLOCK, bool LOCAL, bool HF>
+template <int BLOCK, bool LOCAL, bool GEN>
 static int batch_grid(int device) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK, LOCAL, HF>, BLOCK, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK, LOCAL, GEN>, BLOCK, 0);
   return sms * std::max(per_sm, 1);
 }
 
-template <bool LOCAL, bool HF>
+template <bool LOCAL, bool GEN>
 static int grid_for_t(int block, int device) {
   switch (block) {
-    case 64: return batch_grid<64, LOCAL, HF>(device);
-    case 256: return batch_grid<256, LOCAL, HF>(device);
-    default: return batch_grid<128, LOCAL, HF>(device);
+    case 64: return batch_grid<64, LOCAL, GEN>(device);
+    case 256: return batch_grid<256, LOCAL, GEN>(device);
+    default: return batch_grid<128, LOCAL, GEN>(device);
   }
 }
 
-static int grid_for(int block, bool local, bool hf, int device) {
-  if (local) return hf ? grid_for_t<true, true>(block, device) : grid_for_t<true, false>(block, device);
-  return hf ? grid_for_t<false, true>(block, device) : grid_for_t<false, false>(block, device);
+static int grid_for(int block, bool local, bool gen, int device) {
+  if (local) return gen ? grid_for_t<true, true>(block, device) : grid_for_t<true, false>(block, device);
+  return gen ? grid_for_t<false, true>(block, device) : grid_for_t<false, false>(block, device);
 }
 
-template <bool LOCAL, bool HF>
+template <bool LOCAL, bool GEN>
 static void launch_batch_t(int block, int grid, const JobDev* jobs, const long long* begins, int n, long long total,
                            int chunk, int shade_min, unsigned long long* counters, cudaStream_t st) {
   switch (block) {
-    case 64: k_batch<64, LOCAL, HF><<<grid, 64, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-    case 256: k_batch<256, LOCAL, HF><<<grid, 256, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-    default: k_batch<128, LOCAL, HF><<<grid, 128, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    case 64: k_batch<64, LOCAL, GEN><<<grid, 64, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    case 256: k_batch<256, LOCAL, GEN><<<grid, 256, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    default: k_batch<128, LOCAL, GEN><<<grid, 128, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
   }
 }
 
-static cudaError_t launch_batch(int block, bool local, bool hf, int grid, const JobDev* jobs, const long long* begins,
+static cudaError_t launch_batch(int block, bool local, bool gen, int grid, const JobDev* jobs, const long long* begins,
                                 int n, long long total, int chunk, int shade_min, unsigned long long* counters,
                                 cudaStream_t st) {
   if (local) {
-    if (hf) launch_batch_t<true, true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+    if (gen) launch_batch_t<true, true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
     else launch_batch_t<true, false>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
   } else {
-    if (hf) launch_batch_t<false, true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+    if (gen) launch_batch_t<false, true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
     else launch_batch_t<false, false>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
   }
   return cudaGetLastError();
@@ -176,7 +176,7 @@ struct gpss_batch_s {
   cudaGraphExec_t exec = nullptr;
   bool table_valid = false;
   bool local = false;              // some job's scene uses local majorants
-  bool hf = false;                 // some job's scene has a height-field object
+  bool gen = false;                // some job's scene needs the general kernel instances
   int block = 128, shade_min = kBatchDefaultShade, chunk = kBatchDefaultChunk, grid = 0;
 };
 
@@ -214,12 +214,12 @@ static void fill_table(const gpss_batch_s* b, JobDev* out, float* const* images,
 static float time_shape(gpss_batch b, int block, int shade_min, int chunk, const JobDev* jobs, const long long* begins,
                         long long total, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, bool warm,
                         cudaError_t* err) {
-  const int grid = grid_for(block, b->local, b->hf, b->device);
+  const int grid = grid_for(block, b->local, b->gen, b->device);
   float ms = 0.0f;
   for (int rep = warm ? 0 : 1; rep < 2; ++rep) {
     cudaMemsetAsync(b->counters, 0, 16 * sizeof(unsigned long long), st);
     cudaEventRecord(e0, st);
-    if ((*err = launch_batch(block, b->local, b->hf, grid, jobs, begins, b->n, total, chunk, shade_min, b->counters, st)) != cudaSuccess)
+    if ((*err = launch_batch(block, b->local, b->gen, grid, jobs, begins, b->n, total, chunk, shade_min, b->counters, st)) != cudaSuccess)
       return -1.0f;
     cudaEventRecord(e1, st);
     if ((*err = cudaEventSynchronize(e1)) != cudaSuccess) return -1.0f;
@@ -325,7 +325,7 @@ static gpss_status capture_graph(gpss_batch b) {
     return cuda_fail(e, "begin capture");
   cudaMemsetAsync(b->counters, 0, 16 * sizeof(unsigned long long), b->capture);
   k_zero_films<<<dim3(64, b->n), 256, 0, b->capture>>>(b->table_dev);
-  cudaError_t le = launch_batch(b->block, b->local, b->hf, b->grid, b->table_dev, b->begins_dev, b->n, b->total, b->chunk,
+  cudaError_t le = launch_batch(b->block, b->local, b->gen, b->grid, b->table_dev, b->begins_dev, b->n, b->total, b->chunk,
                                 b->shade_min, b->counters, b->capture);
   e = cudaStreamEndCapture(b->capture, &b->graph);
   if (le != cudaSuccess) return cuda_fail(le, "batch launch (capture)");
@@ -371,7 +371,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
     }
     if (!camera_dev(&cams[i], &b->cams[i])) { free_batch(b); return GPSS_ERR_INVALID_ARG; }
     if (scene_dev(scenes[i]).mg.hot > 0.0f) b->local = true;
-    if (scene_has_heightfield(scene_dev(scenes[i]))) b->hf = true;
+    if (scene_general(scene_dev(scenes[i]))) b->gen = true;
     PathArgs& P = b->args[i];
     P.spp = opts[i].spp;
     P.max_bounces = opts[i].max_bounces;
@@ -408,7 +408,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
   } else {
     b->block = block_size;
   }
-  b->grid = grid_for(b->block, b->local, b->hf, dev);
+  b->grid = grid_for(b->block, b->local, b->gen, dev);
   if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) { st = cuda_fail(e, "batch setup"); free_batch(b); return st; }
   if ((st = capture_graph(b)) != GPSS_OK) { free_batch(b); return st; }
   *out = b;

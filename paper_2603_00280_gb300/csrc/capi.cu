@@ -116,7 +116,37 @@ static gpss_status check_objects(const gpss_object_desc* objs, int n) {
       set_error("object %d: unknown ndf %d", k, o.ndf);
       return GPSS_ERR_INVALID_ARG;
     }
+    for (float l : {o.length_scale_b, o.length_scale_n})
+      if (!(l == 0.0f || (l > 0.0f && std::isfinite(l)))) {
+        set_error("object %d: length_scale_b / length_scale_n must be 0 or finite and > 0", k);
+        return GPSS_ERR_INVALID_ARG;
+      }
+    const float lb = o.length_scale_b > 0.0f ? o.length_scale_b : o.length_scale;
+    const float ln = o.length_scale_n > 0.0f ? o.length_scale_n : o.length_scale;
+    if (lb != o.length_scale && !o.tangent) {
+      set_error("object %d: length_scale_b != length_scale needs a tangent field", k);
+      return GPSS_ERR_INVALID_ARG;
+    }
+    if (o.ndf != GPSS_NDF_GPSS && (lb != o.length_scale || ln != o.length_scale || o.tangent)) {
+      set_error("object %d: height-field macrofacets take an isotropic kernel", k);
+      return GPSS_ERR_INVALID_ARG;
+    }
   }
+  return GPSS_OK;
+}
+
+// Resolves an object's kernel description and makes its optional device grids match
+// the descriptor (allocated where it has them, freed where it no longer does).
+static gpss_status set_kernel(ObjectHost& o, const gpss_object_desc& d) {
+  o.length_scale = d.length_scale;
+  o.length_scale_b = d.length_scale_b > 0.0f ? d.length_scale_b : d.length_scale;
+  o.length_scale_n = d.length_scale_n > 0.0f ? d.length_scale_n : d.length_scale;
+  cudaError_t e = cudaSuccess;
+  if (d.correlation_scale && !o.cscale) e = cudaMalloc(&o.cscale, o.nodes * sizeof(float));
+  if (!d.correlation_scale && o.cscale) { cudaFree(o.cscale); o.cscale = nullptr; }
+  if (e == cudaSuccess && d.tangent && !o.tangent) e = cudaMalloc(&o.tangent, 3 * o.nodes * sizeof(float));
+  if (!d.tangent && o.tangent) { cudaFree(o.tangent); o.tangent = nullptr; }
+  if (e != cudaSuccess) return cuda_fail(e, "kernel grid allocation");
   return GPSS_OK;
 }
 
@@ -145,6 +175,8 @@ static void free_scene(gpss_scene s) {
   for (int k = 0; k < kMaxObjects; ++k) {
     cudaFree(s->obj[k].mv);
     cudaFree(s->obj[k].albedo);
+    cudaFree(s->obj[k].cscale);
+    cudaFree(s->obj[k].tangent);
   }
   cudaFree(s->maj);
   cudaFree(s->skip);
@@ -235,6 +267,10 @@ extern "C" gpss_status gpss_scene_create(const gpss_object_desc* objs, int n_obj
       free_scene(s);
       return cuda_fail(e, "grid allocation");
     }
+    if ((st = set_kernel(o, objs[k])) != GPSS_OK) {
+      free_scene(s);
+      return st;
+    }
   }
   if ((e = cudaMalloc(&s->counters, 16 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&s->tmp_planes, 2 * max_nodes * sizeof(float))) != cudaSuccess ||
@@ -280,8 +316,8 @@ extern "C" gpss_status gpss_scene_update(gpss_scene s, const gpss_object_desc* o
         set_error("object %d: box differs from the scene's", k);
         return GPSS_ERR_INVALID_ARG;
       }
-    s->obj[k].length_scale = objs[k].length_scale;
     s->obj[k].ndf = objs[k].ndf;
+    if ((st = set_kernel(s->obj[k], objs[k])) != GPSS_OK) return st;
   }
   cudaStream_t cs = (cudaStream_t)stream;
   if ((st = scene_upload(s, objs, n_objs, cs)) != GPSS_OK) return st;

@@ -57,7 +57,7 @@ __global__ void k_sample_phase_vndf(const SceneDev S, int k, int n, const float*
   V3 F = v3(0, 0, 0);
   if (inside(o, x)) {
     const Field f = fetch(o, x);
-    const float alpha = sqrtf(f.var) * o.alpha_scale;
+    const float alpha = sqrtf(f.var) * f.as;
     const V3 d = ld3(din, i);
     const V3 u = ld3(u3, i);
     if (!phase_sample_vndf(projected_area(d, f, alpha), d, f, alpha, u.x, u.y, u.z, d2, wF, pd)) wF = 0.0f;

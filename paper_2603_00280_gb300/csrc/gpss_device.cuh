@@ -46,9 +46,17 @@ struct ObjectDev {
   int n[3];
   int channels;            // albedo channels, 1 or 3
   int ndf;                 // kNdfGpss or a height-field macrofacet NDF (gpss_ndf)
-  float alpha_scale;       // sqrt(2)/l: alpha = sigma * alpha_scale (Eq. roughness)
+  float alpha_scale;       // sqrt(2)/l_t: alpha = sigma * alpha_scale (Eq. roughness)
   const float2* mv;        // (mean, variance) per node
   const float* albedo;     // channels planes
+  // Anisotropic / non-stationary kernel (all neutral for the isotropic stationary one):
+  // gradient covariance sigma^2 diag(1/l_t^2, 1/l_b^2, 1/l_n^2) in the frame
+  // (tangent, bitangent, n = grad mu/|grad mu|), every l scaled by s(x).
+  float kb, kn;            // l_t/l_b, l_t/l_n: alpha_y = kb alpha, alpha_z = kn alpha
+  float amax;              // max(1, kb, kn)
+  const float* cscale;     // correlation-scale factor s per node, or null (s = 1)
+  const float* tangent;    // tangent field, 3 planes of nodes, or null
+  int general;             // kb != 1, kn != 1, cscale or tangent
 };
 
 // Majorant grid: piecewise-constant upper bound of sigma_t over all directions,
@@ -209,6 +217,10 @@ struct Field {
   float mu, var;
   V3 g;        // gradient of the mean interpolant
   int ndf;     // the object's NDF kind (gpss_ndf)
+  float as;    // alpha scale at x: sqrt(2)/(s(x) l_t), alpha = sigma * as
+  float cs;    // correlation-scale factor s(x)
+  float kb, kn;  // the object's l_t/l_b, l_t/l_n
+  V3 t;        // tangent field at x (zero without one)
 };
 
 enum NdfKind : int { kNdfGpss = 0, kNdfBeckmann = 1, kNdfGgx = 2 };
@@ -234,7 +246,8 @@ __device__ __forceinline__ bool inside(const ObjectDev& o, V3 x) {
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-__device__ __forceinline__ Field fetch(const ObjectDev& o, V3 x) {
+// Field of an object with the isotropic stationary kernel (the kernel members neutral).
+__device__ __forceinline__ Field fetch_iso(const ObjectDev& o, V3 x) {
   float wx, wy, wz;
   const int b = cell_of(o, x, wx, wy, wz);
   const int sx = 1, sy = o.n[0], sz = o.n[0] * o.n[1];
@@ -256,6 +269,44 @@ __device__ __forceinline__ Field fetch(const ObjectDev& o, V3 x) {
   const float s00 = lerpf(v000.y, v100.y, wx), s10 = lerpf(v010.y, v110.y, wx);
   const float s01 = lerpf(v001.y, v101.y, wx), s11 = lerpf(v011.y, v111.y, wx);
   f.var = lerpf(lerpf(s00, s10, wy), lerpf(s01, s11, wy), wz);
+  f.as = o.alpha_scale;
+  f.cs = 1.0f;
+  f.kb = 1.0f;
+  f.kn = 1.0f;
+  f.t = v3(0.0f, 0.0f, 0.0f);
+  return f;
+}
+
+// Trilinear interpolation of a scalar node grid in the cell with corner node b.
+__device__ __forceinline__ float trilerp(const float* __restrict__ p, int b, int sy, int sz, float wx, float wy,
+                                         float wz) {
+  p += b;
+  const float a0 = lerpf(lerpf(__ldg(p), __ldg(p + 1), wx), lerpf(__ldg(p + sy), __ldg(p + sy + 1), wx), wy);
+  const float a1 =
+      lerpf(lerpf(__ldg(p + sz), __ldg(p + sz + 1), wx), lerpf(__ldg(p + sz + sy), __ldg(p + sz + sy + 1), wx), wy);
+  return lerpf(a0, a1, wz);
+}
+
+// Field of any object: adds the correlation-scale factor and the tangent field
+// (non-stationary and anisotropic kernels) where the object has them.
+__device__ __forceinline__ Field fetch(const ObjectDev& o, V3 x) {
+  Field f = fetch_iso(o, x);
+  if (o.general) {
+    f.kb = o.kb;
+    f.kn = o.kn;
+    if (o.cscale || o.tangent) {
+      float wx, wy, wz;
+      const int b = cell_of(o, x, wx, wy, wz);
+      const int sy = o.n[0], sz = o.n[0] * o.n[1], plane = sz * o.n[2];
+      if (o.cscale) {
+        f.cs = trilerp(o.cscale, b, sy, sz, wx, wy, wz);
+        f.as = o.alpha_scale / f.cs;
+      }
+      if (o.tangent)
+        f.t = v3(trilerp(o.tangent, b, sy, sz, wx, wy, wz), trilerp(o.tangent + plane, b, sy, sz, wx, wy, wz),
+                 trilerp(o.tangent + 2 * plane, b, sy, sz, wx, wy, wz));
+    }
+  }
   return f;
 }
 
@@ -288,9 +339,18 @@ struct Local {
 __device__ __forceinline__ Local local_of(const ObjectDev& o, const Field& f) {
   Local l;
   l.sigma = sqrtf(f.var);
-  l.alpha = l.sigma * o.alpha_scale;
+  l.alpha = l.sigma * f.as;
   l.rho = inv_mills(f.mu / l.sigma) / l.sigma;
   return l;
+}
+
+// Orthonormal basis around a unit vector (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb_z(V3 n, V3& t1, V3& t2) {
+  const float s = copysignf(1.0f, n.z);
+  const float a = -1.0f / (s + n.z);
+  const float b = n.x * n.y * a;
+  t1 = {1.0f + s * n.x * n.x * a, s * b, -s * n.x};
+  t2 = {b, s + n.y * n.y * a, -n.y};
 }
 
 // sigma(d) = Lambda(d) cos(theta) = alpha psi(d . grad mu / alpha)
@@ -331,14 +391,83 @@ __device__ __forceinline__ float hf_ndf(int ndf, V3 m, V3 n, float alpha) {
   return expf(-(1.0f - c2) / (c2 * a2)) / (kPi * a2 * c2 * c2);
 }
 
+// ---------------------------------------------------------------- anisotropic kernels
+// Gradient covariance (alpha^2/2) diag(1, kb^2, kn^2) in the frame (t, b, n) with n =
+// grad mu/|grad mu| (world z where grad mu = 0), t the tangent field's component
+// orthogonal to n (any unit vector orthogonal to n where there is none), b = n x t.
+// alpha is the tangential roughness sqrt(2) sigma/l_t at x.
+struct KFrame {
+  V3 t, b, n;
+};
+
+__device__ __forceinline__ KFrame kernel_frame(const Field& f) {
+  KFrame k;
+  k.n = hf_normal(f.g);
+  const V3 tp = fma3(-dot(f.t, k.n), k.n, f.t);
+  const float l2 = dot(tp, tp);
+  if (l2 > 1e-12f * dot(f.t, f.t) && l2 > 0.0f) {
+    k.t = rsqrtf(l2) * tp;
+    k.b = cross(k.n, k.t);
+  } else {
+    onb_z(k.n, k.t, k.b);
+  }
+  return k;
+}
+
+// sigma(d) = E[max(0, -d.g)] = alpha_e psi(d.grad mu/alpha_e), alpha_e^2 = 2 d^T Sigma d =
+// alpha^2 ((d.t)^2 + kb^2 (d.b)^2 + kn^2 (d.n)^2)  (Eq. generalized_lambda times cos theta
+// in the local frame; (d.t)^2 + (d.b)^2 = |d x n|^2 without cancellation).
+__device__ __forceinline__ float area_aniso(V3 d, const Field& f, float alpha) {
+  const V3 n = hf_normal(f.g);
+  const float dn = dot(d, n);
+  const V3 dxn = cross(d, n);
+  float e2 = fmaf(f.kn * f.kn * dn, dn, dot(dxn, dxn));
+  if (f.kb != 1.0f) {
+    const KFrame k = kernel_frame(f);
+    const float db = dot(d, k.b);
+    e2 = fmaf((f.kb * f.kb - 1.0f) * db, db, e2);
+  }
+  const float ae = alpha * sqrtf(fmaxf(e2, 0.0f));
+  if (!(ae > 0.0f)) return fmaxf(0.0f, -dot(d, f.g));
+  return ae * psi(dot(d, f.g) / ae);
+}
+
+__device__ __forceinline__ float ndf_local(V3 m, float G, float ax, float ay, float az);
+
+// D(m) of the anisotropic GPSS: the local-frame NDF (Eq. macro_ndf) with alpha_x = alpha,
+// alpha_y = kb alpha, alpha_z = kn alpha, mean gradient (0, 0, |grad mu|).
+__device__ __forceinline__ float ndf_aniso(V3 m, const Field& f, float alpha) {
+  const float G = sqrtf(dot(f.g, f.g));
+  V3 ml;
+  if (f.kb != 1.0f) {
+    const KFrame k = kernel_frame(f);
+    ml = v3(dot(m, k.t), dot(m, k.b), dot(m, k.n));
+  } else {
+    const V3 n = hf_normal(f.g);
+    const V3 c = cross(m, n);
+    ml = v3(sqrtf(dot(c, c)), 0.0f, dot(m, n));
+  }
+  return ndf_local(ml, G, alpha, alpha * f.kb, alpha * f.kn);
+}
+
+__device__ __forceinline__ bool is_aniso(const Field& f) { return f.kb != 1.0f || f.kn != 1.0f; }
+
 __device__ __forceinline__ float projected_area(V3 d, const Field& f, float alpha) {
   if (f.ndf != kNdfGpss) return hf_projected_area(f.ndf, d, hf_normal(f.g), alpha);
+  if (is_aniso(f)) return area_aniso(d, f, alpha);
   return alpha * psi(dot(d, f.g) / alpha);
 }
 
 // sigma_t of one object at x for direction d (0 outside its box); fills f/l.
+// GEN = false: the object is known to be an isotropic stationary GPSS.
+template <bool GEN = true>
 __device__ __forceinline__ float sigma_t_object(const ObjectDev& o, V3 x, V3 d, Field& f, Local& l) {
-  f = fetch(o, x);
+  if constexpr (GEN) {
+    f = fetch(o, x);
+  } else {
+    f = fetch_iso(o, x);
+    f.ndf = kNdfGpss;
+  }
   l = local_of(o, f);
   return l.rho * projected_area(d, f, l.alpha);
 }
@@ -444,14 +573,7 @@ __device__ __forceinline__ float projected_area_local(V3 w, float G, float ax, f
 }
 
 // ---------------------------------------------------------------- sampling mixture
-// Orthonormal basis around a unit vector (Duff et al., JCGT 2017).
-__device__ __forceinline__ void onb(V3 n, V3& t1, V3& t2) {
-  const float s = copysignf(1.0f, n.z);
-  const float a = -1.0f / (s + n.z);
-  const float b = n.x * n.y * a;
-  t1 = {1.0f + s * n.x * n.x * a, s * b, -s * n.x};
-  t2 = {b, s + n.y * n.y * a, -n.y};
-}
+__device__ __forceinline__ void onb(V3 n, V3& t1, V3& t2) { onb_z(n, t1, t2); }
 
 // Beckmann proposal frame and roughness: z = sign(-d.n) n, alpha_B = clamp(alpha/|g|, 1e-3, 16);
 // z = -d where |g| < 1e-6.
@@ -571,9 +693,10 @@ __device__ __forceinline__ V3 ggx_sample_vis(V3 wi, V3 n, float a, float u1, flo
   return normalize(fma3(ne.x, b1, fma3(ne.y, b2, ne.z * n)));
 }
 
-// NDF of a field sample's object (GPSS or height field).
+// NDF of a field sample's object (GPSS, anisotropic GPSS or height field).
 __device__ __forceinline__ float ndf_field(V3 m, const Field& f, float alpha) {
   if (f.ndf != kNdfGpss) return hf_ndf(f.ndf, m, hf_normal(f.g), alpha);
+  if (is_aniso(f)) return ndf_aniso(m, f, alpha);
   return ndf_iso(m, f.g, alpha);
 }
 
@@ -773,6 +896,38 @@ __device__ __forceinline__ bool vndf_sample_exact(V3 d, V3 g, float alpha, float
   return true;
 }
 
+// Anisotropic kernels: g = grad mu + L xi with xi ~ N(0, I) and L = Sigma^(1/2) =
+// (alpha/sqrt2) (I + (kb - 1) b b^T + (kn - 1) n n^T).  With v = L d, s = |v| and e = -v/s,
+// -d.g = s (beta + xi.e), beta = -d.grad mu/s: the component xi.e = y - beta with y the
+// visible slope above, the two components of xi orthogonal to e plain normals.
+__device__ __forceinline__ V3 apply_sqrt_cov(V3 w, const KFrame& k, float kb, float kn, float s0) {
+  V3 r = fma3((kb - 1.0f) * dot(w, k.b), k.b, w);
+  r = fma3((kn - 1.0f) * dot(w, k.n), k.n, r);
+  return s0 * r;
+}
+
+__device__ __forceinline__ bool vndf_sample_aniso(V3 d, const Field& f, float alpha, float u0, float u1, float u2,
+                                                  V3& m) {
+  const KFrame k = kernel_frame(f);
+  const float s0 = alpha * kInvSqrt2;
+  const V3 v = apply_sqrt_cov(d, k, f.kb, f.kn, s0);
+  const float s = sqrtf(dot(v, v));
+  if (!(s > 0.0f)) return false;
+  const V3 e = (-1.0f / s) * v;
+  const float beta = -dot(d, f.g) / s;
+  const float y = sample_visible_slope(beta, u0);
+  V3 t1, t2;
+  onb(e, t1, t2);
+  const float n1 = kSqrt2 * erfinvf(fminf(fmaxf(2.0f * u1 - 1.0f, -0.99999994f), 0.99999994f));
+  const float n2 = kSqrt2 * erfinvf(fminf(fmaxf(2.0f * u2 - 1.0f, -0.99999994f), 0.99999994f));
+  const V3 xi = fma3(y - beta, e, fma3(n1, t1, n2 * t2));
+  const V3 g = f.g + apply_sqrt_cov(xi, k, f.kb, f.kn, s0);
+  const float len2 = dot(g, g);
+  if (!(len2 > 0.0f)) return false;
+  m = rsqrtf(len2) * g;
+  return true;
+}
+
 // Exact-vNDF counterpart of phase_sample_mix: weight p/pdf/F = 1, pdf = p/F.
 __device__ __forceinline__ bool phase_sample_vndf(float sd, V3 d, const Field& f, float alpha, float u0, float u1,
                                                   float u2, V3& d2, float& w_over_F, float& pdf) {
@@ -780,7 +935,8 @@ __device__ __forceinline__ bool phase_sample_vndf(float sd, V3 d, const Field& f
   V3 m;
   w_over_F = 0.0f;
   pdf = 0.0f;
-  if (!vndf_sample_exact(d, f.g, alpha, u0, u1, u2, m)) return false;
+  if (!(is_aniso(f) ? vndf_sample_aniso(d, f, alpha, u0, u1, u2, m) : vndf_sample_exact(d, f.g, alpha, u0, u1, u2, m)))
+    return false;
   const float dm = dot(d, m);
   if (!(dm < 0.0f)) return false;
   d2 = normalize(fma3(-2.0f * dm, m, d));
@@ -897,15 +1053,19 @@ __device__ __forceinline__ float power_heuristic(float a, float b) {
 //     edges of (-d_a * diff_a / h_a), and along the piece mu >= mu(x) - B (t'-t);
 //   - the variance lies between the corner minimum and maximum;
 //   - sigma(d) = E[max(0, -d.g)] <= max(0, -d.grad mu) + E[max(0, -d.(g - grad mu))]
-//     = max(0, -d.grad mu) + alpha/(2 sqrt(pi)) (Eq. generalized_lambda with the
-//     slope distribution of the gradient);
+//     = max(0, -d.grad mu) + alpha_e(d)/(2 sqrt(pi)) (Eq. generalized_lambda with the
+//     slope distribution of the gradient), alpha_e <= the largest roughness over the
+//     cell (anisotropic kernels: the largest axis; non-stationary: the smallest
+//     correlation scale at the corners);
 // with rho bounded as for the grid majorant (lambda decreasing).  The piece length
 // follows the distance to the shell: l = (mu(x) - 2 sigma_hi)/B, at least
 // sigma_lo/B, so a ray approaching a thin shell takes a few pieces with about one
 // tentative collision each instead of (cell size / sigma)^2 null collisions.  The
 // bound depends on x only (not on the piece's random numbers), so delta and ratio
 // tracking stay unbiased.  Returns (t_end, majorant), or t_end <= t when x is not
-// inside the object's box (the caller then keeps the cell majorant).
+// inside the object's box (the caller then keeps the cell majorant).  GEN = false: the
+// object is known to have the isotropic stationary kernel.
+template <bool GEN = true>
 static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, V3 d, float t, float t_max) {
   const V3 x = fma3(t, d, o);
   if (!inside(ob, x)) return make_float2(t, 0.0f);
@@ -951,14 +1111,27 @@ static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, 
     l_max = fminf(l_max, fmaxf(frac, 0.0f) / (fabsf(dd[a]) * ob.inv_h[a]));
   }
   const float s_lo = sqrtf(v_lo), s_hi = sqrtf(v_hi);
+  // largest roughness over the cell: alpha_max = sigma_hi sqrt2/(s_lo l_min), s_lo the
+  // smallest correlation-scale factor at the corners (the interpolant stays above it)
+  float a_hi = s_hi * ob.alpha_scale;
+  if constexpr (GEN) {
+    a_hi *= ob.amax;
+    if (ob.cscale) {
+      float c_lo = __ldg(ob.cscale + b);
+#pragma unroll
+      for (int k = 1; k < 8; ++k)
+        c_lo = fminf(c_lo, __ldg(ob.cscale + b + (k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz));
+      a_hi /= c_lo;
+    }
+  }
   float l = l_max;
   if (B > 0.0f) l = fminf(fmaxf((mu - 2.0f * s_hi) / B, s_lo / B), l_max);
   float mu_b = mu - B * l;
   mu_b -= 1e-6f * (fabsf(mu) + B * l) + 1e-7f * s_lo;  // rounding of mu and of the piece's end
   const float u = mu_b >= 0.0f ? mu_b / s_hi : mu_b / s_lo;
   const float rho_ub = inv_mills(u) / s_lo;
-  const float area_ub = ob.ndf == kNdfGpss ? B + s_hi * ob.alpha_scale * (0.5f * kInvSqrtPi)
-                      : 1.0f + s_hi * ob.alpha_scale * (ob.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
+  const float area_ub = ob.ndf == kNdfGpss ? B + a_hi * (0.5f * kInvSqrtPi)
+                      : 1.0f + a_hi * (ob.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
   const float sbar = rho_ub * area_ub * 1.001f;
   return make_float2(t + l, sbar);
 }
@@ -1017,8 +1190,8 @@ __device__ __forceinline__ float slab_exit(float lo, float hi, float o, float in
 }
 
 // LOCAL = false compiles the local-majorant branch out (scenes without thin
-// objects: no register cost for it in the render kernels).
-template <bool LOCAL = true>
+// objects: no register cost for it in the render kernels); GEN as for local_majorant.
+template <bool LOCAL = true, bool GEN = true>
 __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectDev& lob, V3 o, V3 d, Walk& w, float tau,
                                              uint32_t& steps) {
   // Each step moves the cell index strictly past the face the ray left by (or, in
@@ -1036,7 +1209,7 @@ __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectD
     const float seg_end = fminf(fminf(ex, ey), fminf(ez, w.t_end));
     float piece_end = seg_end, sbar = sk.x;
     if (LOCAL && g.hot > 0.0f && sk.x * (seg_end - w.t) > g.hot) {
-      const float2 pc = local_majorant(lob, o, d, w.t, seg_end);
+      const float2 pc = local_majorant<GEN>(lob, o, d, w.t, seg_end);
       if (pc.x > w.t && pc.y < sk.x) {
         piece_end = fminf(pc.x, seg_end);
         sbar = pc.y;

@@ -35,6 +35,12 @@ struct ObjectHost {
   size_t nodes = 0;
   float sigma_min = 0.0f;    // smallest standard deviation over the nodes
   int ndf = 0;               // gpss_ndf
+  float length_scale_b = 0.0f, length_scale_n = 0.0f;  // resolved (l_t where unset)
+  float* cscale = nullptr;   // device correlation-scale factors (nodes), or null
+  float* tangent = nullptr;  // device tangent field (3 planes of nodes), or null
+  bool anisotropic() const {
+    return length_scale_b != length_scale || length_scale_n != length_scale || tangent != nullptr;
+  }
 };
 
 constexpr int kSceneFlagWords = 1 + kMaxObjects;  // validation bits + per-object min variance

@@ -71,54 +71,61 @@ struct AdjOut {
   float2* d_mv;           // interleaved (d mean, d variance) accumulation buffer, or null
   float* d_alb;
   float* d_l;
+  float* d_cs;            // d correlation-scale factor per node, or null
 };
 
 enum Mode : int { kFlight = 0, kShadow = 1 };
 
-// Whether a scene has a height-field object (selects the HF kernel instances).
-inline bool scene_has_heightfield(const SceneDev& S) {
+// Whether a scene needs the general kernel instances: some object is a height-field
+// macrofacet or has an anisotropic or non-stationary kernel.
+inline bool scene_general(const SceneDev& S) {
   for (int k = 0; k < S.n_objs; ++k)
-    if (S.obj[k].ndf != kNdfGpss) return true;
+    if (S.obj[k].ndf != kNdfGpss || S.obj[k].general) return true;
   return false;
 }
 
-// HF = false: the scene has no height-field object (every object uses the GPSS NDF), so
-// a field sample's kind is the constant kNdfGpss and the kind dispatch folds away.
-template <bool HF>
+// GEN = false: every object is an isotropic stationary GPSS, so a field sample's kind and
+// kernel are constants and their dispatch folds away.
+template <bool GEN>
 __device__ __forceinline__ Field fetch_k(const ObjectDev& o, V3 x) {
-  Field f = fetch(o, x);
-  if constexpr (!HF) f.ndf = kNdfGpss;
-  return f;
+  if constexpr (GEN) {
+    return fetch(o, x);
+  } else {
+    Field f = fetch_iso(o, x);
+    f.ndf = kNdfGpss;
+    return f;
+  }
 }
 
+
 // Total extinction at x (single object fast path; several objects add).
-template <bool HF>
+template <bool GEN>
 __device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d) {
   if (S.n_objs == 1) {
     if (!inside(S.obj[0], x)) return 0.0f;
-    const Field f = fetch_k<HF>(S.obj[0], x);
+    const Field f = fetch_k<GEN>(S.obj[0], x);
     const Local l = local_of(S.obj[0], f);
     return l.rho * projected_area(d, f, l.alpha);
   }
   float tot = 0.0f;
   for (int k = 0; k < S.n_objs; ++k) {
     if (!inside(S.obj[k], x)) continue;
-    const Field f = fetch_k<HF>(S.obj[k], x);
+    const Field f = fetch_k<GEN>(S.obj[k], x);
     const Local l = local_of(S.obj[k], f);
     tot += l.rho * projected_area(d, f, l.alpha);
   }
   return tot;
 }
 
-// The scattering object, chosen in proportion to its extinction (reading Q13),
-// and its field at x.
-static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, float u, Field& f, Local& l) {
+// The scattering object, chosen in proportion to its extinction (reading Q13).
+template <bool GEN>
+static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, float u) {
   float tot = 0.0f;
   for (int k = 0; k < S.n_objs; ++k) {
     if (!inside(S.obj[k], x)) continue;
     Field fk;
     Local lk;
-    tot += sigma_t_object(S.obj[k], x, d, fk, lk);
+    tot += sigma_t_object<GEN>(S.obj[k], x, d, fk, lk);
   }
   float acc = 0.0f;
   int last = 0;
@@ -127,11 +134,9 @@ static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, 
     if (!inside(S.obj[k], x)) continue;
     Field fk;
     Local lk;
-    const float st = sigma_t_object(S.obj[k], x, d, fk, lk);
+    const float st = sigma_t_object<GEN>(S.obj[k], x, d, fk, lk);
     if (st <= 0.0f) continue;
     last = k;
-    f = fk;
-    l = lk;
     acc += st;
     if (pick < acc) break;
   }
@@ -139,20 +144,28 @@ static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, 
 }
 
 // Adjoint: scatter the derivative of the extinction (partials ds) at x with weight k.
-__device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, const DSig& ds, float k, float2* d_mv) {
+// The correlation-scale factor s enters through l(x) = s(x) l: d/ds(x) = (d/dl) l/s(x).
+// (GEN = false: the object has no correlation-scale grid.)
+template <bool GEN>
+__device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, const DSig& ds, float k, float cs,
+                                                   const AdjOut& A) {
   if (!isfinite(k) || k == 0.0f) return 0.0f;
-  if (d_mv) scatter_field(ob, x, k * ds.dmu, k * ds.dg, k * ds.dvar, d_mv);
+  if (A.d_mv) scatter_field(ob, x, k * ds.dmu, k * ds.dg, k * ds.dvar, A.d_mv);
+  if constexpr (GEN) {
+    if (A.d_cs) scatter_scalar(ob, x, k * ds.dl * (kSqrt2 / ob.alpha_scale) / cs, A.d_cs);
+  }
   return k * ds.dl;
 }
 
 // Adjoint: gradient of the vertex factors at x (incoming direction d_in): the NEE
 // factor F D(m_nee)/sigma(d_in) with weight Wnee and the sampled direction's factor
 // F D(m_ph)/sigma(d_in) with weight Wph (the sigma(d_in) part is shared).
+template <bool GEN>
 __device__ __forceinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, V3 wl, V3 d_next, float Wnee,
                                                 float Wph, V3 albedo_coef, const AdjOut A) {
-  const Field f = fetch(ob, x);
+  const Field f = fetch_k<GEN>(ob, x);
   const float sig = sqrtf(f.var);
-  const float alpha = sig * ob.alpha_scale;
+  const float alpha = sig * f.as;
   V3 cg = v3(0, 0, 0);
   float dalpha = 0.0f;
   if (Wnee != 0.0f) {
@@ -179,7 +192,12 @@ __device__ __forceinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, 
   if (A.d_mv && (Wnee != 0.0f || Wph != 0.0f)) scatter_field(ob, x, 0.0f, cg, cvar, A.d_mv);
   if (A.d_alb && (albedo_coef.x != 0.0f || albedo_coef.y != 0.0f || albedo_coef.z != 0.0f))
     scatter_albedo(ob, x, albedo_coef, A.d_alb);
-  return -dalpha * alpha * (ob.alpha_scale * kInvSqrt2);  // d/dl through alpha = sqrt2 sigma/l
+  // d/dl through alpha = sqrt2 sigma/(s(x) l); d/ds(x) = (d/dl) l/s(x)
+  const float dl = -dalpha * alpha * (ob.alpha_scale * kInvSqrt2);
+  if constexpr (GEN) {
+    if (A.d_cs && dl != 0.0f) scatter_scalar(ob, x, dl * (kSqrt2 / ob.alpha_scale) / f.cs, A.d_cs);
+  }
+  return dl;
 }
 
 // ---------------------------------------------------------------- per-lane path state
@@ -244,24 +262,15 @@ __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const Pa
 }
 
 // Shading of a real vertex: phase sampling, next-event estimation setup.
-template <bool ADJ, bool HF>
+template <bool ADJ, bool GEN>
 __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                            float* __restrict__ path_T, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
   s.waiting = false;
   const V3 x = fma3(s.w.t, s.d, s.o);
-  Field f;
-  float alpha;
-  int k = 0;
-  if (S.n_objs > 1) {
-    Local l;
-    k = choose_object(S, x, s.d, s.rng.next(), f, l);
-    alpha = l.alpha;
-  } else {
-    f = fetch_k<HF>(S.obj[0], x);
-    alpha = sqrtf(f.var) * S.obj[0].alpha_scale;  // the density rho is not needed for shading
-  }
-  if constexpr (!HF) f.ndf = kNdfGpss;  // also on the several-object path
+  const int k = S.n_objs > 1 ? choose_object<GEN>(S, x, s.d, s.rng.next()) : 0;
+  const Field f = fetch_k<GEN>(S.obj[k], x);
+  const float alpha = sqrtf(f.var) * f.as;  // the density rho is not needed for shading
   const V3 F = fetch_albedo(S.obj[k], x);
   s.o = x;
   s.cont = s.bounce + 1 < P.max_bounces;
@@ -313,7 +322,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
                      F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
                      F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
-    c.acc_l += adj_vertex(S.obj[0], x, s.d, wl, s.d_next, Wnee, Wph, ac, A);
+    c.acc_l += adj_vertex<GEN>(S.obj[0], x, s.d, wl, s.d_next, Wnee, Wph, ac, A);
     s.L = s.L + Ck;
   } else {
     if (path_T && !(scale > 0.0f)) path_T[(size_t)s.pidx * P.max_bounces + s.bounce] = 0.0f;
@@ -342,7 +351,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
 }
 
 // One tentative collision of the lane's current ray; returns true when the path ends.
-template <bool ADJ, bool LOCAL, bool HF>
+template <bool ADJ, bool LOCAL, bool GEN>
 __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                           float* __restrict__ path_T, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
@@ -351,25 +360,27 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
     s.begin = false;
   }
   bool hit = false;
-  if (s.walk_ok) hit = walk_advance<LOCAL>(S.mg, S.obj[0], s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
+  if (s.walk_ok) hit = walk_advance<LOCAL, GEN>(S.mg, S.obj[0], s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
   bool finish = false;
   if (hit) {
     ++s.events;
     const V3 x = fma3(s.w.t, s.d, s.o);
     float st;
     DSig ds;
+    float cs = 1.0f;
     bool inobj = false;
     if constexpr (ADJ) {
       // extinction and its partials from one evaluation (the decision uses the same value)
       inobj = inside(S.obj[0], x);
       st = 0.0f;
       if (inobj) {
-        const Field f = fetch(S.obj[0], x);
+        const Field f = fetch_k<GEN>(S.obj[0], x);
         ds = dsigma_t(S.obj[0], f, s.d);
         st = ds.st;
+        cs = f.cs;
       }
     } else {
-      st = sigma_t_at<HF>(S, x, s.d);
+      st = sigma_t_at<GEN>(S, x, s.d);
     }
     float k_adj = 0.0f;  // adjoint: weight of this collision's extinction derivative
     if (s.mode == kFlight) {
@@ -393,7 +404,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
       if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;  // T = 0: the shadow ray ends here
     }
     if constexpr (ADJ) {
-      if (inobj && k_adj != 0.0f) c.acc_l += adj_scatter_event(S.obj[0], x, ds, k_adj, A.d_mv);
+      if (inobj && k_adj != 0.0f) c.acc_l += adj_scatter_event<GEN>(S.obj[0], x, ds, k_adj, cs, A);
     }
     if (s.events >= kMaxEventsPerPath) {
       ++c.abort;
@@ -511,9 +522,10 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
 }
 
 // ---------------------------------------------------------------- single-render kernel
-// LOCAL: the scene uses local majorants (MajorantDev::hot > 0).  HF: the scene has a
-// height-field object (the adjoint supports the GPSS NDF only: HF = false there).
-template <bool ADJ, bool LOCAL, bool HF>
+// LOCAL: the scene uses local majorants (MajorantDev::hot > 0).  GEN: some object is a
+// height-field macrofacet or has an anisotropic or non-stationary kernel (the adjoint
+// supports the isotropic GPSS, stationary or with a correlation-scale grid).
+template <bool ADJ, bool LOCAL, bool GEN>
 __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
     k_path(const __grid_constant__ SceneDev S, const __grid_constant__ CameraDev C, const __grid_constant__ PathArgs P,
            float* __restrict__ image, float* __restrict__ sqsum, float* __restrict__ path_radiance,
@@ -537,10 +549,10 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
     }
     const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
     if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act)) {
-      if (s.waiting) lane_shade<ADJ, HF>(s, S, P, A, path_T, c);
+      if (s.waiting) lane_shade<ADJ, GEN>(s, S, P, A, path_T, c);
     }
     if (!s.active || s.waiting) continue;
-    if (lane_step<ADJ, LOCAL, HF>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
+    if (lane_step<ADJ, LOCAL, GEN>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
   }
   flush_counters(c, counters, ADJ ? A.d_l : nullptr);
 }

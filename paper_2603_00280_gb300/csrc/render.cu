@@ -28,12 +28,12 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   P.shade_min = shade_min;
   P.exact_vndf = (o.flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
   AdjOut A{};
-  const bool local = S.mg.hot > 0.0f, hf = scene_has_heightfield(S);
-  if (local && hf)
+  const bool local = S.mg.hot > 0.0f, gen = scene_general(S);
+  if (local && gen)
     k_path<false, true, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
   else if (local)
     k_path<false, true, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
-  else if (hf)
+  else if (gen)
     k_path<false, false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
   else
     k_path<false, false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);

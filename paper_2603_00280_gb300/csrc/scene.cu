@@ -36,12 +36,22 @@ __global__ void k_check_albedo(const float* __restrict__ a, size_t n, int* flags
   }
 }
 
+// Correlation-scale factors must be finite and > 0 (bit 8), tangent components finite (bit 16).
+__global__ void k_check_kernel_grid(const float* __restrict__ a, size_t n, int positive, int* flags) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = a[i];
+    if (positive ? !(v > 0.0f && isfinite(v)) : !isfinite(v)) atomicOr(flags, positive ? 8 : 16);
+  }
+}
+
 // Upper bound of sigma_t over a majorant cell, over all directions (row A3):
 //   mu >= mu_lo, var in [v_lo, v_hi], |grad mu| <= G_hi (each gradient component of
 //   the trilinear interpolant is a convex combination of edge differences / h);
 //   lambda is decreasing, so rho <= lambda(mu_lo/sigma_hi)/sigma_lo for mu_lo >= 0 and
 //   lambda(mu_lo/sigma_lo)/sigma_lo otherwise;  sigma(d) = E[max(0,-d.g)] <= G_hi +
-//   alpha_hi/(2 sqrt(pi)) (height-field NDFs: 1 + alpha_hi/(2 sqrt(pi)) or 1 + alpha_hi/2).
+//   alpha_hi/(2 sqrt(pi)) (height-field NDFs: 1 + alpha_hi/(2 sqrt(pi)) or 1 + alpha_hi/2),
+//   alpha_hi = sqrt2 sigma_hi max(1/l_t, 1/l_b, 1/l_n)/s_lo with s_lo the smallest
+//   correlation-scale factor of the cell's nodes (interpolated s stays above it).
 //   Objects' bounds add.  A 1e-3 relative margin covers FP32
 //   rounding of the per-sample evaluation.
 __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
@@ -71,7 +81,8 @@ __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
         hi[a] = i1 + 1;  // node range
       }
       if (!overlap) continue;
-      float mu_lo = INFINITY, v_lo = INFINITY, v_hi = 0.0f, ex = 0.0f, ey = 0.0f, ez = 0.0f;
+      float mu_lo = INFINITY, v_lo = INFINITY, v_hi = 0.0f, ex = 0.0f, ey = 0.0f, ez = 0.0f, c_lo = 1.0f;
+      if (o.cscale) c_lo = INFINITY;
       const int sy = o.n[0], sz = o.n[0] * o.n[1];
       for (int kk = lo[2]; kk <= hi[2]; ++kk)
         for (int jj = lo[1]; jj <= hi[1]; ++jj)
@@ -84,6 +95,7 @@ __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
             if (ii < hi[0]) ex = fmaxf(ex, fabsf(o.mv[idx + 1].x - v.x));
             if (jj < hi[1]) ey = fmaxf(ey, fabsf(o.mv[idx + sy].x - v.x));
             if (kk < hi[2]) ez = fmaxf(ez, fabsf(o.mv[idx + sz].x - v.x));
+            if (o.cscale) c_lo = fminf(c_lo, o.cscale[idx]);
           }
       const float gx = ex * o.inv_h[0], gy = ey * o.inv_h[1], gz = ez * o.inv_h[2];
       const float G_hi = sqrtf(gx * gx + gy * gy + gz * gz);
@@ -92,8 +104,9 @@ __global__ void k_majorant(SceneDev S, MajorantDev g, float* __restrict__ maj) {
       const float rho_ub = inv_mills(u) / s_lo;
       // height-field macrofacets: sigma(d) <= max(0, -d.n) + alpha/(2 sqrt pi) (Beckmann),
       // <= max(0, -d.n) + alpha/2 (GGX), with |n| = 1
-      const float area_ub = o.ndf == kNdfGpss ? G_hi + s_hi * o.alpha_scale * (0.5f * kInvSqrtPi)
-                          : 1.0f + s_hi * o.alpha_scale * (o.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
+      const float a_hi = s_hi * o.alpha_scale * o.amax / c_lo;
+      const float area_ub = o.ndf == kNdfGpss ? G_hi + a_hi * (0.5f * kInvSqrtPi)
+                          : 1.0f + a_hi * (o.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
       total += rho_ub * area_ub;
     }
     maj[c] = total * 1.001f;
@@ -154,6 +167,16 @@ gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cuda
     e = cudaMemcpyAsync(o.albedo, objs[k].albedo, nodes * o.channels * sizeof(float), cudaMemcpyDefault, st);
     if (e != cudaSuccess) return cuda_fail(e, "copy albedo");
     k_check_albedo<<<blocks_for(nodes * o.channels, 256), 256, 0, st>>>(o.albedo, nodes * o.channels, s->flags);
+    if (o.cscale) {
+      e = cudaMemcpyAsync(o.cscale, objs[k].correlation_scale, nodes * sizeof(float), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy correlation scale");
+      k_check_kernel_grid<<<blocks_for(nodes, 256), 256, 0, st>>>(o.cscale, nodes, 1, s->flags);
+    }
+    if (o.tangent) {
+      e = cudaMemcpyAsync(o.tangent, objs[k].tangent, 3 * nodes * sizeof(float), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy tangent field");
+      k_check_kernel_grid<<<blocks_for(3 * nodes, 256), 256, 0, st>>>(o.tangent, 3 * nodes, 0, s->flags);
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "upload kernels");
@@ -166,6 +189,8 @@ gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cuda
   if (flags & 1) { set_error("mean contains non-finite values"); return GPSS_ERR_INVALID_ARG; }
   if (flags & 2) { set_error("variance must be finite and > 0"); return GPSS_ERR_INVALID_ARG; }
   if (flags & 4) { set_error("albedo must lie in [0,1]"); return GPSS_ERR_INVALID_ARG; }
+  if (flags & 8) { set_error("correlation_scale must be finite and > 0"); return GPSS_ERR_INVALID_ARG; }
+  if (flags & 16) { set_error("tangent must be finite"); return GPSS_ERR_INVALID_ARG; }
   // thin: some object's smallest standard deviation lies below its grid spacing,
   // where the grid majorant of the cells at its shell is loose
   s->thin = false;
@@ -225,6 +250,12 @@ SceneDev scene_dev(const gpss_scene_s* s) {
     o.alpha_scale = kSqrt2 / h.length_scale;
     o.mv = h.mv;
     o.albedo = h.albedo;
+    o.kb = h.length_scale / h.length_scale_b;
+    o.kn = h.length_scale / h.length_scale_n;
+    o.amax = fmaxf(1.0f, fmaxf(o.kb, o.kn));
+    o.cscale = h.cscale;
+    o.tangent = h.tangent;
+    o.general = (o.kb != 1.0f || o.kn != 1.0f || o.cscale || o.tangent) ? 1 : 0;
   }
   d.mg = s->mg;
   d.mg.maj = s->maj;

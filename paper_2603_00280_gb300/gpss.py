@@ -34,7 +34,9 @@ class ObjectDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("bbox_min", ctypes.c_float * 3), ("bbox_max", ctypes.c_float * 3),
                 ("mean", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
-                ("albedo_channels", ctypes.c_int), ("length_scale", ctypes.c_float), ("ndf", ctypes.c_int)]
+                ("albedo_channels", ctypes.c_int), ("length_scale", ctypes.c_float), ("ndf", ctypes.c_int),
+                ("length_scale_b", ctypes.c_float), ("length_scale_n", ctypes.c_float),
+                ("tangent", ctypes.c_void_p), ("correlation_scale", ctypes.c_void_p)]
 
 
 NDF_KINDS = {"gpss": 0, "beckmann": 1, "ggx": 2}
@@ -80,7 +82,7 @@ _SIGS = {
     "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
     "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
     "gpss_render_noalloc": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, ctypes.POINTER(Stats), _VP],
-    "gpss_render_adjoint": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, _VP, _VP, _VP,
+    "gpss_render_adjoint": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, _VP, _VP, _VP, _VP,
                             ctypes.POINTER(Stats), _VP],
     "gpss_batch_create": [ctypes.POINTER(_VP), ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _I, _I, _VP,
                           ctypes.POINTER(_VP)],
@@ -199,17 +201,21 @@ def render_opts(opts: dict, flags: int = 0) -> RenderOpts:
     return o
 
 
+def _f32(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float32)
+    return a.contiguous().float()
+
+
 def _object_descs(objects, keep):
+    """Descriptors of object dicts: mean, var (or variance), albedo ((nz,ny,nx) or
+    (channels,nz,ny,nx)), bbox_min, bbox_max, length_scale, optional ndf ("gpss",
+    "beckmann", "ggx"), length_scale_b, length_scale_n, tangent (3,nz,ny,nx) and
+    correlation_scale (nz,ny,nx); arrays are numpy (host) or CUDA tensors."""
     descs = (ObjectDesc * len(objects))()
     for k, o in enumerate(objects):
         mean, var, alb = o["mean"], o["variance"] if "variance" in o else o["var"], o["albedo"]
-        arrs = []
-        for a in (mean, var, alb):
-            if isinstance(a, np.ndarray):
-                a = np.ascontiguousarray(a, dtype=np.float32)
-            else:
-                a = a.contiguous().float()
-            arrs.append(a)
+        arrs = [_f32(a) for a in (mean, var, alb)]
         keep.extend(arrs)
         mean, var, alb = arrs
         nz, ny, nx = mean.shape
@@ -224,6 +230,13 @@ def _object_descs(objects, keep):
         D.albedo_channels = 1 if alb.ndim == 3 else int(alb.shape[0])
         D.length_scale = float(o["length_scale"])
         D.ndf = NDF_KINDS[o.get("ndf", "gpss")]
+        D.length_scale_b = float(o.get("length_scale_b", 0.0))
+        D.length_scale_n = float(o.get("length_scale_n", 0.0))
+        for key in ("tangent", "correlation_scale"):
+            if o.get(key) is not None:
+                a = _f32(o[key])
+                keep.append(a)
+                setattr(D, key, _ptr(a).value)
     return descs
 
 
@@ -302,13 +315,13 @@ def render(scene: Scene, camera: dict, opts: dict, image=None, sqsum=None, want_
 
 
 def render_adjoint(scene: Scene, camera: dict, opts: dict, d_image, d_mean=None, d_variance=None, d_albedo=None,
-                   d_length_scale=None, stats=True, stream=None):
+                   d_length_scale=None, d_correlation_scale=None, stats=True, stream=None):
     st = Stats() if stats else None
     c = camera_desc(camera)
     o = render_opts(opts)
     _call("gpss_render_adjoint", scene.handle, ctypes.byref(c), ctypes.byref(o), _ptr(d_image), _ptr(d_mean),
-          _ptr(d_variance), _ptr(d_albedo), _ptr(d_length_scale), ctypes.byref(st) if st is not None else None,
-          _stream(stream))
+          _ptr(d_variance), _ptr(d_albedo), _ptr(d_length_scale), _ptr(d_correlation_scale),
+          ctypes.byref(st) if st is not None else None, _stream(stream))
     return st.as_dict() if st is not None else None
 
 
@@ -491,7 +504,8 @@ class _RenderFn:
     """torch.autograd.Function wrapper (defined lazily so that importing this
     module needs no CUDA).  Forward: upload the parameter tensors into the scene
     (single object) and render.  Backward: gpss_render_adjoint with the incoming
-    image gradient; returns gradients for mean, variance, albedo, length scale."""
+    image gradient; returns gradients for mean, variance, albedo, length scale
+    and (when given) the correlation-scale grid."""
     fn = None
 
     @classmethod
@@ -501,10 +515,13 @@ class _RenderFn:
 
             class RenderFunction(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, mean, var, albedo, length_scale, scene, obj, camera, opts):
+                def forward(ctx, mean, var, albedo, length_scale, cscale, scene, obj, camera, opts):
                     o = dict(obj)
                     o["mean"], o["var"], o["albedo"] = mean.detach(), var.detach(), albedo.detach()
                     o["length_scale"] = float(length_scale)
+                    if cscale is not None:
+                        o["correlation_scale"] = cscale.detach()
+                    ctx.has_cs = cscale is not None
                     scene.update([o])
                     image, _, _ = render(scene, camera, opts, stats=False, keep_path_radiance=True)
                     ctx.scene, ctx.camera, ctx.opts = scene, camera, opts
@@ -518,15 +535,18 @@ class _RenderFn:
                     dv = torch.zeros(ctx.shapes[1], device="cuda", dtype=torch.float32)
                     da = torch.zeros(ctx.shapes[2], device="cuda", dtype=torch.float32)
                     dl = torch.zeros(1, device="cuda", dtype=torch.float32)
-                    render_adjoint(ctx.scene, ctx.camera, ctx.opts, g, dm, dv, da, dl, stats=False)
-                    return dm, dv, da, dl[0], None, None, None, None
+                    dc = torch.zeros(ctx.shapes[0], device="cuda", dtype=torch.float32) if ctx.has_cs else None
+                    render_adjoint(ctx.scene, ctx.camera, ctx.opts, g, dm, dv, da, dl, dc, stats=False)
+                    return dm, dv, da, dl[0], dc, None, None, None, None
 
             cls.fn = RenderFunction
         return cls.fn
 
 
-def render_differentiable(scene: Scene, obj: dict, mean, var, albedo, length_scale, camera: dict, opts: dict):
+def render_differentiable(scene: Scene, obj: dict, mean, var, albedo, length_scale, camera: dict, opts: dict,
+                          correlation_scale=None):
     """Differentiable render of a single-object scene.  mean/var/albedo are CUDA
-    tensors shaped like the scene's grids; length_scale a 0-d CUDA tensor.  obj
-    supplies the box (bbox_min, bbox_max).  Returns the (H, W, 3) image."""
-    return _RenderFn.get().apply(mean, var, albedo, length_scale, scene, obj, camera, opts)
+    tensors shaped like the scene's grids; length_scale a 0-d CUDA tensor;
+    correlation_scale (optional) a CUDA tensor shaped like mean.  obj supplies the
+    box (bbox_min, bbox_max).  Returns the (H, W, 3) image."""
+    return _RenderFn.get().apply(mean, var, albedo, length_scale, correlation_scale, scene, obj, camera, opts)

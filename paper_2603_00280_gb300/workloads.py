@@ -241,6 +241,50 @@ def differentiable(n=64, width=256, height=256, spp=64, max_bounces=32, seed=123
             "opts": {"spp": spp, "max_bounces": max_bounces, "seed": seed, "mix_R": 0.5}}
 
 
+def tangent_swirl(p, twist=0.25):
+    """Tangent field (3, nz, ny, nx) swirling about z: t = (-y, x, twist) at the node
+    coordinates p (nz, ny, nx, 3)."""
+    return np.ascontiguousarray(np.stack([-p[..., 1], p[..., 0], np.full(p.shape[:-1], twist)]), dtype=np.float32)
+
+
+def correlation_ramp(p, lo=0.5, hi=1.5, axis=2):
+    """Correlation-scale factors rising linearly from lo to hi along `axis` over
+    [-0.5, 0.5] (the correlation grows from bottom to top, as in the paper's
+    non-stationary sweeps)."""
+    return np.ascontiguousarray(lo + (hi - lo) * (p[..., axis] + 0.5), dtype=np.float32)
+
+
+def with_kernel(obj, l_b_ratio=2.0, l_n_ratio=0.5, tangent=True, correlation=True):
+    """Returns a copy of an object on a node grid with an anisotropic (l_b = l_b_ratio
+    l_t along the swirl's bitangent, l_n = l_n_ratio l_t) and non-stationary
+    (correlation ramp) kernel."""
+    o = dict(obj)
+    nz, ny, nx = obj["mean"].shape
+    p = node_coords(obj["bbox_min"], obj["bbox_max"], (nx, ny, nz))
+    l = obj["length_scale"]
+    if tangent:
+        o["tangent"] = tangent_swirl(p)
+        o["length_scale_b"] = l * l_b_ratio
+    if l_n_ratio != 1.0:
+        o["length_scale_n"] = l * l_n_ratio
+    if correlation:
+        o["correlation_scale"] = correlation_ramp(p)
+    return o
+
+
+def nonstationary(n=64, width=256, height=256, spp=64, max_bounces=32, seed=0, length_scale=0.02,
+                  l_b_ratio=2.0, l_n_ratio=0.5):
+    """The heterogeneous sphere-noise GPSS (variance ramp 1e-4..1e-2 along x) with an
+    anisotropic, non-stationary kernel: l_t = length_scale, l_b = l_b_ratio l_t along
+    the bitangent of a tangent field swirling about z, l_n = l_n_ratio l_t, every l
+    scaled by a factor rising from 0.5 at the bottom to 1.5 at the top."""
+    wl = heterogeneous(n=n, width=width, height=height, spp=spp, max_bounces=max_bounces, seed=seed,
+                       length_scale=length_scale)
+    wl["scene"]["objects"] = [with_kernel(wl["scene"]["objects"][0], l_b_ratio, l_n_ratio)]
+    wl["name"] = "nonstationary_%d" % n
+    return wl
+
+
 def batched_scene(s: int, size_scale: float = 1.0):
     """Scene s (0..63) of the batched workload: image side 64..512, grid 32..256
     nodes per axis, spp 4..64, a sphere / plane / box mean with 0.02 noise and a

@@ -51,15 +51,20 @@ def rel_err(a, b, floor=0.0):
 FILM_REL = 2e-5
 
 
-def image_z(gpu_mean, gpu_sqsum, gpu_spp, orc_sum, orc_sumsq, orc_spp):
-    """Per-pixel z of the difference between two Monte Carlo images."""
+def image_z(gpu_mean, gpu_sqsum, gpu_spp, orc_sum, orc_sumsq, orc_spp, orc_sample_var=None):
+    """Per-pixel z of the difference between two Monte Carlo images.  orc_sample_var:
+    the per-sample variance of the oracle's estimator measured by a larger run of the
+    same estimator (the GPU with the oracle's sampler); it raises the oracle's own
+    small-sample estimate where that missed the heavy tail."""
     gm = np.asarray(gpu_mean, np.float64)
     gv = np.maximum(np.asarray(gpu_sqsum, np.float64) / gpu_spp - gm ** 2, 0.0) / gpu_spp
     gv = np.maximum(gv, (FILM_REL * np.abs(gm)) ** 2)
     om = orc_sum / orc_spp
     ovar = np.maximum(orc_sumsq / orc_spp - om ** 2, 0.0)
-    # Under the null hypothesis both sides sample the same per-pixel distribution;
-    # the path weights are heavy tailed, so the smaller sample's variance estimate is
+    if orc_sample_var is not None:
+        ovar = np.maximum(ovar, orc_sample_var)
+    # Where both sides sample the same per-pixel distribution (the same sampler), the
+    # path weights are heavy tailed, so the smaller sample's variance estimate is
     # raised to the pooled estimate (dominated by the larger, GPU sample).
     pooled = (gv * gpu_spp * gpu_spp + ovar * orc_spp) / (gpu_spp + orc_spp)
     ov = np.maximum(ovar, pooled) / orc_spp
@@ -105,3 +110,9 @@ def two_spheres_rgb():
         alb = rng.uniform(0.3, 0.95, size=(3, n[2], n[1], n[0])).astype(np.float32)
         objs.append(W.make_object(W.sdf_sphere(p, c, r), v, alb, lo, hi, 0.05))
     return {"objects": objs, "light": W.sky_light()}
+
+
+def sample_var(mean, sqsum, spp):
+    """Per-sample variance of a GPU image from its sum of squares."""
+    m = np.asarray(mean, np.float64)
+    return np.maximum(np.asarray(sqsum, np.float64) / spp - m * m, 0.0)

@@ -113,10 +113,11 @@ def test_vndf_images_match_oracle_and_reduce_variance():
     spp = 2048
     a, asq, sa = _render(G, cam, dict(wl["opts"], spp=spp, seed=41, sampler="vndf"))
     s, s2, _ = oracle.render(O, cam, dict(wl["opts"], spp=48, seed=42))
-    z, gm, om, gse, ose = C.image_z(a, asq, spp, s, s2, 48)
+    # the oracle samples the mixture: its per-sample variance from the GPU mixture run
+    b, bsq, sb = _render(G, cam, dict(wl["opts"], spp=spp, seed=43))
+    z, gm, om, gse, ose = C.image_z(a, asq, spp, s, s2, 48, orc_sample_var=C.sample_var(b, bsq, spp))
     ok, info = C.check_image_parity(gm, gse, om, ose)
     assert ok, info
-    b, bsq, sb = _render(G, cam, dict(wl["opts"], spp=spp, seed=43))
     va = np.maximum(asq / spp - a * a, 0)
     vb = np.maximum(bsq / spp - b * b, 0)
     lit = b > 1e-3
