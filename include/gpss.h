@@ -179,6 +179,19 @@ gpss_status gpss_scene_set_schedule(gpss_scene s, int shade_min);
  * grid spacing) at a few tentative collisions per crossing.  hot >= 0, 0
  * disables; default 4.  Every choice is unbiased. */
 gpss_status gpss_scene_set_local_majorant(gpss_scene s, float hot);
+/* Surface-limit analytic free flight in the local pieces (enable = 1; the default 0
+ * keeps constant pieces, which are as tight and cheaper once the local projected-area
+ * bound sigma(d) <= a psi(-B/a) applies).  Where the mean rises along the ray (rays
+ * leaving a shell; B < 0 bounds its decrease rate), a piece's majorant follows the
+ * linear lower bound mu(t) >= mu0 - B (t - t0) to the cell's exit:
+ * sbar(t) = K lambda(u)/sigma_lo, u = (mu0 - B (t - t0))/sigma_u, with sigma_u =
+ * sigma_lo while u < 0 and sigma_hi after (lambda the inverse Mills ratio, K the
+ * projected-area bound).  Its optical depth, K sigma_u/(sigma_lo B) times a difference
+ * of ln Phi (Smith's height form of Sec. 4.1), is inverted in closed form, so the
+ * tentative collisions follow the density's decay instead of the start point's
+ * density held over the cell (gpss_eval_local_piece returns these pieces).  Unbiased
+ * either way. */
+gpss_status gpss_scene_set_surface_flight(gpss_scene s, int enable);
 /* Frees the scene.  Call after the stream's work on it has completed. */
 gpss_status gpss_scene_destroy(gpss_scene s);
 /* Majorant grid geometry: dims[3] cells and their values (device copy, may be NULL). */
@@ -282,6 +295,15 @@ gpss_status gpss_batch_destroy(gpss_batch b);
  * entries (org3, dir3: n*3; dir unit length). */
 gpss_status gpss_eval_local_majorant(gpss_scene s, int n, const float* org3, const float* dir3, const float* t0,
                                      const float* t_max, float* t_end, float* sbar, gpss_stream stream);
+/* The local piece the traversal takes at org + t0 dir with surface-limit flight on
+ * (see gpss_scene_set_surface_flight; no cap from the grid majorant): t_end[i], lin[i]
+ * (1: linear-exponential majorant, 0: constant), depth[i] = the majorant's optical
+ * depth over [t0, t_end], and for the optical depth tau[i] < depth[i] the tentative
+ * collision t_hit[i] and the majorant there sbar_hit[i] (t_hit = t_end, sbar_hit = the
+ * majorant at t_end otherwise).  All arrays device, n entries (org3, dir3: n*3). */
+gpss_status gpss_eval_local_piece(gpss_scene s, int n, const float* org3, const float* dir3, const float* t0,
+                                  const float* t_max, const float* tau, float* t_end, int* lin, float* depth,
+                                  float* t_hit, float* sbar_hit, gpss_stream stream);
 /* Exact visible-normal sample of object k's phase function at x (see
  * GPSS_FLAG_EXACT_VNDF): uniforms u3 (n*3) -> d_out3 (n*3), w3_out = F per channel
  * (n*3; zero where no sample), pdf_out = p/F over d_out (n). */

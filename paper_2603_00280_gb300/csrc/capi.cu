@@ -342,6 +342,13 @@ extern "C" gpss_status gpss_scene_set_schedule(gpss_scene s, int shade_min) {
   return GPSS_OK;
 }
 
+extern "C" gpss_status gpss_scene_set_surface_flight(gpss_scene s, int enable) {
+  if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
+  if (enable != 0 && enable != 1) { set_error("enable must be 0 or 1"); return GPSS_ERR_INVALID_ARG; }
+  s->lin_flight = enable != 0;
+  return GPSS_OK;
+}
+
 extern "C" gpss_status gpss_scene_set_local_majorant(gpss_scene s, float hot) {
   if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
   if (!(hot >= 0.0f) || !std::isfinite(hot)) { set_error("hot must be finite and >= 0"); return GPSS_ERR_INVALID_ARG; }

@@ -26,6 +26,39 @@ __global__ void k_eval_local_majorant(const SceneDev S, int n, const float* org,
   sbar[i] = pc.y;
 }
 
+__global__ void k_eval_local_piece(const SceneDev S, int n, const float* org, const float* dir, const float* t0,
+                                   const float* tmax, const float* tau, float* t_end, int* lin, float* depth,
+                                   float* t_hit, float* sbar_hit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const LocalPiece p = local_piece(S.obj[0], ld3(org, i), ld3(dir, i), t0[i], tmax[i], true, INFINITY);
+  t_end[i] = p.t_end;
+  lin[i] = p.lin;
+  if (!(p.t_end > t0[i])) {
+    depth[i] = 0.0f;
+    t_hit[i] = p.t_end;
+    sbar_hit[i] = 0.0f;
+    return;
+  }
+  const float D = p.lin ? lin_depth(p, t0[i], p.t_end) : p.sbar * (p.t_end - t0[i]);
+  depth[i] = D;
+  float sb = p.sbar;
+  float th = p.t_end;
+  if (tau[i] < D) {
+    if (p.lin) {
+      const float2 h = lin_collision(p, t0[i], p.t_end, tau[i]);
+      th = h.x;
+      sb = h.y;
+    } else {
+      th = t0[i] + tau[i] / p.sbar;
+    }
+  } else if (p.lin) {
+    sb = lin_collision(p, t0[i], p.t_end, D).y;  // the majorant at the piece's end
+  }
+  t_hit[i] = th;
+  sbar_hit[i] = sb;
+}
+
 __global__ void k_eval_phase(const SceneDev S, int k, int n, const float* pos, const float* din, const float* dout,
                              float R, float* p3, float* pdf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,6 +323,21 @@ extern "C" gpss_status gpss_eval_sigma_t(gpss_scene s, int n, const float* pos3,
   k_eval_sigma_t<<<nb(n), 128, 0, (cudaStream_t)stream>>>(scene_dev(s), n, pos3, dir3, out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GPSS_OK : cuda_fail(e, "eval_sigma_t");
+}
+
+extern "C" gpss_status gpss_eval_local_piece(gpss_scene s, int n, const float* org3, const float* dir3,
+                                             const float* t0, const float* t_max, const float* tau, float* t_end,
+                                             int* lin, float* depth, float* t_hit, float* sbar_hit,
+                                             gpss_stream stream) {
+  if (!s || !org3 || !dir3 || !t0 || !t_max || !tau || !t_end || !lin || !depth || !t_hit || !sbar_hit) {
+    set_error("null argument");
+    return GPSS_ERR_INVALID_ARG;
+  }
+  CHECK_N(n);
+  k_eval_local_piece<<<nb(n), 128, 0, (cudaStream_t)stream>>>(scene_dev(s), n, org3, dir3, t0, t_max, tau, t_end,
+                                                             lin, depth, t_hit, sbar_hit);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GPSS_OK : cuda_fail(e, "eval_local_piece");
 }
 
 extern "C" gpss_status gpss_eval_local_majorant(gpss_scene s, int n, const float* org3, const float* dir3,

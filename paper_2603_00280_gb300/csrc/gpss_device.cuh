@@ -76,8 +76,11 @@ struct MajorantDev {
   // Local majorants (single-object scenes; 0 = off): where the cell's majorant
   // times the rest of the ray's segment in the cell exceeds `hot` (expected
   // tentative collisions), the walk bounds sigma_t over shorter pieces from the
-  // field at the piece's start (local_majorant).
+  // field at the piece's start (local_piece).
   float hot;
+  // Surface-limit analytic flight in those pieces (1 = on, opt-in): the majorant follows
+  // a linear lower bound of mu along the ray and is sampled in closed form (lin_depth).
+  int lin;
 };
 
 enum LightKind : int { kLightDirectional = 0, kLightSky = 1, kLightUniform = 2 };
@@ -1045,30 +1048,79 @@ __device__ __forceinline__ float power_heuristic(float a, float b) {
 }
 
 // ---------------------------------------------------------------- local majorant
-// Upper bound of sigma_t along the ray piece [t, t_end] that starts at x = o + t d,
-// from the 8 corners of the field cell of `ob` containing x (the piece ends at
-// that cell's exit at the latest).  In the cell the mean is trilinear, so:
+// ln Phi(u) of the standard normal, without underflow or cancellation: log1p of the
+// upper tail for u >= 0, ln(erfcx(-u/sqrt2)/2) - u^2/2 below.
+__device__ __forceinline__ float log_ndtr(float u) {
+  if (u >= 0.0f) return log1pf(-0.5f * erfcf(u * kInvSqrt2));
+  return logf(0.5f * erfcxf(-u * kInvSqrt2)) - 0.5f * u * u;
+}
+
+// The u with ln Phi(u) = L (L <= 0): Phi^-1 through erfcinv where Phi is representable
+// (the upper tail 1 - Phi = -expm1(L) above the median), else the asymptote
+// u^2 = -2L - ln(-2L) - ln(2 pi) below e^-80 refined by two Newton steps on ln Phi,
+// whose derivative is the inverse Mills ratio lambda(u).
+__device__ __forceinline__ float inv_log_ndtr(float L) {
+  if (L > -0.69314718f) return kSqrt2 * erfcinvf(fmaxf(-2.0f * expm1f(L), 1e-37f));
+  if (L > -80.0f) return -kSqrt2 * erfcinvf(2.0f * expf(L));
+  const float a = -2.0f * L;
+  float u = -sqrtf(a - logf(a) - 1.8378771f);  // ln(2 pi)
+#pragma unroll
+  for (int it = 0; it < 2; ++it) u -= (log_ndtr(u) - L) / inv_mills(u);
+  return u;
+}
+
+// A piece of a ray inside one field cell and its majorant: a constant sbar on
+// [t0, t_end), or (lin) the linear-exponential majorant of the surface limit,
+//   sbar(t) = K lambda(u(t))/s_lo,  u(t) = (mu0 - B (t - t0))/sigma_u,
+// with mu0 - B (t - t0) a linear lower bound of the mean along the ray and sigma_u =
+// s_hi where that bound is >= 0, s_lo where it is < 0 (lambda decreasing, so either
+// choice bounds lambda(mu/sigma) for sigma in [s_lo, s_hi] on its side of 0).  Its
+// optical depth is closed form, because d ln Phi(u)/du = lambda(u):
+//   int sbar dt = K sigma_u/(s_lo B) [ln Phi(u(t_a)) - ln Phi(u(t_b))]
+// (the Smith-height form of the transmittance of a linear mean, Sec. 4.1), for either
+// sign of B, and a tentative collision at depth tau inverts it with inv_log_ndtr.
+struct LocalPiece {
+  float t0, t_end, sbar;       // sbar: the constant majorant, or lin's value at t0
+  float mu0, B, s_hi, s_lo, K;
+  int lin;
+};
+
+// Upper bound of sigma_t along the ray piece that starts at x = o + t d, from the 8
+// corners of the field cell of `ob` containing x (the piece ends at that cell's exit at
+// the latest).  In the cell the mean is trilinear, so:
 //   - each gradient component d_a * dmu/dx_a is a bilinear blend of the cell's
 //     4 edge differences along a, hence -d.grad mu <= B = sum_a max over those
 //     edges of (-d_a * diff_a / h_a), and along the piece mu >= mu(x) - B (t'-t);
 //   - the variance lies between the corner minimum and maximum;
-//   - sigma(d) = E[max(0, -d.g)] <= max(0, -d.grad mu) + E[max(0, -d.(g - grad mu))]
-//     = max(0, -d.grad mu) + alpha_e(d)/(2 sqrt(pi)) (Eq. generalized_lambda with the
-//     slope distribution of the gradient), alpha_e <= the largest roughness over the
-//     cell (anisotropic kernels: the largest axis; non-stationary: the smallest
-//     correlation scale at the corners);
-// with rho bounded as for the grid majorant (lambda decreasing).  The piece length
-// follows the distance to the shell: l = (mu(x) - 2 sigma_hi)/B, at least
-// sigma_lo/B, so a ray approaching a thin shell takes a few pieces with about one
-// tentative collision each instead of (cell size / sigma)^2 null collisions.  The
-// bound depends on x only (not on the piece's random numbers), so delta and ratio
-// tracking stay unbiased.  Returns (t_end, majorant), or t_end <= t when x is not
-// inside the object's box (the caller then keeps the cell majorant).  GEN = false: the
-// object is known to have the isotropic stationary kernel.
+//   - sigma(d) = alpha_e psi(d.grad mu/alpha_e) (Eq. generalized_lambda times cos) grows
+//     with alpha_e (its derivative is e^{-a^2}/(2 sqrt pi)) and falls with d.grad mu, so
+//     with d.grad mu >= -B (B signed here) and alpha_e <= a_hi, the largest roughness
+//     over the cell (anisotropic kernels: the largest axis; non-stationary: the
+//     smallest correlation scale at the corners), sigma(d) <= a_hi psi(-B/a_hi): about
+//     B for rays approaching the shell, exponentially small for rays leaving it;
+// with rho bounded as for the grid majorant (lambda decreasing).
+// Rays approaching the shell (B > 0) take constant pieces whose length follows the
+// distance to the shell, l = (mu(x) - 2 sigma_hi)/B, at least sigma_lo/B: a few pieces
+// with about one tentative collision each instead of (cell size / sigma)^2 null
+// collisions.  Rays leaving it (the signed bound B < 0: mu rises at least at rate -B,
+// so the density falls along the piece) take one linear-exponential piece to the cell's
+// exit (allow_lin, when mu rises by more than sigma_lo over it and the majorant at its
+// start is below `cap`, the cell's grid majorant); a constant piece would hold the
+// density of the start over the whole cell.
+// The bound depends on x only (not on the piece's random numbers), so delta and ratio
+// tracking stay unbiased.  Returns t_end <= t when x is not inside the object's box
+// (the caller then keeps the cell majorant).  GEN = false: the object is known to have
+// the isotropic stationary kernel.
 template <bool GEN = true>
-static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, V3 d, float t, float t_max) {
+__device__ __forceinline__ LocalPiece local_piece(const ObjectDev& ob, V3 o, V3 d, float t, float t_max,
+                                                  bool allow_lin, float cap) {
+  LocalPiece p;
+  p.t0 = t;
+  p.t_end = t;
+  p.sbar = 0.0f;
+  p.lin = 0;
   const V3 x = fma3(t, d, o);
-  if (!inside(ob, x)) return make_float2(t, 0.0f);
+  if (!inside(ob, x)) return p;
   const float xx[3] = {x.x, x.y, x.z}, dd[3] = {d.x, d.y, d.z};
   float f[3];
   int ii[3];
@@ -1101,7 +1153,8 @@ static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, 
     if (!(k & 2)) ey = fmaxf(ey, -d.y * (c[k + 2].x - c[k].x));
     if (!(k & 4)) ez = fmaxf(ez, -d.z * (c[k + 4].x - c[k].x));
   }
-  const float B = fmaxf(0.0f, ex * ob.inv_h[0] + ey * ob.inv_h[1] + ez * ob.inv_h[2]);
+  const float Bs = ex * ob.inv_h[0] + ey * ob.inv_h[1] + ez * ob.inv_h[2];  // signed
+  const float B = fmaxf(0.0f, Bs);
   // exit of the field cell
   float l_max = t_max - t;
 #pragma unroll
@@ -1124,16 +1177,111 @@ static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, 
       a_hi /= c_lo;
     }
   }
+  // sigma(d) = alpha_e psi(d.grad mu/alpha_e) grows with alpha_e and falls with
+  // d.grad mu >= -Bs, so sigma(d) <= a_hi psi(-Bs/a_hi) (<= max(0, Bs) + a_hi/(2 sqrt pi);
+  // exponentially small for rays leaving the surface)
+  const float area_ub = ob.ndf == kNdfGpss ? a_hi * psi(-Bs / a_hi)
+                      : 1.0f + a_hi * (ob.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
+  const float K = area_ub * 1.001f;
+  if (allow_lin && -Bs * l_max > s_lo) {
+    // rounding of mu and of the positions along the piece
+    const float mu0 = mu - (1e-6f * (fabsf(mu) - Bs * l_max) + 1e-7f * s_lo);
+    const float s0 = K * inv_mills(mu0 / (mu0 >= 0.0f ? s_hi : s_lo)) / s_lo;
+    if (s0 < cap) {
+      p.t_end = t + l_max;
+      p.sbar = s0;
+      p.mu0 = mu0;
+      p.B = Bs;
+      p.s_hi = s_hi;
+      p.s_lo = s_lo;
+      p.K = K;
+      p.lin = 1;
+      return p;
+    }
+  }
   float l = l_max;
   if (B > 0.0f) l = fminf(fmaxf((mu - 2.0f * s_hi) / B, s_lo / B), l_max);
   float mu_b = mu - B * l;
   mu_b -= 1e-6f * (fabsf(mu) + B * l) + 1e-7f * s_lo;  // rounding of mu and of the piece's end
   const float u = mu_b >= 0.0f ? mu_b / s_hi : mu_b / s_lo;
-  const float rho_ub = inv_mills(u) / s_lo;
-  const float area_ub = ob.ndf == kNdfGpss ? B + a_hi * (0.5f * kInvSqrtPi)
-                      : 1.0f + a_hi * (ob.ndf == kNdfGgx ? 0.5f : 0.5f * kInvSqrtPi);
-  const float sbar = rho_ub * area_ub * 1.001f;
-  return make_float2(t + l, sbar);
+  p.t_end = t + l;
+  p.sbar = inv_mills(u) / s_lo * K;
+  return p;
+}
+
+// Constant-majorant form (t_end, sbar) of local_piece (parity evaluators).
+template <bool GEN = true>
+static __device__ __noinline__ float2 local_majorant(const ObjectDev& ob, V3 o, V3 d, float t, float t_max) {
+  const LocalPiece p = local_piece<GEN>(ob, o, d, t, t_max, false, INFINITY);
+  return make_float2(p.t_end, p.sbar);
+}
+
+// Linear-exponential piece: the depth of one side of the crossing tz of the linear
+// bound (sigma_u fixed) over [ta, tb].
+__device__ __forceinline__ float lin_side_depth(const LocalPiece& p, float su, float ta, float tb) {
+  const float ua = (p.mu0 - p.B * (ta - p.t0)) / su, ub = (p.mu0 - p.B * (tb - p.t0)) / su;
+  return p.K * su / (p.s_lo * p.B) * (log_ndtr(ua) - log_ndtr(ub));
+}
+
+// sigma_u before and after the crossing tz = t0 + mu0/B along the ray: the bound falls
+// through 0 for B > 0 (s_hi, then s_lo) and rises through it for B < 0.
+__device__ __forceinline__ float lin_s_first(const LocalPiece& p) { return p.B > 0.0f ? p.s_hi : p.s_lo; }
+__device__ __forceinline__ float lin_s_second(const LocalPiece& p) { return p.B > 0.0f ? p.s_lo : p.s_hi; }
+
+// Linear-exponential piece: optical depth of the majorant over [ta, tb] (within the piece).
+__device__ __forceinline__ float lin_depth(const LocalPiece& p, float ta, float tb) {
+  const float tz = p.t0 + p.mu0 / p.B;
+  float tau = 0.0f;
+  if (ta < tz) tau += lin_side_depth(p, lin_s_first(p), ta, fminf(tb, tz));
+  if (tb > tz) tau += lin_side_depth(p, lin_s_second(p), fmaxf(ta, tz), tb);
+  return fmaxf(tau, 0.0f);
+}
+
+// Linear-exponential piece: the tentative collision at optical depth tau beyond ta
+// (tau below the depth to t_max), clamped to [ta, t_max], and the majorant there.
+__device__ __forceinline__ float2 lin_collision(const LocalPiece& p, float ta, float t_max, float tau) {
+  const float tz = p.t0 + p.mu0 / p.B;
+  float su = lin_s_second(p);
+  float La;
+  bool first = false;
+  if (ta < tz) {
+    const float s1 = lin_s_first(p);
+    La = log_ndtr((p.mu0 - p.B * (ta - p.t0)) / s1);
+    const float d1 = p.K * s1 / (p.s_lo * p.B) * (La + 0.69314718f);  // to the crossing: ln Phi(0) = -ln 2
+    if (tau < d1) {
+      su = s1;
+      first = true;
+    } else {
+      tau -= d1;
+      ta = tz;
+    }
+  }
+  if (!first) La = log_ndtr((p.mu0 - p.B * (ta - p.t0)) / su);
+  const float u = inv_log_ndtr(La - tau * p.s_lo * p.B / (p.K * su));
+  const float t = fminf(fmaxf(p.t0 + (p.mu0 - su * u) / p.B, ta), t_max);
+  return make_float2(t, p.K * inv_mills(u) / p.s_lo);
+}
+
+// One local piece of the traversal from t (segment end seg_end, cell majorant cap)
+// consuming the optical depth tau, kept out of line so the piece's state never lives in
+// the traversal loop: returns (t_hit, sbar, 0, 1) for a tentative collision,
+// (piece end, sbar, tau left, 2) when the piece is crossed, and w = 0 when no local
+// piece beats the cell majorant.
+template <bool GEN = true>
+static __device__ __noinline__ float4 local_step(const ObjectDev& ob, V3 o, V3 d, float t, float seg_end, float cap,
+                                                 int lin, float tau) {
+  const LocalPiece p = local_piece<GEN>(ob, o, d, t, seg_end, lin != 0, cap);
+  if (!(p.t_end > t && p.sbar < cap)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float pe = fminf(p.t_end, seg_end);
+  const float need = p.lin ? lin_depth(p, t, pe) : p.sbar * (pe - t);
+  if (tau < need) {
+    if (p.lin) {
+      const float2 h = lin_collision(p, t, pe, tau);
+      return make_float4(h.x, h.y, 0.0f, 1.0f);
+    }
+    return make_float4(t + tau / p.sbar, p.sbar, 0.0f, 1.0f);
+  }
+  return make_float4(pe, p.sbar, tau - fmaxf(need, 0.0f), 2.0f);
 }
 
 // ---------------------------------------------------------------- majorant traversal
@@ -1207,24 +1355,33 @@ __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectD
     const float ey = slab_exit(g.gmin[1] + (float)ly * g.cell[1], g.gmin[1] + (float)(hy + 1) * g.cell[1], o.y, w.idy, d.y);
     const float ez = slab_exit(g.gmin[2] + (float)lz * g.cell[2], g.gmin[2] + (float)(hz + 1) * g.cell[2], o.z, w.idz, d.z);
     const float seg_end = fminf(fminf(ex, ey), fminf(ez, w.t_end));
-    float piece_end = seg_end, sbar = sk.x;
+    bool local = false;
     if (LOCAL && g.hot > 0.0f && sk.x * (seg_end - w.t) > g.hot) {
-      const float2 pc = local_majorant<GEN>(lob, o, d, w.t, seg_end);
-      if (pc.x > w.t && pc.y < sk.x) {
-        piece_end = fminf(pc.x, seg_end);
-        sbar = pc.y;
+      const float4 r = local_step<GEN>(lob, o, d, w.t, seg_end, sk.x, g.lin, tau);
+      if (r.w > 0.5f) {
+        ++steps;
+        if (r.w < 1.5f) {
+          w.t = r.x;
+          w.sbar = r.y;
+          return true;
+        }
+        tau = r.z;
+        w.t = fmaxf(w.t, r.x);
+        if (r.x < seg_end) continue;  // next piece in the same cell
+        local = true;
       }
     }
-    const float need = sbar * (piece_end - w.t);
-    ++steps;
-    if (tau < need) {
-      w.t += tau / sbar;
-      w.sbar = sbar;
-      return true;
+    if (!local) {
+      const float need = sk.x * (seg_end - w.t);
+      ++steps;
+      if (tau < need) {
+        w.t += tau / sk.x;
+        w.sbar = sk.x;
+        return true;
+      }
+      tau -= fmaxf(need, 0.0f);
+      w.t = fmaxf(w.t, seg_end);
     }
-    tau -= fmaxf(need, 0.0f);
-    w.t = fmaxf(w.t, piece_end);
-    if (piece_end < seg_end) continue;  // next piece in the same cell
     if (seg_end >= w.t_end) return false;
     // step to the cell beyond the exit face; after a cube jump the other axes are
     // re-derived from the exit point (rounding there only yields empty segments)

@@ -60,6 +60,7 @@ struct gpss_scene_s {
   float kappa = 0.5f;              // expected majorant depth allowed per skip
   int shade_min = 24;              // lanes a warp gathers before shading real vertices
   float hot = 4.0f;                // local-majorant threshold (0 = off; single-object scenes)
+  bool lin_flight = false;         // surface-limit analytic flight in local pieces (opt-in)
   bool thin = false;               // some object's sigma_min < its grid spacing (local majorants pay)
   int brick = 1;                   // majorant cell = brick x finest field cell
   // scratch owned by the scene

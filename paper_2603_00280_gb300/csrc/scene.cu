@@ -261,6 +261,7 @@ SceneDev scene_dev(const gpss_scene_s* s) {
   d.mg.maj = s->maj;
   d.mg.skip = s->skip;
   d.mg.hot = (s->n_objs == 1 && s->thin) ? s->hot : 0.0f;
+  d.mg.lin = s->lin_flight ? 1 : 0;
   d.light = s->light;
   return d;
 }

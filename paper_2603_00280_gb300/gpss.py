@@ -79,6 +79,7 @@ _SIGS = {
     "gpss_scene_set_traversal": [_VP, _I, _F, _VP],
     "gpss_scene_set_schedule": [_VP, _I],
     "gpss_scene_set_local_majorant": [_VP, _F],
+    "gpss_scene_set_surface_flight": [_VP, _I],
     "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
     "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
     "gpss_render_noalloc": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, ctypes.POINTER(Stats), _VP],
@@ -91,6 +92,7 @@ _SIGS = {
     "gpss_batch_destroy": [_VP],
     "gpss_eval_sigma_t": [_VP, _I, _VP, _VP, _VP, _VP],
     "gpss_eval_local_majorant": [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "gpss_eval_local_piece": [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "gpss_eval_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP],
     "gpss_sample_phase": [_VP, _I, _I, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP],
     "gpss_sample_phase_vndf": [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
@@ -267,6 +269,9 @@ class Scene:
     def set_local_majorant(self, hot: float = 4.0):
         _call("gpss_scene_set_local_majorant", self.handle, float(hot))
 
+    def set_surface_flight(self, enable: bool = True):
+        _call("gpss_scene_set_surface_flight", self.handle, 1 if enable else 0)
+
     def set_traversal(self, skip_levels: int = 5, kappa: float = 0.5, stream=None):
         _call("gpss_scene_set_traversal", self.handle, int(skip_levels), float(kappa), _stream(stream))
 
@@ -407,6 +412,19 @@ def eval_local_majorant(scene: Scene, org, dirs, t0, tmax, stream=None):
     _call("gpss_eval_local_majorant", scene.handle, len(org), _ptr(org), _ptr(dirs), _ptr(t0), _ptr(tmax),
           _ptr(t_end), _ptr(sbar), _stream(stream))
     return t_end, sbar
+
+
+def eval_local_piece(scene: Scene, org, dirs, t0, tmax, tau, stream=None):
+    """Returns (t_end, lin, depth, t_hit, sbar_hit) of the traversal's local pieces."""
+    torch = _torch()
+    org, dirs, t0, tmax, tau = _dev(org), _dev(dirs), _dev(t0), _dev(tmax), _dev(tau)
+    n = len(org)
+    outs = [torch.empty(n, device="cuda") for _ in range(5)]
+    outs[1] = torch.empty(n, device="cuda", dtype=torch.int32)
+    t_end, lin, depth, t_hit, sbar_hit = outs
+    _call("gpss_eval_local_piece", scene.handle, n, _ptr(org), _ptr(dirs), _ptr(t0), _ptr(tmax), _ptr(tau),
+          _ptr(t_end), _ptr(lin), _ptr(depth), _ptr(t_hit), _ptr(sbar_hit), _stream(stream))
+    return t_end, lin, depth, t_hit, sbar_hit
 
 
 def eval_phase(scene: Scene, k: int, pos, d_in, d_out, mix_R=0.5, stream=None):
