@@ -22,7 +22,11 @@
 // and chunk (paths per cursor fetch).  Coordinate descent from (128, 24, 256),
 // one axis after the other: each candidate is timed (CUDA events) on a copy of
 // the batch whose spp is reduced so that one launch traces about kTunePaths
-// paths, within a total budget of kTuneBudgetMs.
+// paths, within a total budget of kTuneBudgetMs.  A candidate replaces the
+// incumbent only when it is kTuneMargin faster: the reduced copy floors every
+// scene at 1 spp, which over-weights low-spp scenes, so small differences there
+// do not carry over to the full batch (on the 64-scene uneven batch a 2% win of
+// (shade 8, chunk 64) on the copy was a 15% loss on the batch).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -40,7 +44,8 @@ struct JobDev {
 };
 
 constexpr int kBatchMaxJobs = 4096;
-constexpr long long kTunePaths = 1ll << 22;     // paths per tuning launch (at most, roughly)
+constexpr long long kTunePaths = 1ll << 24;     // paths per tuning launch (at most, roughly)
+constexpr float kTuneMargin = 0.97f;             // a candidate must take < 97% of the incumbent's time
 constexpr float kTuneBudgetMs = 5000.0f;         // tuning stops once its launches took this long
 constexpr int kBatchDefaultShade = 24;
 constexpr int kBatchDefaultChunk = 256;
@@ -299,7 +304,7 @@ static gpss_status autotune(gpss_batch b, cudaStream_t st) {
         if (t < 0.0f) { status = cuda_fail(e, "tuning launch"); goto done; }
         warmed[slot(c.block)] = true;
         spent += warm ? 2.0f * t : t;
-        if (t < best_ms) {
+        if (t < kTuneMargin * best_ms) {
           best_ms = t;
           best = c;
         }
