@@ -50,6 +50,31 @@ def test_scene_create_rejects_bad_descriptors(bad):
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("extra", [
+    dict(length_scale_b=0.2),                    # l_b != l_t needs a tangent field
+    dict(length_scale_n=-0.1),                   # l_n must be 0 or > 0
+    dict(length_scale_b=float("nan")),
+    dict(ndf="ggx", length_scale_n=0.2),         # height fields take an isotropic kernel
+    dict(ndf="beckmann", tangent=np.zeros((3, 3, 3, 3), np.float32)),
+])
+def test_scene_create_rejects_bad_kernels(extra):
+    o = dict(_obj(), **extra)
+    with pytest.raises(gpss.GpssError) as e:
+        gpss.Scene({"objects": [o], "light": {"type": "sky"}}, stream=0)
+    assert e.value.status == 1
+    assert b"object 0" in gpss.load().gpss_last_error()
+
+
+def test_object_descriptor_layout_matches_the_header():
+    """The binding's ctypes mirror of gpss_object_desc has the header's fields in order."""
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {\n  int nx, ny, nz;"):]
+    body = body[:body.index("} gpss_object_desc;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b(\w+)(?:\[\d\])?\s*[,;]", body)
+    assert [f for f, _ in gpss.ObjectDesc._fields_] == names
+
+
 def test_scene_create_rejects_bad_counts_and_boxes():
     L = gpss.load()
     h = ctypes.c_void_p()
@@ -76,6 +101,11 @@ def test_calls_reject_null_and_invalid_arguments():
     assert L.gpss_eval_ndf(0, buf, 1.0, 1.0, 1.0, 1.0, buf, None) == 0      # empty input is a no-op
     assert L.gpss_philox4x32_10(1, None, None, None, None) == 1
     assert L.gpss_scene_destroy(None) == 1
+    assert L.gpss_scene_set_surface_flight(None, 1) == 1
+    assert L.gpss_scene_set_local_majorant(None, 4.0) == 1
+    assert L.gpss_eval_local_piece(None, 1, buf, buf, buf, buf, buf, buf, buf, buf, buf, buf, None) == 1
+    assert L.gpss_render_adjoint(None, ctypes.byref(cam), ctypes.byref(opts), buf, None, None, None, None, None,
+                                 None, None) == 1
     assert L.gpss_last_error() != b""
 
 
