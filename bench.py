@@ -145,12 +145,18 @@ def peak_fp32_tops(torch):
     return sms * 128 * mhz * 1e6 / 1e12, sms, mhz, src
 
 
+# The files the measured render kernel (k_path<0, 0, 0>) is built from: its translation
+# unit render.cu with every header it includes, and the build script's flags.
+KERNEL_SOURCES = ("paper_2603_00280_gb300/csrc/render.cu", "paper_2603_00280_gb300/csrc/path_kernel.cuh",
+                  "paper_2603_00280_gb300/csrc/adjoint_math.cuh", "paper_2603_00280_gb300/csrc/gpss_internal.h",
+                  "paper_2603_00280_gb300/csrc/gpss_device.cuh", "paper_2603_00280_gb300/csrc/moment_fit.inc",
+                  "include/gpss.h", "paper_2603_00280_gb300/build.py")
+
+
 def kernel_source_hash():
     h = hashlib.sha1()
-    csrc = os.path.join(ROOT, "paper_2603_00280_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for rel in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()[:12]
 
 
