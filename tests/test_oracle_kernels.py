@@ -228,3 +228,21 @@ def test_infinite_normal_correlation_is_the_beckmann_height_field():
         assert pg[0, 0] == pytest.approx(ph[0, 0], rel=1e-5)
         checked += 1
     assert checked >= 4
+
+
+def test_ndf_first_moment_is_the_mean_gradient(aniso):
+    """int m D(m) dm over the sphere = int g P(g) dg = grad mu (Eq. gdf_to_ndf with
+    dg = t^2 dt dm): the world-frame NDF's first moment, independent of the projected
+    area.  D(m) is read from the phase function with d = -m (so d2 = m):
+    D(m) = 4 sigma(-m) p(-m, m)/F."""
+    obj, S = aniso
+    for x, f in _points(S, 14, 2, shell=0.05):
+        g = f["grad"]
+        n = g / np.linalg.norm(g)
+        ms, wts = H.sphere_points(n, 384, 256)
+        xs = np.repeat(x[None], len(ms), 0)
+        p, _ = oracle.phase_eval(S, 0, xs, -ms, ms)
+        sd = oracle.sigma_t(S, xs, -ms) / _rho(f)
+        D = 4.0 * sd * p[:, 0] / f["albedo"][0]
+        first = np.sum(wts[:, None] * ms * D[:, None], axis=0)
+        np.testing.assert_allclose(first, g, rtol=0, atol=2e-3 * np.linalg.norm(g))
