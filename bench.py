@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -153,10 +154,19 @@ KERNEL_SOURCES = ("paper_2603_00280_gb300/csrc/render.cu", "paper_2603_00280_gb3
                   "include/gpss.h", "paper_2603_00280_gb300/build.py")
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank lines (string literals in these
+    files hold no comment markers): comment edits leave the compiled kernel unchanged."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash():
     h = hashlib.sha1()
     for rel in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, rel), "rb").read())
+        text = open(os.path.join(ROOT, rel), encoding="utf-8").read()
+        h.update((text if rel.endswith(".py") else strip_comments(text)).encode())
     return h.hexdigest()[:12]
 
 

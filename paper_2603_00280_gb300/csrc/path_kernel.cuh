@@ -9,7 +9,7 @@
 //     optical depth -ln(u) of the majorant, real with probability sigma_t/majorant);
 //   - at each real vertex next-event estimation with a ratio-tracking shadow ray
 //     (T *= 1 - sigma_t/majorant per tentative collision, Russian roulette below
-//     T = 0.1), MIS (power heuristic) against phase sampling for environment lights;
+//     T = kRatioRR = 0.5), MIS (power heuristic) against phase sampling for environment lights;
 //   - phase sampling with the mixture of Sec. 4.2; at most max_bounces real
 //     vertices, no continuation after the last, no Russian roulette on paths.
 //
