@@ -11,10 +11,14 @@
 //     form through moments M_k(q) = int_0^inf s^k exp(-s^2 + 2 q s) ds;
 //   - the conductor phase function (Eq. phase, Eq. microfacet_vndf) and the
 //     sampling mixture R * Beckmann-vNDF + (1-R) * uniform hemisphere (end of
-//     Sec. 4.2);
+//     Sec. 4.2), and exact visible-normal sampling in slope space;
+//   - height-field macrofacets with Beckmann or GGX NDFs (Sec. 4.1) and anisotropic,
+//     non-stationary kernels (the local-frame roughness of Sec. 4.2 with a tangent
+//     field and a correlation-scale grid);
 //   - Philox4x32-10 (Salmon et al., SC'11) keyed by (seed) with counter
 //     (pixel, sample, bounce | purpose << 16, draw);
-//   - Amanatides-Woo traversal of the majorant grid.
+//   - Amanatides-Woo traversal of the majorant grid with skip cubes, local majorants
+//     for thin shells and the surface-limit analytic pieces.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -1,7 +1,11 @@
-// path_kernel.cuh -- the persistent path kernel, in two instances:
+// path_kernel.cuh -- the persistent path kernel k_path<ADJ, LOCAL, GEN>:
 //   ADJ = false  forward render (film accumulation);
 //   ADJ = true   path-replay adjoint: the same paths, traced from the same random
-//                numbers by the same code, with gradient scattering added.
+//                numbers by the same code, with gradient scattering added;
+//   LOCAL        local majorants compiled in (scenes with thin objects);
+//   GEN          height-field objects and anisotropic / non-stationary kernels
+//                compiled in (otherwise every object is an isotropic stationary GPSS
+//                and the kind and kernel dispatch folds away).
 //
 // Integrator (Sec. 5 of the paper: null scattering on the classic exponential
 // medium of Sec. 4):
@@ -10,8 +14,9 @@
 //   - at each real vertex next-event estimation with a ratio-tracking shadow ray
 //     (T *= 1 - sigma_t/majorant per tentative collision, Russian roulette below
 //     T = kRatioRR = 0.5), MIS (power heuristic) against phase sampling for environment lights;
-//   - phase sampling with the mixture of Sec. 4.2; at most max_bounces real
-//     vertices, no continuation after the last, no Russian roulette on paths.
+//   - phase sampling with the mixture of Sec. 4.2 (or exactly from the visible
+//     normals); at most max_bounces real vertices, no continuation after the last,
+//     no Russian roulette on paths.
 //
 // Execution model: one persistent thread per resident lane.  Each iteration of the
 // main loop advances every active lane by ONE tentative collision of its current
