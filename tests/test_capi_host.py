@@ -135,3 +135,22 @@ def test_batch_calls_reject_bad_arguments_on_the_host():
     assert L.gpss_batch_render(None, None, None, None, None) == 1
     assert L.gpss_batch_config(None, None, None, None, None) == 1
     assert L.gpss_batch_destroy(None) == 0
+
+
+def test_object_descriptors_marshal_kernel_fields():
+    """gpss._object_descs fills the kernel fields: 0 / NULL by default (the isotropic
+    stationary kernel), the given scalars and host pointers otherwise."""
+    keep = []
+    plain = gpss._object_descs([_obj()], keep)[0]
+    assert plain.length_scale_b == 0.0 and plain.length_scale_n == 0.0
+    assert not plain.tangent and not plain.correlation_scale
+    o = dict(_obj(), length_scale_b=0.2, length_scale_n=0.05, ndf="ggx",
+             tangent=np.ones((3, 3, 3, 3), np.float64), correlation_scale=np.full((3, 3, 3), 2.0))
+    keep = []
+    d = gpss._object_descs([o], keep)[0]
+    assert d.length_scale_b == pytest.approx(0.2) and d.length_scale_n == pytest.approx(0.05)
+    assert d.ndf == gpss.NDF_KINDS["ggx"]
+    arrays = {a.ctypes.data: a for a in keep if isinstance(a, np.ndarray)}
+    t, c = arrays[d.tangent], arrays[d.correlation_scale]
+    assert t.dtype == np.float32 and t.shape == (3, 3, 3, 3) and t.flags.c_contiguous
+    assert c.dtype == np.float32 and np.all(c == 2.0)
