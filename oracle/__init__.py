@@ -4,7 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library (the CUDA path in
 ``paper_2603_00280_gb300``) never imports, links or calls it, and the two share
 no source.  The arithmetic lives in the C files next to this module
-(``gpss_oracle_medium.c``, ``gpss_oracle_transport.c``); this module only
+(``gpss_oracle_medium.c``, ``gpss_oracle_transport.c``, and the dual numbers of the
+adjoint in ``gpss_oracle_dual.c``); this module only
 compiles them with gcc and marshals arguments through ctypes.
 
 Scenes, cameras, lights and options are the plain dictionaries produced by
@@ -23,7 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["gpss_oracle_medium.c", "gpss_oracle_transport.c"]
+_SOURCES = ["gpss_oracle_medium.c", "gpss_oracle_transport.c", "gpss_oracle_dual.c"]
 _HEADERS = ["gpss_oracle.h", "gpss_oracle_internal.h"]
 _lock = threading.Lock()
 _lib = None
@@ -89,6 +90,13 @@ _D = ctypes.c_double
 _PD = ctypes.POINTER(ctypes.c_double)
 
 
+class _GradOut(ctypes.Structure):
+    _fields_ = [
+        ("nodes", ctypes.POINTER(ctypes.c_int64)), ("n_nodes", ctypes.c_int64),
+        ("d_mean", _PD), ("d_var", _PD), ("d_albedo", _PD), ("d_cscale", _PD), ("d_l", _PD),
+    ]
+
+
 def lib():
     global _lib
     with _lock:
@@ -130,6 +138,13 @@ def lib():
             L.orc_render_diff.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Scene), ctypes.POINTER(_Camera),
                                           ctypes.POINTER(_Opts), _PD, _PD, ctypes.POINTER(_Stats)]
             L.orc_camera_ray.argtypes = [ctypes.POINTER(_Camera), ctypes.c_int, ctypes.c_int, _D, _D, _PD, _PD]
+            L.orc_render_grad.restype = ctypes.c_int
+            L.orc_render_grad.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.POINTER(_Opts), _PD,
+                                          ctypes.POINTER(_GradOut), ctypes.POINTER(_Stats),
+                                          ctypes.POINTER(ctypes.c_uint64)]
+            L.orc_dual_eval.restype = ctypes.c_int
+            L.orc_dual_eval.argtypes = [ctypes.POINTER(_Object), ctypes.c_int, _PD, _PD, _PD, _PD, _PD,
+                                        ctypes.POINTER(ctypes.c_int64)]
             _lib = L
     return _lib
 
@@ -380,3 +395,77 @@ def render_diff(scene_a: Scene, scene_b: Scene, cam: dict, opts: dict, rows=None
     if rc != 0:
         raise ValueError("oracle render rejected its arguments")
     return s, s2, {"paths": st.paths, "vertices": st.vertices, "truncated": st.truncated}
+
+
+# number of derivative slots of the oracle's dual numbers and their layout
+DUAL_SLOTS = 33
+SLOT_MEAN, SLOT_VAR, SLOT_CS, SLOT_L, SLOT_ALB = 0, 8, 16, 24, 25
+_DUAL_WHAT = {"sigma_t": 0, "projected_area": 1, "ndf": 2, "log_phase": 3}
+
+
+def dual_eval(scene: Scene, k: int, what: str, x, d, d2=None):
+    """The oracle's dual-number evaluation of one quantity at x in object k: returns
+    (value, derivative slots (33,), corner node indices (8,)) or None where it is
+    undefined (see gpss_oracle.h, orc_dual_eval)."""
+    xa, xp = _vec(x)
+    da, dp = _vec(d)
+    d2a, d2p = _vec(d2 if d2 is not None else d)
+    v = ctypes.c_double()
+    der = np.zeros(DUAL_SLOTS)
+    node = np.zeros(8, dtype=np.int64)
+    ok = lib().orc_dual_eval(ctypes.byref(scene._objs[k]), _DUAL_WHAT[what], xp, dp, d2p, ctypes.byref(v),
+                             der.ctypes.data_as(_PD), node.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if not ok:
+        return None
+    return v.value, der, node
+
+
+def render_grad(scene: Scene, cam: dict, opts: dict, d_image, rows=None, cols=None, threads: int = 0,
+                nodes=None, want=("mean", "var", "albedo", "l")):
+    """The oracle's adjoint: gradient of sum(d_image * image) over the selected pixels
+    with respect to each object's grids and length scale (path replay of the
+    regular-tracking estimator, partials from dual numbers).  nodes: None (every
+    node) or one array of node indices per object (x fastest); the outputs then
+    follow that order.  Returns (list of dicts per object with the wanted keys of
+    'mean', 'var', 'albedo' (channels, n), 'cscale', 'l'), stats)."""
+    H, Wd = int(cam["height"]), int(cam["width"])
+    g = np.ascontiguousarray(np.asarray(d_image, dtype=np.float64).reshape(H, Wd, 3))
+    n_objs = scene.s.n_objs
+    outs = (_GradOut * n_objs)()
+    res, keep = [], []
+    for k in range(n_objs):
+        ob = scene._objs[k]
+        N = ob.nx * ob.ny * ob.nz
+        o = outs[k]
+        if nodes is not None and nodes[k] is not None:
+            nd = np.ascontiguousarray(np.asarray(nodes[k], dtype=np.int64))
+            keep.append(nd)
+            o.nodes = nd.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            o.n_nodes = len(nd)
+            n = len(nd)
+        else:
+            n = N
+        r = {}
+        for key, field, size in (("mean", "d_mean", n), ("var", "d_var", n), ("albedo", "d_albedo", n * ob.channels),
+                                 ("cscale", "d_cscale", n), ("l", "d_l", 1)):
+            if key in want and (key != "cscale" or bool(ob.cscale)):
+                a = np.zeros(size)
+                r[key] = a
+                setattr(o, field, a.ctypes.data_as(_PD))
+        if "albedo" in r:
+            r["albedo"] = r["albedo"].reshape(ob.channels, n)
+        res.append(r)
+    st = _Stats()
+    mism = ctypes.c_uint64()
+    c = _camera(cam)
+    op = _opts(cam, opts, rows, cols, threads)
+    rc = lib().orc_render_grad(scene.ptr, ctypes.byref(c), ctypes.byref(op), g.ctypes.data_as(_PD), outs,
+                               ctypes.byref(st), ctypes.byref(mism))
+    if rc == 2:
+        raise NotImplementedError("oracle adjoint: isotropic GPSS objects only")
+    if rc != 0:
+        raise ValueError("oracle adjoint rejected its arguments")
+    for r in res:
+        if "l" in r:
+            r["l"] = float(r["l"][0])
+    return res, {"paths": st.paths, "vertices": st.vertices, "truncated": st.truncated, "mismatch": mism.value}

@@ -148,6 +148,38 @@ int orc_render(const orc_scene* s, const orc_camera* cam, const orc_render_opts*
 int orc_render_diff(const orc_scene* a, const orc_scene* b, const orc_camera* cam,
                     const orc_render_opts* o, double* sum, double* sumsq, orc_stats* st);
 
+/* Gradient of the expected image's loss by path replay of the same regular-
+ * tracking estimator (the oracle's adjoint).  d_image: width*height*3 doubles,
+ * dLoss/dpixel (the loss is sum over the selected pixels of d_image * image).
+ * out: one entry per object.  Gradients are ACCUMULATED (+=); a NULL output is
+ * not computed.  nodes != NULL restricts the outputs to those node indices
+ * (x fastest; each output then has n_nodes entries, in that order, albedo
+ * channels planes of n_nodes), else every node (nx*ny*nz).  Isotropic GPSS
+ * objects only (stationary or with a correlation-scale grid).  Returns 0, 1 for
+ * bad arguments, 2 for an unsupported object.  *mismatch (nullable): quadrature
+ * points that fell outside their piece's field cell (expected 0). */
+typedef struct {
+  const int64_t* nodes;
+  int64_t n_nodes;
+  double* d_mean;
+  double* d_var;
+  double* d_albedo;
+  double* d_cscale;          /* objects with a correlation-scale grid only       */
+  double* d_l;               /* 1 double: the object's length scale l_t          */
+} orc_grad_out;
+
+int orc_render_grad(const orc_scene* s, const orc_camera* cam, const orc_render_opts* o,
+                    const double* d_image, orc_grad_out* out, orc_stats* st, uint64_t* mismatch);
+
+/* Dual-number evaluation at one point of object k (test access to the adjoint's
+ * partials): value and the ORC_ND derivative slots (corner k of the cell: mean
+ * k, variance 8+k, correlation scale 16+k, l 24, albedo channel 0 25+k) of
+ * sigma_t(x, d) (what = 0), sigma(d) (1), D(m = d2) (2) or ln(D(m)/sigma(d)) of
+ * the pair (d, d2) (3); node[8] receives the corners' node indices.  Returns 0
+ * outside the object's box or where the quantity is undefined. */
+int orc_dual_eval(const orc_object* o, int what, const double x[3], const double d[3], const double d2[3],
+                  double* out_v, double* out_d, int64_t* node);
+
 /* Camera ray through pixel (px,py) at sub-pixel jitter (jx,jy) in [0,1). */
 void orc_camera_ray(const orc_camera* c, int px, int py, double jx, double jy,
                     double org[3], double dir[3]);

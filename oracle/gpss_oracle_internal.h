@@ -39,5 +39,30 @@ double orc_integrate_rough(orc_fn f, void* ctx, double a, double b);
 double orc_erfinv(double v);
 void orc_uniform4(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t bounce,
                   uint32_t purpose, uint32_t draw, double u[4]);
+/* Gauss-Legendre nodes and weights on [-1, 1] of the adaptive rule; returns the count. */
+int orc_gl_nodes(const double** x, const double** w);
+
+/* ---- forward-mode dual numbers (gpss_oracle_dual.c), for orc_render_grad ---- */
+/* Derivative slots: the 8 cell corners of a field sample for the mean, the
+ * variance and the correlation-scale factor, the object's length scale, and the
+ * 8 corners of one albedo channel. */
+#define ORC_ND 33
+enum { ORC_SLOT_MEAN = 0, ORC_SLOT_VAR = 8, ORC_SLOT_CS = 16, ORC_SLOT_L = 24, ORC_SLOT_ALB = 25 };
+typedef struct { double v; double d[ORC_ND]; } orc_dual;
+typedef struct {
+  orc_dual mu, g[3], var, cs, F[3]; /* trilinear fields and grad mu of the interpolant     */
+  orc_dual sigma, alpha;            /* sqrt(var), sqrt(2) sigma/(l s(x))                    */
+  int64_t node[8];                  /* node index of corner k (the slots' parameters)     */
+} orc_dfield;
+orc_dual orc_dconst(double v);
+int orc_dual_field(const orc_object* o, const double x[3], orc_dfield* f);
+orc_dual orc_dual_projected_area(const orc_dfield* f, const double d[3]);
+orc_dual orc_dual_sigma_t(const orc_dfield* f, const double d[3]);
+orc_dual orc_dual_ndf(const orc_dfield* f, const double m[3]);
+int orc_dual_log_phase(const orc_dfield* f, const double d[3], const double d2[3], orc_dual* out);
+/* Adaptive Gauss-Legendre integral of a dual-valued function over [a, b]: panels are
+ * split until every component (value and each derivative) converges. */
+typedef orc_dual (*orc_dfn)(double t, void* ctx);
+orc_dual orc_integrate_dual(orc_dfn f, void* ctx, const double* breaks, int nbreaks);
 
 #endif

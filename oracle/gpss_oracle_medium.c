@@ -625,6 +625,13 @@ static double gl_adapt(orc_fn f, void* ctx, double a, double b, double whole, do
   return gl_adapt(f, ctx, a, m, l, 0.5 * tol, depth + 1) + gl_adapt(f, ctx, m, b, r, 0.5 * tol, depth + 1);
 }
 
+int orc_gl_nodes(const double** x, const double** w) {
+  pthread_once(&gl_once, gl_init);
+  *x = gl_x;
+  *w = gl_w;
+  return ORC_NGL;
+}
+
 /* Integral of f over [a,b] to an absolute tolerance abs_tol. */
 double orc_integrate(orc_fn f, void* ctx, double a, double b, double abs_tol) {
   pthread_once(&gl_once, gl_init);

@@ -287,11 +287,150 @@ static double power_heuristic(double a, double b) {
   return a2 / (a2 + b2);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint (orc_render_grad).  Path replay: the path is traced a second time  */
+/* with the same random numbers, knowing its total radiance L_tot.  With the  */
+/* sampling densities, the extinction-proportional object choice and the MIS  */
+/* weights held fixed (their derivatives cancel in expectation: the sampled    */
+/* paths' densities do not enter the expected image, and MIS weights sum to   */
+/* one), the derivative of the path's estimate is the sum over its factors f  */
+/* of d ln f times the radiance the path collects downstream of f.  The       */
+/* factors of the regular-tracking estimator are                               */
+/*   flight to a real collision at t:  sigma_t,k(x_t) exp(-int_0^t sigma_t)  */
+/*   escaping flight:                  exp(-int_0^inf sigma_t)               */
+/*   NEE:                              p_k(d, w_L) exp(-int sigma_t along w_L) */
+/*   phase sample:                     p_k(d, d')                             */
+/* (p includes F).  d ln of an exponential factor is -int d sigma_t, which    */
+/* the oracle integrates by quadrature along the segment (not by collisions). */
+/* Every partial comes from the dual numbers of gpss_oracle_dual.c.           */
+/* ------------------------------------------------------------------------ */
+typedef struct {             /* one object's request (shared by the workers) */
+  const int32_t* map;        /* node -> output slot (-1: not wanted); NULL: slot = node */
+  int64_t n;                 /* output length of each field */
+  int channels;
+  int want_mean, want_var, want_alb, want_cs, want_l;
+} greq;
+
+typedef struct {             /* one worker's accumulators for one object */
+  double *mean, *var, *alb, *cs;
+  double l;
+} gacc;
+
+typedef struct {
+  const greq* rq;            /* per object */
+  gacc* acc;                 /* per object, this worker's */
+  double gpix[3];            /* dLoss/dpixel / spp of the path's pixel */
+  double Ltot[3];            /* the path's radiance (first pass) */
+  uint64_t mismatch;         /* quadrature points that left the piece's field cell */
+} gctx;
+
+static int64_t slot_of(const greq* rq, int64_t node) { return rq->map ? (int64_t)rq->map[node] : node; }
+
+/* Whether the extinction of a field sample with these corners matters to the request. */
+static int cell_wanted(const greq* rq, const int64_t node[8]) {
+  if (rq->want_l) return 1;
+  if (!(rq->want_mean || rq->want_var || rq->want_cs)) return 0;
+  for (int k = 0; k < 8; ++k)
+    if (slot_of(rq, node[k]) >= 0) return 1;
+  return 0;
+}
+
+/* accumulates W * dv (dv: derivative slots of a field sample with corners f->node) */
+static void scatter_dual(const greq* rq, gacc* a, const orc_dfield* f, const double* dv, double W) {
+  if (W == 0.0) return;
+  for (int k = 0; k < 8; ++k) {
+    int64_t j = slot_of(rq, f->node[k]);
+    if (j < 0) continue;
+    if (rq->want_mean) a->mean[j] += W * dv[ORC_SLOT_MEAN + k];
+    if (rq->want_var) a->var[j] += W * dv[ORC_SLOT_VAR + k];
+    if (rq->want_cs) a->cs[j] += W * dv[ORC_SLOT_CS + k];
+  }
+  if (rq->want_l) a->l += W * dv[ORC_SLOT_L];
+}
+
+/* accumulates sum_c Wc[c] d ln F_c (F_c the albedo channel c at the sample) */
+static void scatter_albedo(const greq* rq, gacc* a, const orc_dfield* f, const double Wc[3]) {
+  if (!rq->want_alb) return;
+  for (int c = 0; c < 3; ++c) {
+    if (Wc[c] == 0.0 || !(f->F[c].v > 0.0)) continue;
+    int plane = rq->channels == 1 ? 0 : c;
+    for (int k = 0; k < 8; ++k) {
+      int64_t j = slot_of(rq, f->node[k]);
+      if (j >= 0) a->alb[(size_t)plane * rq->n + j] += Wc[c] * f->F[c].d[ORC_SLOT_ALB + k] / f->F[c].v;
+    }
+  }
+}
+
+typedef struct {
+  const orc_object* ob;
+  const double* o;
+  const double* d;
+  int64_t node0;
+  uint64_t* mismatch;
+} seg_ctx;
+
+static orc_dual dsig_along(double t, void* vp) {
+  const seg_ctx* c = (const seg_ctx*)vp;
+  double x[3];
+  ray_at(c->o, c->d, t, x);
+  orc_dfield f;
+  if (!orc_dual_field(c->ob, x, &f) || f.node[0] != c->node0) {
+    ++*c->mismatch;
+    return orc_dconst(0.0);
+  }
+  return orc_dual_sigma_t(&f, c->d);
+}
+
+/* -W int_0^tmax d sigma_t ds along o + s d (the derivative of ln exp(-tau)):
+ * per piece of build_pieces (each inside one field cell of every object) the
+ * dual extinction of each object is integrated by adaptive quadrature. */
+static void grad_segment(const orc_scene* s, gctx* g, const double o[3], const double d[3], double tmax,
+                         double W) {
+  if (W == 0.0) return;
+  double* pc = NULL;
+  int n = build_pieces(s, o, d, 0.0, tmax, &pc);
+  for (int i = 0; i < n; ++i) {
+    double a = pc[2 * i], b = pc[2 * i + 1], mid[3];
+    ray_at(o, d, 0.5 * (a + b), mid);
+    for (int k = 0; k < s->n_objs; ++k) {
+      orc_dfield f;
+      if (!orc_dual_field(&s->objs[k], mid, &f) || !cell_wanted(&g->rq[k], f.node)) continue;
+      seg_ctx c = {&s->objs[k], o, d, f.node[0], &g->mismatch};
+      double br[2] = {a, b};
+      orc_dual I = orc_integrate_dual(dsig_along, &c, br, 2);
+      scatter_dual(&g->rq[k], &g->acc[k], &f, I.d, -W);
+    }
+  }
+  free(pc);
+}
+
+/* Wc[c] = dLoss/dpixel_c / spp times the radiance c the path collects from here on */
+static double downstream(const gctx* g, const double L[3], double Wc[3]) {
+  double W = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    Wc[c] = g->gpix[c] * (g->Ltot[c] - L[c]);
+    W += Wc[c];
+  }
+  return W;
+}
+
+/* d ln p_k(d, d2) with channel weights Wc at the field sample f */
+static void grad_phase(const gctx* g, int k, const orc_dfield* f, const double d[3], const double d2[3],
+                       const double Wc[3]) {
+  double W = Wc[0] + Wc[1] + Wc[2];
+  if (W == 0.0 && Wc[0] == 0.0 && Wc[1] == 0.0 && Wc[2] == 0.0) return;
+  orc_dual lp;
+  if (!orc_dual_log_phase(f, d, d2, &lp)) return;
+  scatter_dual(&g->rq[k], &g->acc[k], f, lp.d, W);
+  scatter_albedo(&g->rq[k], &g->acc[k], f, Wc);
+}
+
 /* One path: camera ray, then per real scattering vertex next-event
  * estimation and phase-function sampling (MIS with the environment).  At
- * most max_bounces real vertices; no continuation after the last. */
+ * most max_bounces real vertices; no continuation after the last.
+ * g != NULL: the gradient replay of a path whose radiance g->Ltot is known. */
 static void trace_path(const orc_scene* s, const orc_camera* cam, const orc_render_opts* op, int px,
-                       int py, int sample, double L[3], uint64_t* nvert, int* truncated) {
+                       int py, int sample, double L[3], uint64_t* nvert, int* truncated, gctx* g) {
   const uint32_t pixel = (uint32_t)(py * cam->width + px);
   const double inv4pi = 1.0 / (4.0 * ORC_PI);
   double u[4], o[3], d[3], beta[3] = {1.0, 1.0, 1.0}, prev_pdf = -1.0;
@@ -302,13 +441,15 @@ static void trace_path(const orc_scene* s, const orc_camera* cam, const orc_rend
   const int env = s->light.type != ORC_LIGHT_DIRECTIONAL;
   for (int bounce = 0;; ++bounce) {
     orc_uniform4(op->seed, pixel, (uint32_t)sample, (uint32_t)bounce, P_FLIGHT, 0, u);
-    double t;
+    double t, Wc[3], Wseg = 0.0;
+    if (g) Wseg = downstream(g, L, Wc);
     if (!free_flight(s, o, d, -log(u[0]), &t)) {
       if (env) {
         double Le[3], w = prev_pdf < 0.0 ? 1.0 : power_heuristic(prev_pdf, inv4pi);
         env_radiance(&s->light, d, Le);
         for (int c = 0; c < 3; ++c) L[c] += beta[c] * Le[c] * w;
       }
+      if (g) grad_segment(s, g, o, d, INFINITY, Wseg);
       return;
     }
     double x[3];
@@ -327,24 +468,46 @@ static void trace_path(const orc_scene* s, const orc_camera* cam, const orc_rend
     while (kk > 0 && sig[kk] == 0.0) --kk;
     orc_fpt p;
     if (!orc_point(&s->objs[kk], x, &p)) return;
-    /* next-event estimation */
-    double pv[3], pdf_ph;
+    orc_dfield df;
+    if (g) {
+      /* flight factor sigma_t,k(x) exp(-int_0^t sigma_t): d ln = d sigma_t,k/sigma_t,k - int d sigma_t */
+      orc_dual_field(&s->objs[kk], x, &df);
+      orc_dual st = orc_dual_sigma_t(&df, d);
+      if (st.v > 0.0) {
+        double dv[ORC_ND];
+        for (int i = 0; i < ORC_ND; ++i) dv[i] = st.d[i] / st.v;
+        scatter_dual(&g->rq[kk], &g->acc[kk], &df, dv, Wseg);
+      }
+      grad_segment(s, g, o, d, t, Wseg);
+    }
+    /* next-event estimation: contribution C = beta p Tr Le (w / light pdf) */
+    double pv[3], pdf_ph, C[3] = {0.0, 0.0, 0.0}, wl[3];
     if (!env) {
-      const double* wl = s->light.dir;
+      for (int a = 0; a < 3; ++a) wl[a] = s->light.dir[a];
       orc_phase_eval_point(&p, d, wl, op->mix_R, pv, &pdf_ph);
       double Tr = orc_transmittance(s, x, wl, INFINITY);
-      for (int c = 0; c < 3; ++c) L[c] += beta[c] * pv[c] * Tr * s->light.radiance[c];
+      for (int c = 0; c < 3; ++c) C[c] = beta[c] * pv[c] * Tr * s->light.radiance[c];
     } else {
       double z = 1.0 - 2.0 * u[2], ph = 2.0 * ORC_PI * u[3], r = sqrt(fmax(0.0, 1.0 - z * z));
-      double wl[3] = {r * cos(ph), r * sin(ph), z};
+      wl[0] = r * cos(ph);
+      wl[1] = r * sin(ph);
+      wl[2] = z;
       orc_phase_eval_point(&p, d, wl, op->mix_R, pv, &pdf_ph);
       if (pv[0] > 0.0 || pv[1] > 0.0 || pv[2] > 0.0) {
         double Tr = orc_transmittance(s, x, wl, INFINITY);
         double Le[3], w = power_heuristic(inv4pi, pdf_ph);
         env_radiance(&s->light, wl, Le);
-        for (int c = 0; c < 3; ++c) L[c] += beta[c] * pv[c] * Tr * Le[c] * w / inv4pi;
+        for (int c = 0; c < 3; ++c) C[c] = beta[c] * pv[c] * Tr * Le[c] * w / inv4pi;
       }
     }
+    if (g) {
+      /* NEE factors p_k(d, w_L) and exp(-int sigma_t along w_L), weighted by C itself */
+      double Wn[3];
+      for (int c = 0; c < 3; ++c) Wn[c] = g->gpix[c] * C[c];
+      grad_phase(g, kk, &df, d, wl, Wn);
+      grad_segment(s, g, x, wl, INFINITY, Wn[0] + Wn[1] + Wn[2]);
+    }
+    for (int c = 0; c < 3; ++c) L[c] += C[c];
     if (bounce + 1 >= op->max_bounces) {
       *truncated = 1;
       return;
@@ -352,6 +515,11 @@ static void trace_path(const orc_scene* s, const orc_camera* cam, const orc_rend
     orc_uniform4(op->seed, pixel, (uint32_t)sample, (uint32_t)bounce, P_PHASE, 0, u);
     double d2[3], wgt[3], pdf;
     if (!orc_phase_sample_point(&p, d, op->mix_R, u, d2, wgt, &pdf)) return;
+    if (g) {
+      /* phase-sample factor p_k(d, d2), weighted by everything collected after this vertex's NEE */
+      downstream(g, L, Wc);
+      grad_phase(g, kk, &df, d, d2, Wc);
+    }
     for (int c = 0; c < 3; ++c) beta[c] *= wgt[c];
     prev_pdf = pdf;
     for (int a = 0; a < 3; ++a) { o[a] = x[a]; d[a] = d2[a]; }
@@ -383,12 +551,12 @@ static void* worker(void* vp) {
       for (int s = 0; s < j->op->spp; ++s) {
         double La[3], Lb[3] = {0.0, 0.0, 0.0};
         int tr;
-        trace_path(j->a, j->cam, j->op, px, py, s, La, &nv, &tr);
+        trace_path(j->a, j->cam, j->op, px, py, s, La, &nv, &tr, NULL);
         nt += tr;
         if (j->b) {
           uint64_t nv2 = 0;
           int tr2;
-          trace_path(j->b, j->cam, j->op, px, py, s, Lb, &nv2, &tr2);
+          trace_path(j->b, j->cam, j->op, px, py, s, Lb, &nv2, &tr2, NULL);
         }
         for (int c = 0; c < 3; ++c) {
           double v = La[c] - Lb[c];
@@ -442,4 +610,152 @@ int orc_render_diff(const orc_scene* a, const orc_scene* b, const orc_camera* ca
                     const orc_render_opts* o, double* sum, double* sumsq, orc_stats* st) {
   if (!b) return 1;
   return run(a, b, cam, o, sum, sumsq, st);
+}
+
+/* ------------------------------------------------------------------------ */
+/* orc_render_grad: workers over pixel rows, each with its own accumulators. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_scene* s;
+  const orc_camera* cam;
+  const orc_render_opts* op;
+  const double* d_image;
+  const greq* rq;
+  orc_grad_out* out;
+  int next, nrows;
+  uint64_t paths, vertices, truncated, mismatch;
+  pthread_mutex_t mu;
+} gjob_t;
+
+static double* zalloc(size_t n) { return n ? (double*)calloc(n, sizeof(double)) : NULL; }
+
+static void* grad_worker(void* vp) {
+  gjob_t* j = (gjob_t*)vp;
+  const int no = j->s->n_objs;
+  gacc acc[16];
+  gctx g;
+  memset(&g, 0, sizeof(g));
+  g.rq = j->rq;
+  g.acc = acc;
+  for (int k = 0; k < no; ++k) {
+    const greq* r = &j->rq[k];
+    acc[k].mean = r->want_mean ? zalloc((size_t)r->n) : NULL;
+    acc[k].var = r->want_var ? zalloc((size_t)r->n) : NULL;
+    acc[k].alb = r->want_alb ? zalloc((size_t)r->n * r->channels) : NULL;
+    acc[k].cs = r->want_cs ? zalloc((size_t)r->n) : NULL;
+    acc[k].l = 0.0;
+  }
+  uint64_t np = 0, nv = 0, nt = 0;
+  for (;;) {
+    int r = __atomic_fetch_add(&j->next, 1, __ATOMIC_RELAXED);
+    if (r >= j->nrows) break;
+    int py = j->op->row_begin + r * j->op->row_step;
+    for (int px = j->op->col_begin; px < j->op->col_end; ++px) {
+      size_t pix = (size_t)py * j->cam->width + px;
+      for (int c = 0; c < 3; ++c) g.gpix[c] = j->d_image[pix * 3 + c] / j->op->spp;
+      int any = g.gpix[0] != 0.0 || g.gpix[1] != 0.0 || g.gpix[2] != 0.0;
+      for (int smp = 0; smp < j->op->spp; ++smp) {
+        double L[3];
+        int tr;
+        uint64_t v0 = 0;
+        trace_path(j->s, j->cam, j->op, px, py, smp, L, &v0, &tr, NULL);
+        nv += v0;
+        nt += tr;
+        ++np;
+        if (!any || (L[0] == 0.0 && L[1] == 0.0 && L[2] == 0.0)) continue;
+        for (int c = 0; c < 3; ++c) g.Ltot[c] = L[c];
+        double L2[3];
+        uint64_t v1 = 0;
+        trace_path(j->s, j->cam, j->op, px, py, smp, L2, &v1, &tr, &g);
+      }
+    }
+  }
+  pthread_mutex_lock(&j->mu);
+  for (int k = 0; k < no; ++k) {
+    const greq* r = &j->rq[k];
+    orc_grad_out* o = &j->out[k];
+    for (int64_t i = 0; i < r->n; ++i) {
+      if (acc[k].mean) o->d_mean[i] += acc[k].mean[i];
+      if (acc[k].var) o->d_var[i] += acc[k].var[i];
+      if (acc[k].cs) o->d_cscale[i] += acc[k].cs[i];
+    }
+    if (acc[k].alb)
+      for (int64_t i = 0; i < r->n * r->channels; ++i) o->d_albedo[i] += acc[k].alb[i];
+    if (r->want_l) *o->d_l += acc[k].l;
+    free(acc[k].mean);
+    free(acc[k].var);
+    free(acc[k].alb);
+    free(acc[k].cs);
+  }
+  j->paths += np;
+  j->vertices += nv;
+  j->truncated += nt;
+  j->mismatch += g.mismatch;
+  pthread_mutex_unlock(&j->mu);
+  return NULL;
+}
+
+int orc_render_grad(const orc_scene* s, const orc_camera* cam, const orc_render_opts* op,
+                    const double* d_image, orc_grad_out* out, orc_stats* st, uint64_t* mismatch) {
+  if (!s || !cam || !op || !d_image || !out || op->spp <= 0 || op->max_bounces <= 0 || op->row_step <= 0)
+    return 1;
+  if (s->n_objs < 1 || s->n_objs > 16) return 1;
+  if (op->row_begin < 0 || op->row_end > cam->height || op->col_begin < 0 || op->col_end > cam->width) return 1;
+  for (int k = 0; k < s->n_objs; ++k) {
+    const orc_object* ob = &s->objs[k];
+    double lb = ob->length_scale_b > 0.0 ? ob->length_scale_b : ob->length_scale;
+    double ln = ob->length_scale_n > 0.0 ? ob->length_scale_n : ob->length_scale;
+    if (ob->ndf != ORC_NDF_GPSS || lb != ob->length_scale || ln != ob->length_scale || ob->tangent) return 2;
+    if (out[k].d_cscale && !ob->cscale) return 1;
+  }
+  greq rq[16];
+  int32_t* maps[16] = {NULL};
+  int rc = 0;
+  for (int k = 0; k < s->n_objs; ++k) {
+    const orc_object* ob = &s->objs[k];
+    const int64_t N = (int64_t)ob->nx * ob->ny * ob->nz;
+    greq* r = &rq[k];
+    memset(r, 0, sizeof(*r));
+    r->channels = ob->channels;
+    r->want_mean = out[k].d_mean != NULL;
+    r->want_var = out[k].d_var != NULL;
+    r->want_alb = out[k].d_albedo != NULL;
+    r->want_cs = out[k].d_cscale != NULL;
+    r->want_l = out[k].d_l != NULL;
+    if (out[k].nodes) {
+      maps[k] = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+      for (int64_t i = 0; i < N; ++i) maps[k][i] = -1;
+      for (int64_t i = 0; i < out[k].n_nodes; ++i) {
+        int64_t v = out[k].nodes[i];
+        if (v < 0 || v >= N) rc = 1;
+        else maps[k][v] = (int32_t)i;
+      }
+      r->map = maps[k];
+      r->n = out[k].n_nodes;
+    } else {
+      r->n = N;
+    }
+  }
+  if (rc == 0) {
+    gjob_t j;
+    memset(&j, 0, sizeof(j));
+    j.s = s; j.cam = cam; j.op = op; j.d_image = d_image; j.rq = rq; j.out = out;
+    j.nrows = op->row_end > op->row_begin ? (op->row_end - op->row_begin + op->row_step - 1) / op->row_step : 0;
+    pthread_mutex_init(&j.mu, NULL);
+    int nt = op->threads > 0 ? op->threads : (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nt < 1) nt = 1;
+    if (nt > 256) nt = 256;
+    pthread_t th[256];
+    for (int i = 0; i < nt; ++i) pthread_create(&th[i], NULL, grad_worker, &j);
+    for (int i = 0; i < nt; ++i) pthread_join(th[i], NULL);
+    pthread_mutex_destroy(&j.mu);
+    if (st) {
+      st->paths = j.paths;
+      st->vertices = j.vertices;
+      st->truncated = j.truncated;
+    }
+    if (mismatch) *mismatch = j.mismatch;
+  }
+  for (int k = 0; k < s->n_objs; ++k) free(maps[k]);
+  return rc;
 }

@@ -115,40 +115,73 @@ def dyadic_slab(albedo=0.75, light=None, mean="plane", nodes=(17, 17, 9), sigma=
     return {"objects": [obj], "light": light or W.directional_light((0.0, 0.0, 1.0), 1.0)}
 
 
-def slab_projected_area(d, sigma=SLAB_SIGMA, l=SLAB_L):
-    """sigma(d) for the plane mean (grad = (0,0,1)); textbook E[max(0,X)],
-    X ~ N(m, s^2) = m Phi(m/s) + s phi(m/s) with m = -d_z, s = sigma/l."""
+def slab_projected_area(d, sigma=SLAB_SIGMA, l=SLAB_L, slope=1.0):
+    """sigma(d) for the plane mean mu = slope * z (grad = (0,0,slope)); textbook
+    E[max(0,X)], X ~ N(m, s^2) = m Phi(m/s) + s phi(m/s) with m = -slope d_z, s = sigma/l."""
     s = sigma / l
-    m = -d[2]
+    m = -slope * d[2]
     return m * sp.ndtr(m / s) + s * math.exp(-0.5 * (m / s) ** 2) / math.sqrt(2 * math.pi)
 
 
-def slab_optical_depth(z0, z1, d, sigma=SLAB_SIGMA, l=SLAB_L):
-    """Optical depth between heights z0 and z1 along d for the plane mean:
-    int lambda(u) du = ln Phi(u), so tau = sigma(d)/d_z (lnPhi(z1/sigma) - lnPhi(z0/sigma))."""
-    return slab_projected_area(d, sigma, l) / d[2] * (sp.log_ndtr(z1 / sigma) - sp.log_ndtr(z0 / sigma))
+def slab_optical_depth(z0, z1, d, sigma=SLAB_SIGMA, l=SLAB_L, slope=1.0):
+    """Optical depth between heights z0 and z1 along d for the plane mean mu = slope z:
+    int lambda(u) du = ln Phi(u) with u = slope z/sigma, so
+    tau = sigma(d)/(slope d_z) (lnPhi(slope z1/sigma) - lnPhi(slope z0/sigma))."""
+    return slab_projected_area(d, sigma, l, slope) / (slope * d[2]) * (
+        sp.log_ndtr(slope * z1 / sigma) - sp.log_ndtr(slope * z0 / sigma))
 
 
-def slab_single_scatter(d, wl, albedo, sigma=SLAB_SIGMA, l=SLAB_L, irradiance=1.0, ztop=0.125, zbot=-0.125, shift=0.0):
+def slab_single_scatter(d, wl, albedo, sigma=SLAB_SIGMA, l=SLAB_L, irradiance=1.0, ztop=0.125, zbot=-0.125, shift=0.0,
+                        slope=1.0):
     """Exact single-scattered radiance for a ray entering the slab top along d
     (d_z < 0) and leaving through the bottom, lit by a directional light from
     wl (wl_z > 0, leaving through the top).  p is constant along the ray, so
     L = int Tr_cam sigma_t p Tr_light E dt is a 1-D integral of closed forms.
-    `shift` moves the mean to mu = z + shift (the box stays put)."""
+    `shift` moves the mean to mu = slope (z + shift) (the box stays put); `slope`
+    scales the plane mean's gradient to (0, 0, slope)."""
     from scipy.integrate import quad
     alpha = math.sqrt(2) * sigma / l
     m = np.asarray(wl) - np.asarray(d)
     m /= np.linalg.norm(m)
-    sd = slab_projected_area(d, sigma, l)
-    D = ndf_paper_closed_form(np.array([math.sqrt(max(0, 1 - m[2] ** 2)), 0, m[2]]), 1.0, alpha, alpha, alpha)
+    sd = slab_projected_area(d, sigma, l, slope)
+    D = ndf_paper_closed_form(np.array([math.sqrt(max(0, 1 - m[2] ** 2)), 0, m[2]]), slope, alpha, alpha, alpha)
     p = albedo * D / (4 * sd)
 
     def f(z):
-        u = (z + shift) / sigma
+        u = slope * (z + shift) / sigma
         rho = math.exp(-0.5 * u * u - 0.5 * math.log(2 * math.pi) - sp.log_ndtr(u)) / sigma
-        tau_c = slab_optical_depth(ztop + shift, z + shift, d, sigma, l)
-        tau_l = slab_optical_depth(z + shift, ztop + shift, wl, sigma, l)
+        tau_c = slab_optical_depth(ztop + shift, z + shift, d, sigma, l, slope)
+        tau_l = slab_optical_depth(z + shift, ztop + shift, wl, sigma, l, slope)
         return math.exp(-tau_c - tau_l) * rho * sd * p * irradiance / abs(d[2])
+
+    return quad(f, zbot, ztop, epsabs=0, epsrel=1e-12, limit=400)[0]
+
+
+def slab_single_scatter_objects(d, wl, objects, irradiance=1.0, ztop=0.125, zbot=-0.125):
+    """Exact single scattering (as slab_single_scatter) in a slab holding several
+    co-located plane-mean objects, each a tuple (albedo, sigma, l): extinctions add
+    along both rays, and the scattered radiance at height z is the sum over objects
+    of sigma_t,k(z) p_k (each object scatters with its own phase function and albedo)."""
+    from scipy.integrate import quad
+    m = np.asarray(wl) - np.asarray(d)
+    m /= np.linalg.norm(m)
+    mloc = np.array([math.sqrt(max(0, 1 - m[2] ** 2)), 0, m[2]])
+    terms = []
+    for F, sig, l in objects:
+        alpha = math.sqrt(2) * sig / l
+        sd = slab_projected_area(d, sig, l)
+        D = ndf_paper_closed_form(mloc, 1.0, alpha, alpha, alpha)
+        terms.append((F * D / (4 * sd), sd, sig, l))
+
+    def f(z):
+        tau = 0.0
+        scat = 0.0
+        for p, sd, sig, l in terms:
+            tau += slab_optical_depth(ztop, z, d, sig, l) + slab_optical_depth(z, ztop, wl, sig, l)
+            u = z / sig
+            rho = math.exp(-0.5 * u * u - 0.5 * math.log(2 * math.pi) - sp.log_ndtr(u)) / sig
+            scat += rho * sd * p
+        return math.exp(-tau) * scat * irradiance / abs(d[2])
 
     return quad(f, zbot, ztop, epsabs=0, epsrel=1e-12, limit=400)[0]
 

@@ -120,3 +120,49 @@ def test_orthographic_camera_convention():
     up = np.cross(right, D45)
     x, y = 2 * 0.5 / 4 - 1, 1 - 2 * 0.5 / 2
     np.testing.assert_allclose(o, -2 * D45 + x * 0.5 * right + y * 0.5 * up, atol=1e-15)
+
+
+def test_two_objects_choose_the_scatterer_by_extinction():
+    """Several objects (reading Q13): extinctions add, and a real collision scatters
+    off object k with probability sigma_t,k/sigma_t.  Two co-located plane-mean
+    objects with different variances, length scales and albedos: the single-
+    scattered radiance is exactly int T (sigma_t,A p_A + sigma_t,B p_B) T_L dt, a 1-D
+    integral of closed forms.  A uniform choice of the object would converge to
+    0.90x of it here, always the first object to 1.23x, always the second to 0.57x."""
+    objs = [(0.9, H.SLAB_SIGMA, H.SLAB_L), (0.2, 0.125, 0.25)]
+    a = H.dyadic_slab(albedo=objs[0][0], sigma=objs[0][1], l=objs[0][2])["objects"][0]
+    b = H.dyadic_slab(albedo=objs[1][0], sigma=objs[1][1], l=objs[1][2])["objects"][0]
+    S = oracle.Scene({"objects": [a, b], "light": W.directional_light((0.0, 0.0, 1.0), 1.0)})
+    ref = H.slab_single_scatter_objects(D45, np.array([0.0, 0.0, 1.0]), objs)
+    cam = W.ortho_camera_45(16, 16, film=0.5)
+    spp = 2048
+    s, s2, st = oracle.render(S, cam, {"spp": spp, "max_bounces": 1, "seed": 21}, rows=(6, 10, 1), cols=(6, 10))
+    v = s[6:10, 6:10, 0] / spp
+    se = np.sqrt(np.maximum(s2[6:10, 6:10, 0] / spp - v ** 2, 0) / spp)
+    se_mean = np.sqrt(np.sum(se ** 2)) / v.size
+    assert abs(v.mean() - ref) < 4 * se_mean, (v.mean(), ref, se_mean)
+    assert se_mean < 0.015 * ref  # a uniform choice (10% off) fails by more than 6 SE
+
+
+@pytest.mark.parametrize("tau", [100.0, 600.0, 740.0, 800.0, 5000.0, 20000.0])
+def test_transmittance_across_the_underflow_cutoff(tau):
+    """The oracle stops integrating once a rough optical depth exceeds 1e4, where
+    exp(-tau) is exactly 0 in double precision: on a constant-mean slab (sigma_t
+    constant, Tr = exp(-sigma_t L)) the returned transmittance equals the closed
+    form on both sides of underflow (tau = 745) and of the cut-off."""
+    sig, l, mu = 2.0 ** -8, 2.0 ** -11, -0.125
+    S = oracle.Scene(H.dyadic_slab(mean=mu, sigma=sig, l=l))
+    alpha = math.sqrt(2) * sig / l
+    st = oracle.inv_mills(mu / sig) / sig * alpha / (2 * math.sqrt(math.pi))
+    assert st > 1e4  # a unit length is beyond the cut-off
+    o = np.array([-0.45, 0.0, 0.0])
+    d = np.array([1.0, 0.0, 0.0])
+    L = tau / st
+    assert L < 0.9
+    ref = math.exp(-st * L)
+    got = oracle.transmittance(S, o, d, L)
+    if ref > 1e-300:
+        assert got == pytest.approx(ref, rel=1e-9)
+    else:
+        assert abs(got - ref) <= 1e-320
+    assert oracle.optical_depth(S, o, d, L) == pytest.approx(st * L, rel=1e-11)
