@@ -211,14 +211,17 @@ gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const gpss_render_
 
 /* Forward render that allocates no device memory during the call (the paper has
  * no counterpart; it is an integration aid).  For callers that may not allocate
- * at render time: applications that account for every device byte themselves,
- * real-time loops where an allocation's latency or failure is unacceptable, or
- * code recording work into a stream capture.  Same result as gpss_render with
+ * at render time: applications that account for every device byte themselves
+ * (a hidden cudaMalloc would break their budget), and real-time loops where an
+ * allocation's latency or failure is unacceptable.  Same result as gpss_render with
  * the same scene, camera and options (image only: no sqsum, no per-path
  * radiance, stats->ms = 0).  The work counters and a film of at most 65536
  * pixels (e.g. 256 x 256) live in a fixed 0.8 MB static device array that every
  * GPU loading the library keeps until the process exits; larger images are
- * rejected with GPSS_ERR_INVALID_ARG.  image: W*H*3 floats, host or device.
+ * rejected with GPSS_ERR_INVALID_ARG, and so are renders of more than 2^46 paths
+ * (W*H*spp), as in gpss_render.  image: W*H*3 floats, host or device; a host
+ * image (pinned or pageable) and stats are complete when the call returns (the
+ * stream is synchronised), a device image is written asynchronously on `stream`.
  * The first call on a device looks up the array's device address (make that
  * first call before any stream capture).  All calls share the array and clear
  * it before use: calls that overlap on the GPU race and must be serialised by

@@ -390,7 +390,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
     b->begins[i + 1] = b->begins[i] + P.total;
   }
   b->total = b->begins[n];
-  if (b->total > (1LL << 46)) { set_error("too many paths in the batch"); free_batch(b); return GPSS_ERR_INVALID_ARG; }
+  if (check_path_total(b->total, 1, "paths in the batch") != GPSS_OK) { free_batch(b); return GPSS_ERR_INVALID_ARG; }
   cudaStream_t cs = (cudaStream_t)stream;
   if ((e = cudaMallocHost(&b->table_host, n * sizeof(JobDev))) != cudaSuccess ||
       (e = cudaMalloc(&b->table_dev, n * sizeof(JobDev))) != cudaSuccess ||

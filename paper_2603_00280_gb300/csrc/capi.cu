@@ -373,13 +373,21 @@ extern "C" gpss_status gpss_scene_majorant(gpss_scene s, int dims[3], float* val
   return GPSS_OK;
 }
 
-static bool is_device_ptr(const void* p) {
+bool gpss::is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+gpss_status gpss::check_path_total(long long npx, long long spp, const char* what) {
+  if (npx > 0 && spp > (1LL << 46) / npx) {
+    set_error("too many paths (%s above 2^46)", what);
+    return GPSS_ERR_INVALID_ARG;
+  }
+  return GPSS_OK;
 }
 
 static gpss_status ensure(float** buf, size_t* cap, size_t n, const char* what) {
@@ -402,7 +410,7 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
   if (!camera_dev(cam, &C)) return GPSS_ERR_INVALID_ARG;
   const size_t npx = (size_t)C.width * C.height;
   const long long total = (long long)npx * opts->spp;
-  if (total > (1LL << 46)) { set_error("too many paths (W*H*spp)"); return GPSS_ERR_INVALID_ARG; }
+  if ((st = check_path_total((long long)npx, opts->spp, "W*H*spp")) != GPSS_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e;
   const bool host_img = !is_device_ptr(image);

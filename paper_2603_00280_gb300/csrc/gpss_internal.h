@@ -86,6 +86,12 @@ void set_error(const char* fmt, ...);
 // Fills *st from the kCntNum device counters copied to the host.
 void fill_stats(gpss_stats* st, const unsigned long long* c, float ms);
 gpss_status cuda_fail(cudaError_t e, const char* what);
+// Whether p is device (or managed) memory; host memory, pinned or pageable, gives false.
+bool is_device_ptr(const void* p);
+// INVALID_ARG (with the message set) when a render of npx pixels at spp samples has
+// more than 2^46 paths: every render entry point (single, allocation-free, batched)
+// enforces this one limit.
+gpss_status check_path_total(long long npx, long long spp, const char* what);
 
 gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cudaStream_t st);
 gpss_status build_majorant(gpss_scene s, cudaStream_t st);

@@ -3,10 +3,8 @@
 //
 // Who needs it: callers that may not allocate device memory at render time, e.g.
 // a host application that accounts for every device byte itself and forbids
-// hidden allocations, code that renders from a real-time loop where an
-// allocation's latency or a failure to allocate is unacceptable, or code issuing
-// work while a stream is being captured (allocation calls are not capturable
-// stream work).  gpss_render itself allocates nothing for device outputs, but it
+// hidden allocations, or code that renders from a real-time loop where an
+// allocation's latency or a failure to allocate is unacceptable.  gpss_render itself allocates nothing for device outputs, but it
 // keeps its work counters in the scene and allocates a staging film the first
 // time it is given a host image; this variant uses the file-scope array below
 // instead, for every call.
@@ -82,6 +80,8 @@ extern "C" gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam,
               C.width, C.height);
     return GPSS_ERR_INVALID_ARG;
   }
+  if ((st = check_path_total((long long)npx, opts->spp, "W*H*spp")) != GPSS_OK) return st;
+  const bool host_img = !is_device_ptr(image);
   void* base = nullptr;
   if ((st = noalloc_scratch(&base)) != GPSS_OK) return st;
   unsigned long long* counters = (unsigned long long*)base;
@@ -97,11 +97,15 @@ extern "C" gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam,
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   if ((e = cudaMemcpyAsync(image, film, 3 * npx * sizeof(float), cudaMemcpyDefault, cs)) != cudaSuccess)
     return cuda_fail(e, "image copy");
-  if (stats) {
-    unsigned long long c[kNoAllocCounterWords];
-    if ((e = cudaMemcpyAsync(c, counters, sizeof(c), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
-      return cuda_fail(e, "stats copy");
+  // a host image (pinned or pageable) or host stats are complete when the call returns,
+  // as with gpss_render: the stream is synchronised whenever either is on the host
+  unsigned long long c[kNoAllocCounterWords];
+  if (stats && (e = cudaMemcpyAsync(c, counters, sizeof(c), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+    return cuda_fail(e, "stats copy");
+  if (stats || host_img) {
     if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "render");
+  }
+  if (stats) {
     fill_stats(stats, c, 0.0f);
     stats->ms = 0.0f;
   }

@@ -1,8 +1,8 @@
 """The allocation-free render entry point against the regular one.
 
 gpss_render_noalloc serves callers that may not allocate device memory while
-rendering (strict device-memory accounting, real-time loops, work recorded into
-a stream capture).  It keeps its scratch in a fixed static device array instead
+rendering (applications that account for every device byte themselves, real-time
+loops where an allocation's latency or failure is unacceptable).  It keeps its scratch in a fixed static device array instead
 of scene-owned buffers.  Given the same scene, camera and options it renders the
 same paths, so its image must equal gpss_render's up to the summation order of
 the film's float atomics -- on two calls in a row, which also checks that the
@@ -48,6 +48,12 @@ def test_noalloc_render_matches_regular_render_twice():
         assert rc == 0, L.gpss_last_error()
         torch.cuda.synchronize()
         np.testing.assert_allclose(host, ref, rtol=1e-5, atol=1e-7)
+        # pinned host output without stats: complete when the call returns (no extra synchronize)
+        pinned = torch.full((24, 40, 3), -1.0, dtype=torch.float32).pin_memory()
+        rc = L.gpss_render_noalloc(S.handle, ctypes.byref(cam), ctypes.byref(opts), ctypes.c_void_p(pinned.data_ptr()),
+                                   None, stream)
+        assert rc == 0, L.gpss_last_error()
+        np.testing.assert_allclose(pinned.numpy(), ref, rtol=1e-5, atol=1e-7)
 
 
 def test_noalloc_render_rejects_images_beyond_its_scratch():
