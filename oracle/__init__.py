@@ -78,7 +78,7 @@ class _Opts(ctypes.Structure):
         ("spp", ctypes.c_int), ("max_bounces", ctypes.c_int), ("seed", ctypes.c_uint64),
         ("mix_R", ctypes.c_double), ("row_begin", ctypes.c_int), ("row_end", ctypes.c_int),
         ("row_step", ctypes.c_int), ("col_begin", ctypes.c_int), ("col_end", ctypes.c_int),
-        ("threads", ctypes.c_int),
+        ("threads", ctypes.c_int), ("sampler", ctypes.c_int),
     ]
 
 
@@ -127,6 +127,8 @@ def lib():
             L.orc_phase_eval.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, _PD, _PD, _PD, _D, _PD, _PD]
             L.orc_phase_sample.restype = ctypes.c_int
             L.orc_phase_sample.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, _PD, _PD, _D, _PD, _PD, _PD, _PD]
+            L.orc_phase_sample_exact.restype = ctypes.c_int
+            L.orc_phase_sample_exact.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, _PD, _PD, _PD, _PD, _PD, _PD]
             L.orc_optical_depth.restype = _D
             L.orc_optical_depth.argtypes = [ctypes.POINTER(_Scene), _PD, _PD, _D]
             L.orc_transmittance.restype = _D
@@ -331,6 +333,25 @@ def phase_sample(scene: Scene, k: int, pos, d_in, u, R: float = 0.5):
     return d2, w, pdf, ok
 
 
+def phase_sample_exact(scene: Scene, k: int, pos, d_in, u):
+    """Exact visible-normal samples (GPSS objects, Beckmann height fields): returns
+    (d_out, weight rgb (= F), pdf (= p/F), ok)."""
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    d_in = np.ascontiguousarray(np.asarray(d_in, dtype=np.float64).reshape(-1, 3))
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 3))
+    n = len(pos)
+    d2, w, pdf, ok = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n), np.zeros(n, bool)
+    L = lib()
+    a, b = np.zeros(3), np.zeros(3)
+    for i in range(n):
+        v = ctypes.c_double()
+        ok[i] = bool(L.orc_phase_sample_exact(scene.ptr, int(k), pos[i].ctypes.data_as(_PD),
+                                              d_in[i].ctypes.data_as(_PD), u[i].ctypes.data_as(_PD),
+                                              a.ctypes.data_as(_PD), b.ctypes.data_as(_PD), ctypes.byref(v)))
+        d2[i], w[i], pdf[i] = a, b, v.value
+    return d2, w, pdf, ok
+
+
 def optical_depth(scene: Scene, org, d, tmax=np.inf) -> float:
     oa, op = _vec(org)
     da, dp = _vec(d)
@@ -362,6 +383,7 @@ def _opts(cam, opts, rows, cols, threads):
     o.row_begin, o.row_end, o.row_step = int(r[0]), int(r[1]), int(r[2]) if len(r) > 2 else 1
     o.col_begin, o.col_end = int(c[0]), int(c[1])
     o.threads = int(threads)
+    o.sampler = {"mixture": 0, "vndf": 1}[opts.get("sampler", "mixture")]
     return o
 
 

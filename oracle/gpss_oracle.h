@@ -95,7 +95,13 @@ typedef struct {
   int row_begin, row_end, row_step;
   int col_begin, col_end;
   int threads;               /* <= 0: all hardware threads                    */
+  int sampler;               /* ORC_SAMPLER_MIXTURE (the paper's) or _EXACT     */
 } orc_render_opts;
+
+/* Phase sampling of the path tracer: the paper's mixture (end of Sec. 4.2), or
+ * exact visible-normal sampling where the object supports it (GPSS, Beckmann
+ * height fields; GGX keeps uniform half vectors).  Same expectation. */
+enum { ORC_SAMPLER_MIXTURE = 0, ORC_SAMPLER_EXACT = 1 };
 
 typedef struct {
   uint64_t paths, vertices, truncated;
@@ -134,6 +140,11 @@ int orc_phase_eval(const orc_scene* s, int k, const double x[3], const double d[
 int orc_phase_sample(const orc_scene* s, int k, const double x[3], const double d[3],
                      double R, const double u[3], double d2[3], double w_out[3],
                      double* pdf_out);
+/* Exact visible-normal sample of object k's phase function (GPSS objects and
+ * Beckmann height fields): d2 with pdf p/F, weight F (per channel).  Returns 0
+ * where unsupported (GGX) or for a measure-zero failure. */
+int orc_phase_sample_exact(const orc_scene* s, int k, const double x[3], const double d[3], const double u[3],
+                           double d2[3], double w_out[3], double* pdf_out);
 /* Optical depth and transmittance along o + t d, t in [0, tmax]. */
 double orc_optical_depth(const orc_scene* s, const double o[3], const double d[3], double tmax);
 double orc_transmittance(const orc_scene* s, const double o[3], const double d[3], double tmax);

@@ -34,6 +34,9 @@ int orc_phase_eval_point(const orc_fpt* p, const double d[3], const double d2[3]
                          double p_out[3], double* pdf_out);
 int orc_phase_sample_point(const orc_fpt* p, const double d[3], double R, const double u[3],
                            double d2[3], double w_out[3], double* pdf_out);
+int orc_phase_sample_exact_point(const orc_fpt* p, const double d[3], const double u[3], double d2[3],
+                                 double w_out[3], double* pdf_out);
+double orc_phase_pdf_exact(const orc_fpt* p, const double d[3], const double d2[3]);
 double orc_integrate(orc_fn f, void* ctx, double a, double b, double abs_tol);
 double orc_integrate_rough(orc_fn f, void* ctx, double a, double b);
 double orc_erfinv(double v);

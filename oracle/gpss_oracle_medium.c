@@ -573,6 +573,125 @@ int orc_phase_sample_point(const orc_fpt* p, const double d[3], double R, const 
   return 1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Exact visible-normal sampling.  The visible-normal density                */
+/* max(0, -d.m) D(m) / sigma(d) of Eq. microfacet_vndf is, by Eq. gdf_to_ndf   */
+/* (D(m) = int t^3 P(t m) dt and dg = t^2 dt dm), the direction of a slope g  */
+/* drawn with density proportional to max(0, -d.g) N(g; g0, Sigma).  With     */
+/* Sigma = L L^T (L symmetric), v = L d, s = |v| and e = -v/s, -d.g = s (beta + */
+/* e.xi) for g = g0 + L xi, beta = -d.g0/s: the component y = beta + e.xi has */
+/* density proportional to y phi(y - beta) on y > 0, and the components of xi */
+/* orthogonal to e are independent standard normals.  GPSS objects: g0 =     */
+/* grad mu, Sigma = sum_a (alpha_a^2/2) f_a f_a^T in the kernel frame.  Beckmann */
+/* height fields: the same with g0 = n and alpha_n = 0 (the Beckmann NDF is   */
+/* the GPSS with infinite correlation along n, Sec. 4.1).  The sample's pdf  */
+/* over d2 is p/F = D(m)/(4 sigma(d)) and its weight p/pdf is F.  (The paper  */
+/* samples a mixture instead; this sampler gives the oracle bounded path      */
+/* weights, so per-pixel sample variances are reliable.)                      */
+/* ------------------------------------------------------------------------ */
+static double std_pdf(double x) { return exp(-0.5 * x * x) / sqrt(2.0 * ORC_PI); }
+
+/* Mills ratio R(x) = (1 - Phi(x))/phi(x) = sqrt(pi/2) erfcx(x/sqrt2) */
+static double mills(double x) { return sqrt(0.5 * ORC_PI) * orc_erfcx(x / ORC_SQRT2); }
+
+/* Unnormalised CDF H(y) = int_0^y t phi(t - beta) dt = beta (Phi(y-beta) - Phi(-beta))
+ * + phi(beta) - phi(y-beta); for beta < 0 divided by phi(beta) and written with the
+ * Mills ratio (B = -beta): [1 - B R(B)] - E [1 - B R(y+B)], E = e^{-y^2/2 - y B}. */
+static double vis_cdf(double y, double beta) {
+  if (beta >= 0.0) {
+    double dPhi = 0.5 * (erfc(-(y - beta) / ORC_SQRT2) - erfc(beta / ORC_SQRT2));
+    return beta * dPhi + std_pdf(beta) - std_pdf(y - beta);
+  }
+  double B = -beta, E = exp(-0.5 * y * y - y * B);
+  return (1.0 - B * mills(B)) - E * (1.0 - B * mills(y + B));
+}
+
+static double vis_total(double beta) {
+  if (beta >= 0.0) return beta * 0.5 * erfc(-beta / ORC_SQRT2) + std_pdf(beta);
+  double B = -beta;
+  return 1.0 - B * mills(B);
+}
+
+/* y > 0 with density proportional to y phi(y - beta), at CDF value xi (bisection) */
+static double visible_slope(double beta, double xi) {
+  double target = xi * vis_total(beta);
+  double lo = 0.0, hi = (beta > 0.0 ? beta : 0.0) + 40.0;
+  for (int it = 0; it < 400 && hi - lo > 1e-15 * (1.0 + hi); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (vis_cdf(mid, beta) < target) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+static int exact_supported(const orc_fpt* p) { return p->ndf == ORC_NDF_GPSS || p->ndf == ORC_NDF_BECKMANN; }
+
+/* L v for the gradient covariance of the field point (see above) */
+static void cov_sqrt_apply(const orc_fpt* p, const double v[3], double out[3]) {
+  double a[3] = {p->ax, p->ay, p->az};
+  if (p->ndf == ORC_NDF_BECKMANN) { a[0] = a[1] = p->alpha; a[2] = 0.0; }
+  const double* f[3] = {p->ft, p->fb, p->fn};
+  out[0] = out[1] = out[2] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double c = a[k] / ORC_SQRT2 * dot3(f[k], v);
+    for (int i = 0; i < 3; ++i) out[i] += c * f[k][i];
+  }
+}
+
+/* pdf over d2 of the exact sampler: p/F = D(m) / (4 sigma(d)) */
+double orc_phase_pdf_exact(const orc_fpt* p, const double d[3], const double d2[3]) {
+  double m[3] = {d2[0] - d[0], d2[1] - d[1], d2[2] - d[2]};
+  double len = sqrt(dot3(m, m));
+  if (!(len > 0.0)) return 0.0;
+  for (int i = 0; i < 3; ++i) m[i] /= len;
+  if (dot3(d, m) >= 0.0) return 0.0;
+  double sd = orc_projected_area_world(d, p);
+  return sd > 0.0 ? orc_ndf_world(m, p) / (4.0 * sd) : 0.0;
+}
+
+int orc_phase_sample_exact_point(const orc_fpt* p, const double d[3], const double u[3], double d2[3],
+                                 double w_out[3], double* pdf_out) {
+  w_out[0] = w_out[1] = w_out[2] = 0.0;
+  *pdf_out = 0.0;
+  if (!exact_supported(p)) return 0;
+  double g0[3];
+  if (p->ndf == ORC_NDF_GPSS) {
+    for (int i = 0; i < 3; ++i) g0[i] = p->g[i];
+  } else {
+    for (int i = 0; i < 3; ++i) g0[i] = p->fn[i];
+  }
+  double v[3], xi[3], e1[3], e2[3], g[3];
+  cov_sqrt_apply(p, d, v);
+  double s = sqrt(dot3(v, v));
+  if (!(s > 0.0)) return 0;
+  double e[3] = {-v[0] / s, -v[1] / s, -v[2] / s};
+  double beta = -dot3(d, g0) / s;
+  double y = visible_slope(beta, u[0]);
+  basis(e, e1, e2);
+  double z1 = ORC_SQRT2 * orc_erfinv(2.0 * u[1] - 1.0), z2 = ORC_SQRT2 * orc_erfinv(2.0 * u[2] - 1.0);
+  for (int i = 0; i < 3; ++i) xi[i] = (y - beta) * e[i] + z1 * e1[i] + z2 * e2[i];
+  cov_sqrt_apply(p, xi, g);
+  for (int i = 0; i < 3; ++i) g[i] += g0[i];
+  double gl = sqrt(dot3(g, g));
+  if (!(gl > 0.0)) return 0;
+  double m[3] = {g[0] / gl, g[1] / gl, g[2] / gl};
+  double dm = dot3(d, m);
+  if (dm >= 0.0) return 0;
+  for (int i = 0; i < 3; ++i) d2[i] = d[i] - 2.0 * dm * m[i];
+  normalize3(d2);
+  double pdf = orc_phase_pdf_exact(p, d, d2);
+  if (!(pdf > 0.0)) return 0;
+  for (int c = 0; c < 3; ++c) w_out[c] = p->F[c];
+  *pdf_out = pdf;
+  return 1;
+}
+
+int orc_phase_sample_exact(const orc_scene* s, int k, const double x[3], const double d[3], const double u[3],
+                           double d2[3], double w_out[3], double* pdf_out) {
+  orc_fpt p;
+  if (k < 0 || k >= s->n_objs || !orc_point(&s->objs[k], x, &p)) return 0;
+  return orc_phase_sample_exact_point(&p, d, u, d2, w_out, pdf_out);
+}
+
 int orc_phase_sample(const orc_scene* s, int k, const double x[3], const double d[3],
                      double R, const double u[3], double d2[3], double w_out[3],
                      double* pdf_out) {

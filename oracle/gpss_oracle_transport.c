@@ -493,6 +493,8 @@ static void trace_path(const orc_scene* s, const orc_camera* cam, const orc_rend
       wl[1] = r * sin(ph);
       wl[2] = z;
       orc_phase_eval_point(&p, d, wl, op->mix_R, pv, &pdf_ph);
+      if (op->sampler == ORC_SAMPLER_EXACT && (p.ndf == ORC_NDF_GPSS || p.ndf == ORC_NDF_BECKMANN))
+        pdf_ph = orc_phase_pdf_exact(&p, d, wl);  /* the phase sampler's pdf of w_L (MIS) */
       if (pv[0] > 0.0 || pv[1] > 0.0 || pv[2] > 0.0) {
         double Tr = orc_transmittance(s, x, wl, INFINITY);
         double Le[3], w = power_heuristic(inv4pi, pdf_ph);
@@ -514,7 +516,11 @@ static void trace_path(const orc_scene* s, const orc_camera* cam, const orc_rend
     }
     orc_uniform4(op->seed, pixel, (uint32_t)sample, (uint32_t)bounce, P_PHASE, 0, u);
     double d2[3], wgt[3], pdf;
-    if (!orc_phase_sample_point(&p, d, op->mix_R, u, d2, wgt, &pdf)) return;
+    if (op->sampler == ORC_SAMPLER_EXACT && (p.ndf == ORC_NDF_GPSS || p.ndf == ORC_NDF_BECKMANN)) {
+      if (!orc_phase_sample_exact_point(&p, d, u, d2, wgt, &pdf)) return;
+    } else if (!orc_phase_sample_point(&p, d, op->mix_R, u, d2, wgt, &pdf)) {
+      return;
+    }
     if (g) {
       /* phase-sample factor p_k(d, d2), weighted by everything collected after this vertex's NEE */
       downstream(g, L, Wc);

@@ -108,3 +108,89 @@ def test_sampler_histogram_matches_pdf(hetero):
     np.testing.assert_allclose(w[:50, 0], pe[:, 0] / pdfe, rtol=1e-9)
     F = oracle.field(hetero, 0, x)["albedo"][0]
     assert abs(w[:, 0].mean() - F) < 4 * w[:, 0].std() / math.sqrt(n)
+
+
+def _hist_chi2(scene, x, d, d2, pdf_fn, nc=8, nphi=8):
+    """chi^2 p-value of sampled half vectors (from d2) against a pdf over d2, with the
+    expected bin probabilities by 8x8 Gauss-Legendre per (cos, phi) bin about -d."""
+    n = len(d2)
+    m = d2 - d
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    fx, fy, fz = H.frame(-d)
+    c = m @ fz
+    ph = np.mod(np.arctan2(m @ fy, m @ fx), 2 * math.pi)
+    obs, _, _ = np.histogram2d(c, ph, bins=[np.linspace(0, 1, nc + 1), np.linspace(0, 2 * math.pi, nphi + 1)])
+    gx, gw = np.polynomial.legendre.leggauss(8)
+    exp_p = np.zeros((nc, nphi))
+    for i in range(nc):
+        cc = (i + 0.5 + 0.5 * gx) / nc
+        cw = 0.5 * gw / nc
+        for j in range(nphi):
+            pp = (j + 0.5 + 0.5 * gx) * 2 * math.pi / nphi
+            pw = 0.5 * gw * 2 * math.pi / nphi
+            CC, PP = np.meshgrid(cc, pp, indexing="ij")
+            WW = np.outer(cw, pw)
+            s = np.sqrt(1 - CC ** 2)
+            mm = ((s * np.cos(PP))[..., None] * fx + (s * np.sin(PP))[..., None] * fy + CC[..., None] * fz).reshape(-1, 3)
+            dd2 = np.array([_reflect(d, q) for q in mm])
+            exp_p[i, j] = np.sum(WW.reshape(-1) * pdf_fn(dd2) * 4 * np.abs(mm @ d))
+    assert exp_p.sum() == pytest.approx(1.0, rel=2e-3)
+    e = exp_p.ravel() / exp_p.sum() * n
+    o = obs.ravel()
+    small = e < 5  # bins the density (nearly) never reaches are pooled into one
+    if small.any():
+        e = np.append(e[~small], e[small].sum())
+        o = np.append(o[~small], o[small].sum())
+        if e[-1] < 1e-9:
+            assert o[-1] == 0
+            e, o = e[:-1], o[:-1]
+    return chisquare(o, e * o.sum() / e.sum())[1]
+
+
+def _exact_cases():
+    wl = W.heterogeneous(n=16, length_scale=0.05)
+    iso = wl["scene"]
+    obj = dict(iso["objects"][0])
+    aniso = {"objects": [W.with_kernel(obj, tangent=True, correlation=True)], "light": iso["light"]}
+    p = W.node_coords((-0.5, -0.5, -0.25), (0.5, 0.5, 0.25), (9, 9, 9))
+    hf = {"objects": [dict(W.make_object(p[..., 2] + 0.05 * np.sin(4 * p[..., 0]), 0.02 ** 2, 0.7, (-0.5, -0.5, -0.25),
+                                         (0.5, 0.5, 0.25), 0.05), ndf="beckmann")], "light": iso["light"]}
+    return {"gpss": iso, "anisotropic": aniso, "beckmann": hf}
+
+
+@pytest.mark.parametrize("case", ["gpss", "anisotropic", "beckmann"])
+@pytest.mark.parametrize("side", ["approaching", "leaving"])
+def test_exact_visible_normal_sampler(case, side):
+    """The oracle's exact visible-normal sampler (slope-space sampling, visible slope
+    by bisection of its closed-form CDF): the returned weight is F and the pdf is p/F
+    at the sampled direction, and a chi^2 test of the sampled half vectors against
+    p/F (the oracle's phase function, quadrature of the NDF's definition) holds, for
+    rays approaching (beta > 0) and leaving (beta < 0) the mean surface."""
+    sc = _exact_cases()[case]
+    S = oracle.Scene(sc)
+    rng = np.random.default_rng(11)
+    while True:
+        x = rng.uniform(-0.3, 0.3, 3) if case != "beckmann" else np.array([0.1, -0.05, 0.01])
+        f = oracle.field(S, 0, x)
+        if abs(f["mean"]) < 0.1:
+            break
+    nrm = f["grad"] / np.linalg.norm(f["grad"])
+    d = -0.6 * nrm + 0.8 * H.frame(nrm)[0] if side == "approaching" else 0.5 * nrm + 0.866 * H.frame(nrm)[1]
+    d /= np.linalg.norm(d)
+    if case == "beckmann" and side == "leaving":
+        d = -0.3 * nrm + 0.954 * H.frame(nrm)[1]  # height fields sample uniformly from below; stay above
+        d /= np.linalg.norm(d)
+    n = 20000
+    u = np.random.default_rng(12).random((n, 3))
+    d2, w, pdf, ok = oracle.phase_sample_exact(S, 0, np.repeat(x[None], n, 0), np.repeat(d[None], n, 0), u)
+    assert ok.mean() > 0.999
+    d2, w, pdf = d2[ok], w[ok], pdf[ok]
+    np.testing.assert_allclose(w, np.repeat(f["albedo"][None], len(w), 0), rtol=1e-12)
+    pe, _ = oracle.phase_eval(S, 0, np.repeat(x[None], 64, 0), np.repeat(d[None], 64, 0), d2[:64])
+    np.testing.assert_allclose(pdf[:64], pe[:, 0] / f["albedo"][0], rtol=1e-10)
+
+    def pdf_fn(dd2):
+        pv, _ = oracle.phase_eval(S, 0, np.repeat(x[None], len(dd2), 0), np.repeat(d[None], len(dd2), 0), dd2)
+        return pv[:, 0] / f["albedo"][0]
+
+    assert _hist_chi2(S, x, d, d2, pdf_fn) > 1e-4

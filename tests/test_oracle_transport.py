@@ -69,13 +69,16 @@ def test_single_scattering_is_exact():
     assert st["truncated"] == st["vertices"]
 
 
-def test_white_furnace():
+@pytest.mark.parametrize("sampler", ["mixture", "vndf"])
+def test_white_furnace(sampler):
     """Albedo 1 under a uniform unit environment: every pixel equals 1 when no
-    path is truncated (energy conservation of Eq. phase and the integrator)."""
+    path is truncated (energy conservation of Eq. phase and the integrator), with
+    the paper's sampling mixture and with exact visible-normal sampling."""
     S = oracle.Scene(H.dyadic_slab(albedo=1.0, mean=0.0625, light=W.uniform_light(1.0)))
     cam = W.ortho_camera_45(16, 16, film=0.5)
     spp = 2048
-    s, s2, st = oracle.render(S, cam, {"spp": spp, "max_bounces": 512, "seed": 9}, rows=(6, 10, 1), cols=(6, 10))
+    s, s2, st = oracle.render(S, cam, {"spp": spp, "max_bounces": 512, "seed": 9, "sampler": sampler},
+                              rows=(6, 10, 1), cols=(6, 10))
     assert st["truncated"] == 0
     n = 16 * spp
     m = s[6:10, 6:10, 0].sum() / n
@@ -166,3 +169,20 @@ def test_transmittance_across_the_underflow_cutoff(tau):
     else:
         assert abs(got - ref) <= 1e-320
     assert oracle.optical_depth(S, o, d, L) == pytest.approx(st * L, rel=1e-11)
+
+
+def test_exact_sampler_and_mixture_render_the_same_image():
+    """Multi-bounce heterogeneous scene: the oracle's two phase samplers are
+    estimators of the same image (pixel sums over the image agree within their
+    standard errors), and the exact sampler's per-path variance is far lower."""
+    wl = W.heterogeneous(n=16, width=8, height=8, spp=64, max_bounces=8, length_scale=0.03)
+    S = oracle.Scene(wl["scene"])
+    out = {}
+    for sampler, spp in (("mixture", 256), ("vndf", 256)):
+        s, s2, _ = oracle.render(S, wl["camera"], dict(wl["opts"], spp=spp, seed=31, sampler=sampler))
+        m = s[..., 0] / spp
+        var = np.maximum(s2[..., 0] / spp - m * m, 0)
+        out[sampler] = (m.sum(), math.sqrt(var.sum() / spp), var.sum())
+    (a, sa, va), (b, sb, vb) = out["mixture"], out["vndf"]
+    assert abs(a - b) < 4 * math.sqrt(sa * sa + sb * sb), (a, sa, b, sb)
+    assert vb < 0.5 * va
