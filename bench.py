@@ -3,14 +3,20 @@
 
 A *path vertex* is one real scattering event of a path (free flight into it,
 next-event estimation and phase sampling at it).  One benchmark step is one full
-forward render of the workload; the default workload is the heterogeneous GPSS
-(128^3 sphere-noise mean, variance ramp, 512x512, 64 spp, 32 bounces, sky light).
+forward render of the workload; the default workload is the surface-to-volume
+scene, the largest configuration (torus, box and sphere on their own 256^3 grids,
+variances 1e-6 / 2.24e-4 / 0.05, RGB albedo; 1024x1024, 256 spp, 64 bounces, sky
+light; about 1 GB of grids, more than L2).  The tiny slab and the heterogeneous
+128^3 workload are timed too, as extra keys.
 
 Output: one JSON line (rank 0).  ``value`` is the whole-job throughput with the
 scene resident in HBM; ``e2e`` is the same metric through the C-ABI with host
 buffers (grids uploaded and the image read back every step); ``roofline`` is
-the FP32-issue bound of the render kernel; ``cpu_baseline`` is the FP64 oracle
-on a bounded sample of the same workload on this machine's cores.
+the FP32-issue bound of the render kernel (algorithmic ops from the committed
+tally of the formulas, paper_2603_00280_gb300/opcounts.json); ``roofline_hbm``
+sets the algorithmic gather bytes against HBM; ``cpu_baseline`` is the FP64
+oracle on a bounded sample of the same workload on this machine's cores (and on
+one core).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -33,11 +39,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "M path-vertices/s at 1 GB300 (fwd; fwd+adjoint) and fraction of FP32-issue roofline"
 UNIT = "M path-vertices/s"
-# Algorithmic FP32 work per unit (counted from the formulas, not the code): one extinction
-# evaluation (field fetch + sigma_t) per tentative collision, plus the shading of
-# each real vertex (phase sampling + NEE phase evaluation + MIS).
-OPS_PER_SIGMA_T = 130
-OPS_PER_VERTEX_SHADING = 330
+
+
+def opcounts():
+    """Algorithmic FP32 work per unit, tallied from the formulas (not the code): one
+    extinction evaluation (field fetch + sigma_t + the tracking step) per tentative
+    collision, plus the shading of each real vertex (phase sampling + NEE phase
+    evaluation + MIS); and the field bytes one extinction evaluation gathers."""
+    from paper_2603_00280_gb300 import opcounts as oc
+    t = oc.load()
+    return t["ops_per_extinction_evaluation"], t["ops_per_vertex_shading"], t["bytes_per_extinction_evaluation"]
 
 
 def parse():
@@ -46,7 +57,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["heterogeneous", "tiny_slab"], default="heterogeneous")
+    ap.add_argument("--workload", choices=["surface_to_volume", "heterogeneous", "tiny_slab"],
+                    default="surface_to_volume")
+    ap.add_argument("--no-configs", action="store_true", help="skip the extra configurations (tiny slab, 128^3)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -64,6 +77,8 @@ def workload(name, seed_offset=0, image=0, spp=0):
     from paper_2603_00280_gb300 import workloads as W
     if name == "tiny_slab":
         wl = W.tiny_slab()
+    elif name == "surface_to_volume":
+        wl = W.surface_to_volume()
     else:
         wl = W.heterogeneous()
     wl["opts"] = dict(wl["opts"], seed=wl["opts"]["seed"] + seed_offset)
@@ -78,8 +93,11 @@ def workload(name, seed_offset=0, image=0, spp=0):
 
 def config_of(wl, l2):
     cam, opts = wl["camera"], wl["opts"]
-    obj = wl["scene"]["objects"][0]
-    return {"workload": wl["name"], "grid": list(obj["mean"].shape[::-1]), "image": [cam["width"], cam["height"]],
+    objs = wl["scene"]["objects"]
+    grids = [list(o["mean"].shape[::-1]) for o in objs]
+    nbytes = sum(o["mean"].size * 4 * (2 + (o["albedo"].shape[0] if o["albedo"].ndim == 4 else 1)) for o in objs)
+    return {"workload": wl["name"], "objects": len(objs), "grid": grids[0] if len(grids) == 1 else grids,
+            "grid_bytes": nbytes, "image": [cam["width"], cam["height"]],
             "spp": opts["spp"], "max_bounces": opts["max_bounces"], "light": wl["scene"]["light"]["type"],
             "l2": l2}
 
@@ -184,35 +202,43 @@ def measured_traffic(workload_name):
     return None
 
 
+def evaluations(st):
+    """Extinction evaluations of a render: one per tentative collision (real, null, shadow)."""
+    return st["vertices"] + st["null_collisions"] + st["shadow_steps"]
+
+
 def algorithmic_ops(st):
-    evals = st["vertices"] + st["null_collisions"] + st["shadow_steps"]
-    return OPS_PER_SIGMA_T * evals + OPS_PER_VERTEX_SHADING * st["vertices"]
+    per_eval, per_vertex, _ = opcounts()
+    return per_eval * evaluations(st) + per_vertex * st["vertices"]
 
 
 # ----------------------------------------------------------------- CPU oracle sample
 def oracle_sample(wl, target_seconds, threads=0):
-    """Renders a bounded block of pixels of the workload at its full spp and
-    bounce limit with the FP64 oracle; returns (vertices/s, description, cores)."""
+    """Renders a bounded block of pixels of the workload with the FP64 oracle (its
+    bounce limit, at most 16 samples per pixel, 4 pixels per row with one row per
+    worker thread at a time); returns (vertices/s, description, cores, seconds)."""
     import oracle
     O = oracle.Scene(wl["scene"])
     cam, opts = wl["camera"], wl["opts"]
     H, W = cam["height"], cam["width"]
     cy, cx = H // 2, W // 2
-    cols = 8
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
+    spp = min(opts["spp"], 16)
+    sopts = dict(opts, spp=spp)
     t0 = time.perf_counter()
-    _, _, st = oracle.render(O, cam, opts, rows=(cy, cy + 1, 1), cols=(cx - cols // 2, cx + cols // 2), threads=threads)
-    dt = time.perf_counter() - t0
-    per_px = dt / cols
-    n_rows = max(1, min(H // 4, int(target_seconds / max(per_px * 16, 1e-6))))
+    oracle.render(O, cam, sopts, rows=(cy, cy + 1, 1), cols=(cx, cx + 1), threads=1)
+    per_px = max(time.perf_counter() - t0, 1e-4)  # one pixel's paths on one thread
+    cols = 4
+    per_row = per_px * cols
+    n_rows = max(1, min(H // 2, int(target_seconds / per_row) * cores))
     step = max(1, (H // 2) // n_rows)
     rows = (H // 4, H // 4 + n_rows * step, step)
-    c0, c1 = cx - 8, cx + 8
+    c0, c1 = cx - cols // 2, cx + cols // 2
     t0 = time.perf_counter()
-    _, _, st = oracle.render(O, cam, opts, rows=rows, cols=(c0, c1), threads=threads)
+    _, _, st = oracle.render(O, cam, sopts, rows=rows, cols=(c0, c1), threads=threads)
     dt = time.perf_counter() - t0
-    cores = threads if threads > 0 else (os.cpu_count() or 1)
-    desc = "%d pixels (rows %d:%d:%d, cols %d:%d) x %d spp, %d paths, %d vertices, %.1f s" % (
-        n_rows * 16, rows[0], rows[1], rows[2], c0, c1, opts["spp"], st["paths"], st["vertices"], dt)
+    desc = "%d pixels (rows %d:%d:%d, cols %d:%d) x %d spp, %d paths, %d vertices, %.1f s on %d thread(s)" % (
+        n_rows * cols, rows[0], rows[1], rows[2], c0, c1, spp, st["paths"], st["vertices"], dt, cores)
     return st["vertices"] / dt / 1e6, desc, cores, dt
 
 
@@ -381,6 +407,66 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def time_renders(gpss, torch, S, cam, opts, image, flush, steps, warmup):
+    """W warm-up renders, then K timed renders, each after an L2 flush: CUDA events on
+    the launching stream around each step, and the render kernel's own event time."""
+    for _ in range(warmup):
+        gpss.render(S, cam, opts, image=image, stats=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    step_ms, kernel_ms, verts, ops, evals = [], [], 0, 0, 0
+    stats = None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, stats = gpss.render(S, cam, opts, image=image, stats=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kernel_ms.append(stats["ms"])
+        verts += stats["vertices"]
+        ops += algorithmic_ops(stats)
+        evals += evaluations(stats)
+    return {"step_ms": step_ms, "kernel_ms": kernel_ms, "verts": verts, "ops": ops, "evals": evals, "stats": stats}
+
+
+def work_of(stats, kernel_ms):
+    return {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
+            "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
+            "majorant_cells_per_step": stats["majorant_cells"], "max_path_events": stats.get("max_path_events"),
+            "kernel_ms": statistics.mean(kernel_ms)}
+
+
+def hbm_peak_gbs():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def measure_configs(args, gpss, torch, flush, rank, headline):
+    """The other single-GPU configurations, each timed like the headline (fewer steps)."""
+    out = {}
+    for name in ("heterogeneous", "tiny_slab"):
+        if name == headline:
+            continue
+        wl = workload(name, seed_offset=1000 * rank)
+        S = gpss.Scene(wl["scene"])
+        cam, opts = wl["camera"], wl["opts"]
+        image = torch.empty((cam["height"], cam["width"], 3), device="cuda")
+        t = time_renders(gpss, torch, S, cam, opts, image, flush, min(args.steps, 10), max(3, min(args.warmup, 3)))
+        peak = peak_fp32_tops(torch)[0]
+        achieved = t["ops"] / (sum(t["kernel_ms"]) / 1e3) / 1e12
+        out[wl["name"]] = {"config": config_of(wl, "flushed between steps (256 MB write)"),
+                           "value": t["verts"] / (sum(t["step_ms"]) / 1e3) / 1e6, "unit": UNIT,
+                           "ms_per_step": statistics.mean(t["step_ms"]), "steps": len(t["step_ms"]),
+                           "roofline_frac": achieved / peak, "achieved_tops": achieved,
+                           "work": work_of(t["stats"], t["kernel_ms"])}
+        S.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -400,34 +486,22 @@ def run_ours(args):
     S = gpss.Scene(wl["scene"])
     H, W = cam["height"], cam["width"]
     image = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)  # 256 MB > L2
     for _ in range(args.warmup):
         gpss.render(S, cam, opts, image=image, stats=False)
     torch.cuda.synchronize()
-    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)  # 256 MB > L2
-    stream = torch.cuda.current_stream()
     clocks = Clocks(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, kernel_ms, verts, ops = [], [], 0, 0
-    stats = None
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, stats = gpss.render(S, cam, opts, image=image, stats=True)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        kernel_ms.append(stats["ms"])
-        verts += stats["vertices"]
-        ops += algorithmic_ops(stats)
+    t = time_renders(gpss, torch, S, cam, opts, image, flush, args.steps, 0)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms, all_verts = job_totals(sum(step_ms), verts, dist, "cuda")
+    stats, kernel_ms = t["stats"], t["kernel_ms"]
+    total_ms, all_verts = job_totals(sum(t["step_ms"]), t["verts"], dist, "cuda")
     value = all_verts / (total_ms / 1e3) / 1e6
 
     # e2e through the C-ABI with host buffers: upload the grids from pinned host
@@ -444,47 +518,64 @@ def run_ours(args):
             objs.append(d)
         host_img = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
         e2e_ms, e2e_verts = [], 0
-        for i in range(args.warmup + args.steps):
+        e_warm, e_steps = min(args.warmup, 3), min(args.steps, 10)
+        for i in range(e_warm + e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             S.update(objs)
             _, _, st = gpss.render(S, cam, opts, image=host_img.numpy(), stats=True)
             t1 = time.perf_counter()
-            if i >= args.warmup:
+            if i >= e_warm:
                 e2e_ms.append(1e3 * (t1 - t0))
                 e2e_verts += st["vertices"]
         e_ms, e_verts = job_totals(sum(e2e_ms), e2e_verts, dist, "cuda")
-        e2e = {"value": e_verts / (e_ms / 1e3) / 1e6, "unit": UNIT,
+        e2e = {"value": e_verts / (e_ms / 1e3) / 1e6, "unit": UNIT, "steps": e_steps,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": H * W * 3 * 4}
+        del objs
+    S.close()
 
+    configs = None if (args.no_configs or world > 1) else measure_configs(args, gpss, torch, flush, rank, args.workload)
     adj = None if args.no_adjoint else measure_adjoint(args, gpss, torch, flush, rank)
     batched = None if (args.no_batched or world > 1) else measure_batched(args, gpss, torch, flush)
-    vndf = None if (args.no_vndf or world > 1) else measure_vndf(args, gpss, torch, flush, wl, S, image)
+    vndf = None
+    if not (args.no_vndf or world > 1):
+        wv = workload("heterogeneous", seed_offset=1000 * rank)
+        Sv = gpss.Scene(wv["scene"])
+        img_v = torch.empty((wv["camera"]["height"], wv["camera"]["width"], 3), device="cuda")
+        vndf = measure_vndf(args, gpss, torch, flush, wv, Sv, img_v)
+        Sv.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+    per_eval, per_vertex, bytes_eval = opcounts()
     peak, sms, mhz, peak_src = peak_fp32_tops(torch)
-    achieved = ops / (sum(kernel_ms) / 1e3) / 1e12
+    kernel_s = sum(kernel_ms) / 1e3
+    achieved = t["ops"] / kernel_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": measured_traffic(wl["name"]),
             "note": "FP32 issue roofline: %d SMs x 128 lanes x %.0f MHz (%s), one FMA = one op; algorithmic ops = "
-                    "%d per extinction evaluation + %d per vertex" % (sms, mhz, peak_src, OPS_PER_SIGMA_T,
-                                                                       OPS_PER_VERTEX_SHADING)}
+                    "%d per extinction evaluation + %d per vertex (paper_2603_00280_gb300/opcounts.json, tallied "
+                    "from the formulas)" % (sms, mhz, peak_src, per_eval, per_vertex)}
+    hbm, hbm_src = hbm_peak_gbs()
+    gbs = t["evals"] * bytes_eval / kernel_s / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "note": "algorithmic field gathers: %d B (8 corners x (mean, variance)) per extinction evaluation; "
+                        "peak %s" % (bytes_eval, hbm_src)}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl, "flushed between steps (256 MB write)"),
-           "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
-           "clocks": clk, "fwd_adjoint": adj, "batched": batched, "exact_vndf": vndf,
-           "work": {"vertices_per_step": stats["vertices"], "null_collisions_per_step": stats["null_collisions"],
-                    "shadow_steps_per_step": stats["shadow_steps"], "paths_per_step": stats["paths"],
-                    "majorant_cells_per_step": stats["majorant_cells"],
-                    "kernel_ms": statistics.mean(kernel_ms)}}
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config_of(wl, "inputs larger than L2 and L2 flushed between steps (256 MB write)"),
+           "roofline": roof, "roofline_hbm": roof_hbm, "e2e": e2e, "gpu_launches": args.steps,
+           "clocks": clk, "configs": configs, "fwd_adjoint": adj, "batched": batched, "exact_vndf": vndf,
+           "work": work_of(stats, kernel_ms)}
     if world == 1 and not args.no_cpu_baseline:
         v, desc, cores, _ = oracle_sample(wl, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        v1, desc1, _, _ = oracle_sample(wl, max(2.0, args.cpu_seconds / 2), threads=1)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                               "one_core": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1}}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
