@@ -286,10 +286,19 @@ def measure_adjoint(args, gpss, torch, flush, rank):
         ta.append(sa["ms"])
         mism = sa["aborted"]
     t_f, t_a = sum(tf), sum(ta)
+    S.close()
+    # inverse rendering from the perturbed start field toward the ground truth's image
+    # (Adam through the forward render and the adjoint, L2 image loss)
+    from paper_2603_00280_gb300 import optimize
+    st = W.differentiable(start=True)
+    fit = optimize.fit(st["scene"], img.clone(), cam, opts, steps=10)
     return {"workload": wl["name"], "image": [Wd, H], "spp": opts["spp"], "max_bounces": opts["max_bounces"],
             "value": verts / ((t_f + t_a) / 1e3) / 1e6, "unit": UNIT, "fwd_ms": t_f / args.steps,
             "adj_ms": t_a / args.steps, "ratio_fwd_plus_adj_over_fwd": (t_f + t_a) / t_f,
-            "replay_mismatches": mism}
+            "replay_mismatches": mism,
+            "optimisation": {"ms_per_iteration": fit["ms_per_iteration"], "iterations": 10,
+                             "loss_first": fit["losses"][0], "loss_last": fit["losses"][-1],
+                             "step": "scene update + forward render (kept path radiance) + adjoint + Adam"}}
 
 
 # ----------------------------------------------------------------- exact visible-normal sampling

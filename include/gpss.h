@@ -138,6 +138,7 @@ typedef struct {
   uint64_t paths, vertices, null_collisions, shadow_steps, majorant_cells, truncated, aborted;
   uint64_t max_path_events;  /* most tentative collisions of one path (flight + shadow) */
   float ms;                /* device time of the render kernel                      */
+  uint64_t nonfinite;      /* adjoint: gradient contributions skipped as not finite  */
 } gpss_stats;
 
 /* ---------------------------------------------------------------- scenes */
@@ -231,16 +232,22 @@ gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam, const gpss
 
 /* Path-replay adjoint (gradients of the image's expectation).  d_image: H*W*3
  * (dLoss/dimage, device).  Gradients are ACCUMULATED (+=) into d_mean, d_variance
- * (nx*ny*nz each), d_albedo (channels planes), d_length_scale (1 float: the
- * object's l_t) and d_correlation_scale (nx*ny*nz: the correlation-scale factors;
- * only for an object that has them, INVALID_ARG otherwise); any output may be
- * NULL.  Single-object scenes with the GPSS NDF and an isotropic kernel only
- * (UNSUPPORTED otherwise; the correlation-scale grid is supported).  The
- * paths are those of gpss_render with equal camera and options: if the scene
- * kept their per-path radiance (GPSS_FLAG_KEEP_PATH_RADIANCE on that render, no
- * scene update since) it is reused, else the forward paths are traced first.
+ * and d_correlation_scale (the nodes of every object, one object's grid after the
+ * other in object order), d_albedo (each object's channel planes, objects in order)
+ * and d_length_scale (one float per object: its l_t); any output may be NULL.
+ * d_correlation_scale needs some object with a correlation-scale grid (the others'
+ * parts stay untouched), INVALID_ARG otherwise.  Objects with the GPSS NDF and an
+ * isotropic kernel only (UNSUPPORTED otherwise; the correlation-scale grid is
+ * supported).  The paths are those of gpss_render with equal camera and options:
+ * if the scene kept their per-path radiance (GPSS_FLAG_KEEP_PATH_RADIANCE on that
+ * render, 12 bytes per path, no scene update since) it is reused, else the forward
+ * paths are traced first.  Nothing else is kept: each shadow ray is replayed from
+ * its random numbers, first for its final transmittance, then for its gradient.
  * stats->aborted counts replayed paths that did not reproduce their forward
- * radiance (expected 0). */
+ * radiance (expected 0); stats->nonfinite the gradient contributions skipped
+ * because their coefficients were not finite (expected ~0).  Method: path replay
+ * backpropagation (Vicini et al. 2021) of the Sec. 5 estimator on the Sec. 4
+ * medium; the partials of Eq. generalized_sigma_t, Eq. macro_ndf and Eq. phase. */
 gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss_render_opts* opts,
                                 const float* d_image, float* d_mean, float* d_variance, float* d_albedo,
                                 float* d_length_scale, float* d_correlation_scale, gpss_stats* stats,

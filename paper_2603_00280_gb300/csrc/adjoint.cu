@@ -51,17 +51,20 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   if (!s || !d_image) { set_error("null scene or d_image"); return GPSS_ERR_INVALID_ARG; }
   gpss_status st = check_opts(opts);
   if (st != GPSS_OK) return st;
-  if (s->n_objs != 1) { set_error("the adjoint supports single-object scenes"); return GPSS_ERR_UNSUPPORTED; }
-  if (s->obj[0].ndf != GPSS_NDF_GPSS) {
-    set_error("the adjoint supports the GPSS NDF only (not the height-field macrofacets)");
-    return GPSS_ERR_UNSUPPORTED;
+  bool any_cs = false;
+  for (int k = 0; k < s->n_objs; ++k) {
+    if (s->obj[k].ndf != GPSS_NDF_GPSS) {
+      set_error("the adjoint supports the GPSS NDF only (not the height-field macrofacets)");
+      return GPSS_ERR_UNSUPPORTED;
+    }
+    if (s->obj[k].anisotropic()) {
+      set_error("the adjoint supports isotropic kernels only (l_b = l_n = l_t, no tangent field)");
+      return GPSS_ERR_UNSUPPORTED;
+    }
+    any_cs = any_cs || s->obj[k].cscale;
   }
-  if (s->obj[0].anisotropic()) {
-    set_error("the adjoint supports isotropic kernels only (l_b = l_n = l_t, no tangent field)");
-    return GPSS_ERR_UNSUPPORTED;
-  }
-  if (d_correlation_scale && !s->obj[0].cscale) {
-    set_error("d_correlation_scale given for an object without a correlation-scale grid");
+  if (d_correlation_scale && !any_cs) {
+    set_error("d_correlation_scale given for a scene without a correlation-scale grid");
     return GPSS_ERR_INVALID_ARG;
   }
   CameraDev C;
@@ -75,7 +78,6 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   const int grid = render_grid_size(s->device, block);
   if (s->path_tag != fp) {
     // no kept radiance of this render: run the forward pass first (paths only)
-    const size_t nT = (size_t)total * opts->max_bounces;
     if (s->path_capacity < 3 * (size_t)total) {
       cudaFree(s->path_radiance);
       s->path_radiance = nullptr;
@@ -83,14 +85,6 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
       if ((e = cudaMalloc(&s->path_radiance, 3 * (size_t)total * sizeof(float))) != cudaSuccess)
         return cuda_fail(e, "path radiance allocation");
       s->path_capacity = 3 * (size_t)total;
-    }
-    if (s->pathT_capacity < nT) {
-      cudaFree(s->path_T);
-      s->path_T = nullptr;
-      s->pathT_capacity = 0;
-      if ((e = cudaMalloc(&s->path_T, nT * sizeof(float))) != cudaSuccess)
-        return cuda_fail(e, "path transmittance allocation");
-      s->pathT_capacity = nT;
     }
     if (s->film_capacity < 6 * npx) {
       cudaFree(s->film);
@@ -102,7 +96,7 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
     if ((e = cudaMemsetAsync(s->film, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear film");
     if ((e = cudaMemsetAsync(s->counters, 0, 16 * sizeof(unsigned long long), cs)) != cudaSuccess)
       return cuda_fail(e, "clear counters");
-    e = launch_render(scene_dev(s), C, *opts, s->film, nullptr, s->path_radiance, s->path_T, s->counters, grid, block,
+    e = launch_render(scene_dev(s), C, *opts, s->film, nullptr, s->path_radiance, s->counters, grid, block,
                       s->shade_min, cs);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     s->path_tag = fp;
@@ -128,8 +122,17 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   AdjOut A;
   A.d_image = d_image;
   A.L_path = s->path_radiance;
-  A.T_path = s->path_T;
-  const size_t nodes = s->obj[0].nodes;
+  // gradient grids of the objects one after another (object order); albedo: each
+  // object's channel planes
+  size_t nodes = 0, alb = 0;
+  for (int k = 0; k < kMaxObjects; ++k) {
+    A.node_off[k] = (long long)nodes;
+    A.alb_off[k] = (long long)alb;
+    if (k < s->n_objs) {
+      nodes += s->obj[k].nodes;
+      alb += s->obj[k].nodes * (size_t)s->obj[k].channels;
+    }
+  }
   A.d_mv = nullptr;
   if (d_mean || d_variance) {
     if (s->grad_capacity < nodes) {
@@ -158,13 +161,13 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   const int agrid = sms * (per_sm > 0 ? per_sm : 1);
   float* const nf = nullptr;
   if (local && gen)
-    k_path<true, true, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
+    k_path<true, true, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
   else if (local)
-    k_path<true, true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
+    k_path<true, true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
   else if (gen)
-    k_path<true, false, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
+    k_path<true, false, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
   else
-    k_path<true, false, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, nf, s->counters, A);
+    k_path<true, false, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   if (A.d_mv) {

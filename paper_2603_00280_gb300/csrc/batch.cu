@@ -61,43 +61,46 @@ __device__ __forceinline__ int find_job(const long long* __restrict__ begins, in
   return lo;
 }
 
-// The persistent kernel over all jobs: k_path's loop with per-lane job lookup.
-// Register cap 96 for every block size, so that 640 lanes per SM stay resident.
+// Work source of a batch: indices of the flattened job space; a lane looks its job up
+// when a new index leaves its current job's range, and a path's scene, options and
+// film are its job's.
+struct BatchSource {
+  const JobDev* __restrict__ jobs;
+  const long long* __restrict__ begins;
+  int n_jobs;
+  long long total;
+  int chunk;
+  unsigned long long* cursor;
+  AdjOut A;
+  WarpCursor wc;
+  __device__ __forceinline__ void take(Lane& s, unsigned need, int lane) {
+    const long long g = warp_take(wc, !s.active, need, lane, cursor, total, chunk);
+    if (!s.active && g >= 0 && g < total) {
+      if (g < begins[s.job] || g >= begins[s.job + 1]) s.job = find_job(begins, n_jobs, g);
+      const JobDev& J = jobs[s.job];
+      lane_start<false>(s, J.C, J.P, A, g - begins[s.job]);
+    }
+  }
+  __device__ __forceinline__ bool exhausted() const { return wc.exhausted || wc.next >= total; }
+  __device__ __forceinline__ const SceneDev& scene(const Lane& s) const { return jobs[s.job].S; }
+  __device__ __forceinline__ const PathArgs& args(const Lane& s) const { return jobs[s.job].P; }
+  __device__ __forceinline__ const AdjOut& adj() const { return A; }
+  __device__ __forceinline__ void finish(Lane& s, LaneCounters& c) {
+    const JobDev& J = jobs[s.job];
+    lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
+  }
+};
+
+// The persistent kernel over all jobs: k_path's loop over the batch's work source.  Register cap 96 for every block size, so that 640 lanes per
+// SM stay resident.
 template <int BLOCK, bool LOCAL, bool GEN>
 __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const long long* __restrict__ begins,
                                         int n_jobs, long long total, int chunk, int shade_min,
                                         unsigned long long* __restrict__ counters) {
-  const unsigned FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
-  WarpCursor wc{0, 0, false};
-  Lane s;
-  lane_init(s);
-  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, 0.0f};
-  const AdjOut A{};
-  for (;;) {
-    const unsigned need = __ballot_sync(FULL, !s.active);
-    if (need && !wc.exhausted) {
-      const long long g = warp_take(wc, !s.active, need, lane, counters + kCntNum, total, chunk);
-      if (!s.active && g >= 0 && g < total) {
-        if (g < begins[s.job] || g >= begins[s.job + 1]) s.job = find_job(begins, n_jobs, g);
-        const JobDev& J = jobs[s.job];
-        lane_start<false>(s, J.C, J.P, A, g - begins[s.job]);
-      }
-    }
-    const unsigned act = __ballot_sync(FULL, s.active);
-    if (act == 0) {
-      if (wc.exhausted || wc.next >= total) break;
-      continue;
-    }
-    const JobDev& J = jobs[s.job];
-    const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
-    if (wait_mask && (__popc(wait_mask) >= shade_min || wait_mask == act)) {
-      if (s.waiting) lane_shade<false, GEN>(s, J.S, J.P, A, nullptr, c);
-    }
-    if (!s.active || s.waiting) continue;
-    if (lane_step<false, LOCAL, GEN>(s, J.S, J.P, A, nullptr, c)) lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
-  }
-  flush_counters(c, counters, nullptr);
+  BatchSource src{jobs, begins, n_jobs, total, chunk, counters + kCntNum, AdjOut{}, WarpCursor{0, 0, false}};
+  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, {0.0f, 0.0f, 0.0f, 0.0f}, 0};
+  path_loop<false, LOCAL, GEN>(src, shade_min, c);
+  flush_counters(c, counters, nullptr, 0);
 }
 
 // Zeroes every job's film (and sqsum film when present); blockIdx.y = job.

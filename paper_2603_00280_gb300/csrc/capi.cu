@@ -28,6 +28,7 @@ void fill_stats(gpss_stats* st, const unsigned long long* c, float ms) {
   st->aborted = c[kCntAborted];
   st->max_path_events = c[kCntMaxEvents];
   st->ms = ms;
+  st->nonfinite = c[kCntNonFinite];
 }
 
 gpss_status cuda_fail(cudaError_t e, const char* what) {
@@ -187,7 +188,6 @@ static void free_scene(gpss_scene s) {
   cudaFree(s->grad_mv);
   cudaFree(s->film);
   cudaFree(s->path_radiance);
-  cudaFree(s->path_T);
   delete s;
 }
 
@@ -423,15 +423,10 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
     if (host_sq) dsq = s->film + 3 * npx;
   }
   float* path_rad = nullptr;
-  float* path_T = nullptr;
   if (opts->flags & GPSS_FLAG_KEEP_PATH_RADIANCE) {
     if ((st = ensure(&s->path_radiance, &s->path_capacity, 3 * (size_t)total, "path radiance allocation")) != GPSS_OK)
       return st;
-    if ((st = ensure(&s->path_T, &s->pathT_capacity, (size_t)total * opts->max_bounces, "path transmittance allocation")) !=
-        GPSS_OK)
-      return st;
     path_rad = s->path_radiance;
-    path_T = s->path_T;
   }
   if ((e = cudaMemsetAsync(dimg, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear image");
   if (dsq && (e = cudaMemsetAsync(dsq, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear sqsum");
@@ -445,7 +440,7 @@ extern "C" gpss_status gpss_render(gpss_scene s, const gpss_camera* cam, const g
   }
   const int block = render_block_size();
   const int grid = render_grid_size(s->device, block);
-  e = launch_render(scene_dev(s), C, *opts, dimg, dsq, path_rad, path_T, s->counters, grid, block, s->shade_min, cs);
+  e = launch_render(scene_dev(s), C, *opts, dimg, dsq, path_rad, s->counters, grid, block, s->shade_min, cs);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   if (stats) cudaEventRecord(ev1, cs);
   if (host_img && (e = cudaMemcpyAsync(image, dimg, 3 * npx * sizeof(float), cudaMemcpyDeviceToHost, cs)) != cudaSuccess)

@@ -254,7 +254,8 @@ __global__ void k_estimate_tr(const SceneDev S, int n, const float* org, const f
     Walk w;
     float T = 1.0f;
     if (walk_begin(S.mg, o, d, tmax[i], w)) {
-      while (walk_advance(S.mg, S.obj[0], o, d, w, -__logf(rng.next()), cells)) {
+      for (float tau = -__logf(rng.next()); walk_advance(S.mg, S.obj[0], o, d, w, tau, cells) == kWalkHit;
+           tau = -__logf(rng.next())) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
         if (!ratio_step(T, st, w.sbar, rng)) break;
@@ -279,7 +280,8 @@ __global__ void k_free_flight(const SceneDev S, int n, const float* org, const f
     Walk w;
     float t_hit = INFINITY;
     if (walk_begin(S.mg, o, d, INFINITY, w)) {
-      while (walk_advance(S.mg, S.obj[0], o, d, w, -__logf(rng.next()), cells)) {
+      for (float tau = -__logf(rng.next()); walk_advance(S.mg, S.obj[0], o, d, w, tau, cells) == kWalkHit;
+           tau = -__logf(rng.next())) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
         if (rng.next() * w.sbar < st) {

@@ -1343,9 +1343,13 @@ __device__ __forceinline__ float slab_exit(float lo, float hi, float o, float in
 
 // LOCAL = false compiles the local-majorant branch out (scenes without thin
 // objects: no register cost for it in the render kernels); GEN as for local_majorant.
+// Returns kWalkHit (w.t and w.sbar at the tentative collision) or kWalkExit (the ray
+// left the grid); tau is consumed.
+enum WalkResult : int { kWalkExit = 0, kWalkHit = 1 };
+
 template <bool LOCAL = true, bool GEN = true>
-__device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectDev& lob, V3 o, V3 d, Walk& w, float tau,
-                                             uint32_t& steps) {
+__device__ __forceinline__ int walk_advance(const MajorantDev& g, const ObjectDev& lob, V3 o, V3 d, Walk& w, float& tau,
+                                            uint32_t& steps) {
   // Each step moves the cell index strictly past the face the ray left by (or, in
   // a local piece, t strictly forward); the cap only guards against non-finite
   // input (the ray then counts as leaving).
@@ -1367,7 +1371,7 @@ __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectD
         if (r.w < 1.5f) {
           w.t = r.x;
           w.sbar = r.y;
-          return true;
+          return kWalkHit;
         }
         tau = r.z;
         w.t = fmaxf(w.t, r.x);
@@ -1381,38 +1385,38 @@ __device__ __forceinline__ bool walk_advance(const MajorantDev& g, const ObjectD
       if (tau < need) {
         w.t += tau / sk.x;
         w.sbar = sk.x;
-        return true;
+        return kWalkHit;
       }
       tau -= fmaxf(need, 0.0f);
       w.t = fmaxf(w.t, seg_end);
     }
-    if (seg_end >= w.t_end) return false;
+    if (seg_end >= w.t_end) return kWalkExit;
     // step to the cell beyond the exit face; after a cube jump the other axes are
     // re-derived from the exit point (rounding there only yields empty segments)
     if (ex <= ey && ex <= ez) {
       w.cx = d.x > 0.0f ? hx + 1 : lx - 1;
-      if ((unsigned)w.cx >= (unsigned)g.dims[0]) return false;
+      if ((unsigned)w.cx >= (unsigned)g.dims[0]) return kWalkExit;
       if (r > 0) {
         w.cy = cell_index(fmaf(w.t, d.y, o.y), g.gmin[1], g.inv_cell[1], g.dims[1]);
         w.cz = cell_index(fmaf(w.t, d.z, o.z), g.gmin[2], g.inv_cell[2], g.dims[2]);
       }
     } else if (ey <= ez) {
       w.cy = d.y > 0.0f ? hy + 1 : ly - 1;
-      if ((unsigned)w.cy >= (unsigned)g.dims[1]) return false;
+      if ((unsigned)w.cy >= (unsigned)g.dims[1]) return kWalkExit;
       if (r > 0) {
         w.cx = cell_index(fmaf(w.t, d.x, o.x), g.gmin[0], g.inv_cell[0], g.dims[0]);
         w.cz = cell_index(fmaf(w.t, d.z, o.z), g.gmin[2], g.inv_cell[2], g.dims[2]);
       }
     } else {
       w.cz = d.z > 0.0f ? hz + 1 : lz - 1;
-      if ((unsigned)w.cz >= (unsigned)g.dims[2]) return false;
+      if ((unsigned)w.cz >= (unsigned)g.dims[2]) return kWalkExit;
       if (r > 0) {
         w.cx = cell_index(fmaf(w.t, d.x, o.x), g.gmin[0], g.inv_cell[0], g.dims[0]);
         w.cy = cell_index(fmaf(w.t, d.y, o.y), g.gmin[1], g.inv_cell[1], g.dims[1]);
       }
     }
   }
-  return false;
+  return kWalkExit;
 }
 
 // One ratio-tracking step (NEE transmittance): T *= 1 - sigma_t/majorant.  Below

@@ -21,6 +21,7 @@ enum Counter : int {
   kCntTruncated,
   kCntAborted,
   kCntMaxEvents,   // max over paths (atomicMax)
+  kCntNonFinite,   // adjoint: gradient contributions skipped as not finite
   kCntNum
 };
 static_assert(kCntNum + 1 <= 16, "counters + cursor must fit the 16-word counter area");
@@ -72,8 +73,6 @@ struct gpss_scene_s {
   size_t film_capacity = 0;
   float* path_radiance = nullptr;  // per-path radiance kept for the adjoint (optional)
   size_t path_capacity = 0;
-  float* path_T = nullptr;         // per-vertex final shadow transmittance kept for the adjoint
-  size_t pathT_capacity = 0;
   uint64_t path_tag = 0;           // fingerprint of the render that filled path_radiance
   float2* grad_mv = nullptr;       // adjoint: interleaved (d mean, d variance) accumulation
   size_t grad_capacity = 0;
@@ -102,7 +101,7 @@ bool camera_dev(const gpss_camera* c, CameraDev* out);
 // kernels (launch wrappers)
 uint64_t path_fingerprint(const gpss_camera* cam, const gpss_render_opts* o, uint64_t scene_version);
 cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
-                          float* sqsum, float* path_radiance, float* path_T, unsigned long long* counters, int grid,
+                          float* sqsum, float* path_radiance, unsigned long long* counters, int grid,
                           int block, int shade_min, cudaStream_t st);
 int render_block_size();
 int render_grid_size(int device, int block);

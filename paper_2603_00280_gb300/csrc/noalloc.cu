@@ -93,7 +93,7 @@ extern "C" gpss_status gpss_render_noalloc(gpss_scene s, const gpss_camera* cam,
   if ((e = cudaMemsetAsync(film, 0, 3 * npx * sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "clear film");
   const int block = render_block_size();
   const int grid = render_grid_size(s->device, block);
-  e = launch_render(scene_dev(s), C, *opts, film, nullptr, nullptr, nullptr, counters, grid, block, s->shade_min, cs);
+  e = launch_render(scene_dev(s), C, *opts, film, nullptr, nullptr, counters, grid, block, s->shade_min, cs);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   if ((e = cudaMemcpyAsync(image, film, 3 * npx * sizeof(float), cudaMemcpyDefault, cs)) != cudaSuccess)
     return cuda_fail(e, "image copy");

@@ -23,30 +23,36 @@
 // ray (free-flight or shadow ray), so the lanes of a warp run the same traversal +
 // extinction code together.  Lanes that reach a real vertex wait; the warp serves
 // its waiting lanes together once at least `shade_min` of them wait or no lane can
-// step, so the long shading code runs with many lanes active.  Shading code and the Philox block are out of
-// line, keeping the traversal loop small in the instruction cache.  A finished
-// lane takes the next (sample, pixel) index from a warp-private chunk of the
-// global work cursor (one atomic per chunk; ranks from __ballot_sync/__popc).  Path
-// state lives in registers.  Path index = sample * npix + pixel.
+// step, so the long shading code runs with many lanes active.  (A warp-private
+// pool that parked waiting paths in shared memory and handed their lanes other
+// paths was measured slower: its state swap runs every iteration on the few lanes
+// that just reached a vertex.)  Shading code and the Philox block are out of line,
+// keeping the traversal loop small in the instruction cache.  A finished lane takes
+// the next (sample, pixel) index from a warp-private chunk of the global work cursor
+// (one atomic per chunk; ranks from __ballot_sync/__popc).  Path state lives in
+// registers.  Path index = sample * npix + pixel.
 //
 // Adjoint (path replay backpropagation, Vicini et al. 2021; null-collision terms of
 // differential delta/ratio tracking, Nimier-David et al. 2022): with the majorant,
 // sampling and light pdfs, MIS weights and roulette probabilities held fixed, every
 // factor of the estimator contributes d(log factor) times the radiance the path
 // collects downstream of it.  The path radiance L is read from the forward render
-// (kept per path, with each vertex's final shadow transmittance), so downstream
-// radiance is L - L_so_far at every event:
+// (12 bytes kept per path), so downstream radiance is L - L_so_far at every event:
 //   - tentative collision of a flight: weight <g, L - L_so_far> times
-//     d sigma_t / sigma_t (real) or -d sigma_t/(majorant - sigma_t) (null);
-//   - shadow ray: each tentative collision scatters -d sigma_t/(majorant - sigma_t)
-//     with weight <g, pend> T, pend = the vertex's NEE contribution before T and T
-//     the ray's final transmittance, recorded per vertex by the forward render;
+//     d sigma_t,k / sigma_t,k (real, k the scattering object; with several objects
+//     taken when the vertex is shaded and k chosen) or -d sigma_t/(majorant - sigma_t)
+//     (null; every object's partials to its own nodes);
+//   - shadow ray: replayed twice from its random numbers -- first for its final
+//     transmittance T (nothing is stored by the forward render), then, when the
+//     vertex's NEE contribution carries gradient, with each tentative collision
+//     scattering -d sigma_t/(majorant - sigma_t) with weight <g, pend> T, pend = the
+//     vertex's NEE contribution before T;
 //   - vertex: d ln(F D(m_L)/sigma(d)) with weight <g, C_k> (C_k = pend T) and
 //     d ln(F D(m)/sigma(d)) of the sampled direction with weight <g, radiance after
-//     the vertex's NEE>, both known when the vertex is shaded (T is the forward's),
-//     so the vertex gradient is taken in the shading step;
+//     the vertex's NEE>, taken once the shadow ray's first pass gives T;
 // where g = dLoss/dpixel / spp.  Each evaluation scatters to the 8 grid nodes it
-// interpolates (float atomics); the length-scale gradient is reduced per warp.
+// interpolates (float atomics); the length-scale gradient is reduced per warp and
+// object.
 #pragma once
 
 #include "adjoint_math.cuh"
@@ -72,14 +78,23 @@ struct PathArgs {
 struct AdjOut {
   const float* d_image;   // dLoss/dimage (H*W*3)
   const float* L_path;    // per-path radiance of the forward render (3 per path)
-  const float* T_path;    // per-vertex final shadow transmittance (max_bounces per path)
   float2* d_mv;           // interleaved (d mean, d variance) accumulation buffer, or null
   float* d_alb;
-  float* d_l;
+  float* d_l;             // one per object
   float* d_cs;            // d correlation-scale factor per node, or null
+  long long node_off[kMaxObjects];  // object k's first node in d_mv and d_cs (objects in order)
+  long long alb_off[kMaxObjects];   // object k's first albedo value in d_alb (channels x nodes each)
 };
 
-enum Mode : int { kFlight = 0, kShadow = 1 };
+// Per-lane work counters, reduced per warp at the end of the kernel.
+struct LaneCounters {
+  uint32_t paths, vert, null_, shadow, cells, trunc, abort;
+  uint32_t max_events;  // most tentative collisions of one path
+  float acc_l[kMaxObjects];  // adjoint: length-scale gradient per object
+  uint32_t nonfinite;   // adjoint: contributions skipped as not finite
+};
+
+enum Mode : int { kFlight = 0, kShadow = 1, kShadowPre = 2 };  // kShadowPre: adjoint only
 
 // Whether a scene needs the general kernel instances: some object is a height-field
 // macrofacet or has an anisotropic or non-stationary kernel.
@@ -148,26 +163,60 @@ static __device__ __noinline__ int choose_object(const SceneDev& S, V3 x, V3 d, 
   return last;
 }
 
-// Adjoint: scatter the derivative of the extinction (partials ds) at x with weight k.
-// The correlation-scale factor s enters through l(x) = s(x) l: d/ds(x) = (d/dl) l/s(x).
-// (GEN = false: the object has no correlation-scale grid.)
+// Adjoint: scatter the derivative of object k's extinction (partials ds) at x with
+// weight w.  The correlation-scale factor s enters through l(x) = s(x) l: d/ds(x) =
+// (d/dl) l/s(x).  (GEN = false: the object has no correlation-scale grid.)  Returns the
+// length-scale part.
 template <bool GEN>
-__device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, V3 x, const DSig& ds, float k, float cs,
-                                                   const AdjOut& A) {
-  if (!isfinite(k) || k == 0.0f) return 0.0f;
-  if (A.d_mv) scatter_field(ob, x, k * ds.dmu, k * ds.dg, k * ds.dvar, A.d_mv);
-  if constexpr (GEN) {
-    if (A.d_cs) scatter_scalar(ob, x, k * ds.dl * (kSqrt2 / ob.alpha_scale) / cs, A.d_cs);
+__device__ __forceinline__ float adj_scatter_event(const ObjectDev& ob, int k, V3 x, const DSig& ds, float w, float cs,
+                                                   const AdjOut& A, uint32_t& nonfinite) {
+  if (w == 0.0f) return 0.0f;
+  const float cmu = w * ds.dmu, cvar = w * ds.dvar, cl = w * ds.dl;
+  const V3 cg = w * ds.dg;
+  // a contribution that is not finite (an extinction evaluated at the edge of FP32
+  // range) is skipped and counted, so that it cannot poison the gradient grids
+  if (!isfinite(cmu + cvar + cl + cg.x + cg.y + cg.z)) {
+    ++nonfinite;
+    return 0.0f;
   }
-  return k * ds.dl;
+  if (A.d_mv) scatter_field(ob, x, cmu, cg, cvar, A.d_mv + A.node_off[k]);
+  if constexpr (GEN) {
+    if (A.d_cs && ob.cscale) scatter_scalar(ob, x, cl * (kSqrt2 / ob.alpha_scale) / cs, A.d_cs + A.node_off[k]);
+  }
+  return cl;
 }
 
-// Adjoint: gradient of the vertex factors at x (incoming direction d_in): the NEE
-// factor F D(m_nee)/sigma(d_in) with weight Wnee and the sampled direction's factor
-// F D(m_ph)/sigma(d_in) with weight Wph (the sigma(d_in) part is shared).
+// The partials of ln sigma_t (a real collision's factor): each divided by sigma_t before
+// any weight multiplies it, so a tiny sigma_t cannot overflow the weight.
+__device__ __forceinline__ DSig dlog_of(const DSig& ds) {
+  const float inv = 1.0f / ds.st;
+  DSig r = ds;
+  r.dmu *= inv;
+  r.dvar *= inv;
+  r.dl *= inv;
+  r.dg = inv * ds.dg;
+  return r;
+}
+
+// Adjoint: w d sigma_t of every object at x (the total extinction's derivative, each
+// object's partials scattered to its own nodes); the length-scale parts per object.
 template <bool GEN>
-__device__ __forceinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, V3 wl, V3 d_next, float Wnee,
-                                                float Wph, V3 albedo_coef, const AdjOut A) {
+__device__ __forceinline__ void adj_scatter_all(const SceneDev& S, V3 x, V3 d, float w, const AdjOut& A,
+                                                LaneCounters& c) {
+  for (int k = 0; k < S.n_objs; ++k) {
+    if (!inside(S.obj[k], x)) continue;
+    const Field f = fetch_k<GEN>(S.obj[k], x);
+    const DSig ds = dsigma_t(S.obj[k], f, d);
+    c.acc_l[k] += adj_scatter_event<GEN>(S.obj[k], k, x, ds, w, f.cs, A, c.nonfinite);
+  }
+}
+
+// Adjoint: gradient of the vertex factors of object k at x (incoming direction d_in):
+// the NEE factor F D(m_nee)/sigma(d_in) with weight Wnee and the sampled direction's
+// factor F D(m)/sigma(d_in) with weight Wph (the sigma(d_in) part is shared).
+template <bool GEN>
+__device__ __forceinline__ float adj_vertex(const ObjectDev& ob, int k, V3 x, V3 d_in, V3 wl, V3 d_next, float Wnee,
+                                            float Wph, V3 albedo_coef, const AdjOut& A, uint32_t& nonfinite) {
   const Field f = fetch_k<GEN>(ob, x);
   const float sig = sqrtf(f.var);
   const float alpha = sig * f.as;
@@ -194,13 +243,18 @@ __device__ __forceinline__ float adj_vertex(const ObjectDev& ob, V3 x, V3 d_in, 
     dalpha = fmaf(-W, ea_over * inv_a, dalpha);
   }
   const float cvar = dalpha * alpha / (2.0f * f.var);
-  if (A.d_mv && (Wnee != 0.0f || Wph != 0.0f)) scatter_field(ob, x, 0.0f, cg, cvar, A.d_mv);
-  if (A.d_alb && (albedo_coef.x != 0.0f || albedo_coef.y != 0.0f || albedo_coef.z != 0.0f))
-    scatter_albedo(ob, x, albedo_coef, A.d_alb);
   // d/dl through alpha = sqrt2 sigma/(s(x) l); d/ds(x) = (d/dl) l/s(x)
   const float dl = -dalpha * alpha * (ob.alpha_scale * kInvSqrt2);
+  if (!isfinite(cg.x + cg.y + cg.z + cvar + dl + albedo_coef.x + albedo_coef.y + albedo_coef.z)) {
+    ++nonfinite;  // skipped and counted (see adj_scatter_event)
+    return 0.0f;
+  }
+  if (A.d_mv && (Wnee != 0.0f || Wph != 0.0f)) scatter_field(ob, x, 0.0f, cg, cvar, A.d_mv + A.node_off[k]);
+  if (A.d_alb && (albedo_coef.x != 0.0f || albedo_coef.y != 0.0f || albedo_coef.z != 0.0f))
+    scatter_albedo(ob, x, albedo_coef, A.d_alb + A.alb_off[k]);
   if constexpr (GEN) {
-    if (A.d_cs && dl != 0.0f) scatter_scalar(ob, x, dl * (kSqrt2 / ob.alpha_scale) / f.cs, A.d_cs);
+    if (A.d_cs && ob.cscale && dl != 0.0f)
+      scatter_scalar(ob, x, dl * (kSqrt2 / ob.alpha_scale) / f.cs, A.d_cs + A.node_off[k]);
   }
   return dl;
 }
@@ -217,15 +271,12 @@ struct Lane {
   int bounce, mode;
   uint32_t events;
   Walk w;
-  // adjoint state
+  // adjoint state: the path's forward radiance, dLoss/dpixel / spp, the current
+  // vertex's final shadow transmittance, its arriving direction and scattering object
   V3 Ltot, gpix;
   float Tfin;
-};
-
-struct LaneCounters {
-  uint32_t paths, vert, null_, shadow, cells, trunc, abort;
-  uint32_t max_events;  // most tentative collisions of one path
-  float acc_l;  // adjoint: length-scale gradient
+  V3 d_in;
+  int kobj;
 };
 
 __device__ __forceinline__ void lane_init(Lane& s) {
@@ -266,10 +317,41 @@ __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const Pa
   return true;
 }
 
+// Adjoint: the vertex's gradient once its NEE contribution C = pend T_fin is known (T_fin
+// = the shadow ray's final transmittance, recomputed by the replay), and C added to the
+// radiance so far.  wl: the NEE direction.
+template <bool GEN>
+__device__ __forceinline__ void adj_vertex_done(Lane& s, const SceneDev& S, const AdjOut& A, V3 wl, float Tfin,
+                                                LaneCounters& c) {
+  const V3 x = s.o;
+  const V3 F = fetch_albedo(S.obj[s.kobj], x);
+  const V3 Ck = v3(s.pend.x * Tfin, s.pend.y * Tfin, s.pend.z * Tfin);
+  const V3 after = s.Ltot - s.L - Ck;
+  const float Wnee = dot(s.gpix, Ck);
+  const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
+  const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
+                   F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
+                   F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
+  c.acc_l[s.kobj] += adj_vertex<GEN>(S.obj[s.kobj], s.kobj, x, s.d_in, wl, s.d_next, Wnee, Wph, ac, A, c.nonfinite);
+  s.L = s.L + Ck;
+}
+
+// After the shadow ray (or in place of it): the next flight, or the end of the path.
+__device__ __forceinline__ bool lane_continue(Lane& s) {
+  if (!s.cont) return true;
+  s.mode = kFlight;
+  s.d = s.d_next;
+  s.beta = s.beta_next;
+  s.prev_pdf = s.pdf_next;
+  s.rng.start((uint32_t)s.bounce, kPurposeFlight);
+  s.begin = true;
+  return false;
+}
+
 // Shading of a real vertex: phase sampling, next-event estimation setup.
 template <bool ADJ, bool GEN>
 __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
-                                           float* __restrict__ path_T, LaneCounters& c) {
+                                           LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
   s.waiting = false;
   const V3 x = fma3(s.w.t, s.d, s.o);
@@ -277,6 +359,19 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   const Field f = fetch_k<GEN>(S.obj[k], x);
   const float alpha = sqrtf(f.var) * f.as;  // the density rho is not needed for shading
   const V3 F = fetch_albedo(S.obj[k], x);
+  if constexpr (ADJ) {
+    // several objects: the real collision's factor is the chosen object's sigma_t,k (the
+    // choice probability sigma_t,k/sigma_t is held fixed), known only now
+    if (S.n_objs > 1) {
+      const float W = dot(s.gpix, s.Ltot - s.L);
+      if (W != 0.0f) {
+        const DSig ds = dsigma_t(S.obj[k], f, s.d);
+        if (ds.st > 0.0f) c.acc_l[k] += adj_scatter_event<GEN>(S.obj[k], k, x, dlog_of(ds), W, f.cs, A, c.nonfinite);
+      }
+    }
+    s.d_in = s.d;
+    s.kobj = k;
+  }
   s.o = x;
   s.cont = s.bounce + 1 < P.max_bounces;
   float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
@@ -316,35 +411,18 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   const float lw = env ? power_heuristic(kInv4Pi, pe.pdf) * (4.0f * kPi) : 1.0f;
   const float scale = pe.p_over_F * lw;
   s.pend = v3(s.beta.x * F.x * scale * Le.x, s.beta.y * F.y * scale * Le.y, s.beta.z * F.z * scale * Le.z);
-  if constexpr (ADJ) {
-    // the vertex's gradient, now: its NEE contribution C = pend T (T = the forward's
-    // final shadow transmittance) and the radiance after it are already known
-    s.Tfin = scale > 0.0f ? A.T_path[(size_t)s.pidx * P.max_bounces + s.bounce] : 0.0f;
-    const V3 Ck = v3(s.pend.x * s.Tfin, s.pend.y * s.Tfin, s.pend.z * s.Tfin);
-    const V3 after = s.Ltot - s.L - Ck;
-    const float Wnee = dot(s.gpix, Ck);
-    const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
-    const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
-                     F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
-                     F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
-    c.acc_l += adj_vertex<GEN>(S.obj[0], x, s.d, wl, s.d_next, Wnee, Wph, ac, A);
-    s.L = s.L + Ck;
-  } else {
-    if (path_T && !(scale > 0.0f)) path_T[(size_t)s.pidx * P.max_bounces + s.bounce] = 0.0f;
-  }
   ++s.bounce;
   if (scale > 0.0f) {
-    s.mode = kShadow;
+    // the shadow ray; the adjoint first replays it for its final transmittance (pre-pass)
+    s.mode = ADJ ? kShadowPre : kShadow;
     s.d = wl;
     s.T = 1.0f;
     s.begin = true;
-  } else if (s.cont) {
-    s.mode = kFlight;
-    s.d = s.d_next;
-    s.beta = s.beta_next;
-    s.prev_pdf = s.pdf_next;
-    s.rng.start((uint32_t)s.bounce, kPurposeFlight);
-    s.begin = true;
+    return;
+  }
+  if constexpr (ADJ) adj_vertex_done<GEN>(s, S, A, wl, 0.0f, c);  // no NEE contribution
+  if (s.cont) {
+    lane_continue(s);
   } else {
     // no shadow ray and no continuation: with walk_ok = false and beta = 0 the
     // step treats the lane as an escaped flight that adds nothing
@@ -356,93 +434,125 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
 }
 
 // One tentative collision of the lane's current ray; returns true when the path ends.
+// Adjoint shadow rays run twice from the same random numbers: a pre-pass (kShadowPre)
+// that only computes the ray's final transmittance T_fin, then -- when the vertex's
+// NEE contribution pend T_fin carries gradient -- the gradient pass (kShadow) whose
+// tentative collisions scatter -d sigma_t/(majorant - sigma_t) with weight <g, pend> T_fin.
 template <bool ADJ, bool LOCAL, bool GEN>
 __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
-                                          float* __restrict__ path_T, LaneCounters& c) {
+                                          LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
   if (s.begin) {
     s.walk_ok = walk_begin(S.mg, s.o, s.d, INFINITY, s.w);
     s.begin = false;
   }
   bool hit = false;
-  if (s.walk_ok) hit = walk_advance<LOCAL, GEN>(S.mg, S.obj[0], s.o, s.d, s.w, -__logf(s.rng.next()), c.cells);
-  bool finish = false;
+  if (s.walk_ok) {
+    float tau = -__logf(s.rng.next());
+    hit = walk_advance<LOCAL, GEN>(S.mg, S.obj[0], s.o, s.d, s.w, tau, c.cells) == kWalkHit;
+  }
   if (hit) {
     ++s.events;
     const V3 x = fma3(s.w.t, s.d, s.o);
-    float st;
-    DSig ds;
-    float cs = 1.0f;
-    bool inobj = false;
-    if constexpr (ADJ) {
+    if (ADJ && s.mode == kShadowPre) {
+      ++c.shadow;
+      if (!ratio_step(s.T, sigma_t_at<GEN>(S, x, s.d), s.w.sbar, s.rng)) s.walk_ok = false;
+    } else if (ADJ && S.n_objs == 1) {
       // extinction and its partials from one evaluation (the decision uses the same value)
-      inobj = inside(S.obj[0], x);
-      st = 0.0f;
+      float st = 0.0f, cs = 1.0f, k_adj = 0.0f;
+      bool real = false;
+      DSig ds;
+      const bool inobj = inside(S.obj[0], x);
       if (inobj) {
         const Field f = fetch_k<GEN>(S.obj[0], x);
         ds = dsigma_t(S.obj[0], f, s.d);
         st = ds.st;
         cs = f.cs;
       }
-    } else {
-      st = sigma_t_at<GEN>(S, x, s.d);
-    }
-    float k_adj = 0.0f;  // adjoint: weight of this collision's extinction derivative
-    if (s.mode == kFlight) {
-      const bool real = s.rng.next() * s.w.sbar < st;
-      if constexpr (ADJ) {
+      if (s.mode == kFlight) {
+        real = s.rng.next() * s.w.sbar < st;
         const float W = dot(s.gpix, s.Ltot - s.L);
-        if (W != 0.0f) k_adj = real ? W / st : -W / (s.w.sbar - st);
-      }
-      if (real) {
-        ++c.vert;
-        s.waiting = true;  // real scattering vertex: shaded with the warp's other waiting lanes
+        if (W != 0.0f) k_adj = real ? W : -W / (s.w.sbar - st);  // real: times d ln sigma_t
+        if (real) {
+          ++c.vert;
+          s.waiting = true;
+        } else {
+          ++c.null_;
+        }
       } else {
-        ++c.null_;
-      }
-    } else {
-      ++c.shadow;
-      if constexpr (ADJ) {
+        ++c.shadow;
         const float Wn = dot(s.gpix, s.pend) * s.Tfin;
         if (Wn != 0.0f) k_adj = -Wn / (s.w.sbar - st);
+        if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;
       }
-      if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;  // T = 0: the shadow ray ends here
-    }
-    if constexpr (ADJ) {
-      if (inobj && k_adj != 0.0f) c.acc_l += adj_scatter_event<GEN>(S.obj[0], x, ds, k_adj, cs, A);
+      if (inobj && k_adj != 0.0f)
+        c.acc_l[0] += adj_scatter_event<GEN>(S.obj[0], 0, x, real ? dlog_of(ds) : ds, k_adj, cs, A, c.nonfinite);
+    } else {
+      const float st = sigma_t_at<GEN>(S, x, s.d);
+      float k_adj = 0.0f;  // adjoint (several objects): weight of every object's d sigma_t here
+      if (s.mode == kFlight) {
+        const bool real = s.rng.next() * s.w.sbar < st;
+        if constexpr (ADJ) {
+          // a real collision's gradient waits for the object choice at shading
+          const float W = dot(s.gpix, s.Ltot - s.L);
+          if (!real && W != 0.0f) k_adj = -W / (s.w.sbar - st);
+        }
+        if (real) {
+          ++c.vert;
+          s.waiting = true;  // real scattering vertex: parked and shaded with the warp's pool
+        } else {
+          ++c.null_;
+        }
+      } else {
+        ++c.shadow;
+        if constexpr (ADJ) {
+          const float Wn = dot(s.gpix, s.pend) * s.Tfin;
+          if (Wn != 0.0f) k_adj = -Wn / (s.w.sbar - st);
+        }
+        if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;  // T = 0: the shadow ray ends here
+      }
+      if constexpr (ADJ) {
+        if (k_adj != 0.0f) adj_scatter_all<GEN>(S, x, s.d, k_adj, A, c);
+      }
     }
     if (s.events >= kMaxEventsPerPath) {
       ++c.abort;
-      finish = true;
       s.waiting = false;
+      return true;
+    }
+    return false;
+  }
+  if (s.mode == kFlight) {
+    if (env) {
+      const V3 Le = env_radiance(S.light, s.d);
+      const float wm = s.prev_pdf < 0.0f ? 1.0f : power_heuristic(s.prev_pdf, kInv4Pi);
+      s.L = v3(fmaf(s.beta.x * Le.x, wm, s.L.x), fmaf(s.beta.y * Le.y, wm, s.L.y), fmaf(s.beta.z * Le.z, wm, s.L.z));
+    }
+    return true;
+  }
+  if constexpr (ADJ) {
+    if (s.mode == kShadowPre) {
+      // T_fin known: the vertex's gradient; then the gradient pass of the same shadow ray
+      // (its random numbers replayed from the start of the NEE stream) if it carries any
+      const float Tfin = s.T;
+      adj_vertex_done<GEN>(s, S, A, s.d, Tfin, c);
+      if (Tfin > 0.0f && dot(s.gpix, s.pend) != 0.0f) {
+        s.Tfin = Tfin;
+        s.mode = kShadow;
+        s.T = 1.0f;
+        s.begin = true;
+        s.rng.start((uint32_t)(s.bounce - 1), kPurposeNee);
+        if (env) {
+          s.rng.next();
+          s.rng.next();
+        }
+        return false;
+      }
     }
   } else {
-    if (s.mode == kFlight) {
-      if (env) {
-        const V3 Le = env_radiance(S.light, s.d);
-        const float wm = s.prev_pdf < 0.0f ? 1.0f : power_heuristic(s.prev_pdf, kInv4Pi);
-        s.L = v3(fmaf(s.beta.x * Le.x, wm, s.L.x), fmaf(s.beta.y * Le.y, wm, s.L.y), fmaf(s.beta.z * Le.z, wm, s.L.z));
-      }
-      finish = true;
-    } else {
-      // shadow ray done (the adjoint added the vertex's contribution when shading it)
-      if constexpr (!ADJ) {
-        s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
-        if (path_T) path_T[(size_t)s.pidx * P.max_bounces + (s.bounce - 1)] = s.T;
-      }
-      if (s.cont) {
-        s.mode = kFlight;
-        s.d = s.d_next;
-        s.beta = s.beta_next;
-        s.prev_pdf = s.pdf_next;
-        s.rng.start((uint32_t)s.bounce, kPurposeFlight);
-        s.begin = true;
-      } else {
-        finish = true;
-      }
-    }
+    s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
   }
-  return finish;
+  return lane_continue(s);
 }
 
 // Film accumulation (forward) or the replay check (adjoint) of a finished path.
@@ -506,13 +616,16 @@ __device__ __forceinline__ long long warp_take(WarpCursor& wc, bool want, unsign
   return mine;
 }
 
-__device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned long long* counters, float* d_l) {
+__device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned long long* counters, float* d_l,
+                                               int n_objs) {
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
   if (d_l) {
-    float a = c.acc_l;
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(FULL, a, off);
-    if (lane == 0 && a != 0.0f) atomicAdd(d_l, a);
+    for (int k = 0; k < n_objs; ++k) {
+      float a = c.acc_l[k];
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(FULL, a, off);
+      if (lane == 0 && a != 0.0f) atomicAdd(d_l + k, a);
+    }
   }
   const uint32_t vals[7] = {c.paths, c.vert, c.null_, c.shadow, c.cells, c.trunc, c.abort};
 #pragma unroll
@@ -521,45 +634,83 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
     if (lane == 0 && v) atomicAdd(counters + i, v);
   }
+  unsigned long long nf = c.nonfinite;
+  for (int off = 16; off > 0; off >>= 1) nf += __shfl_down_sync(FULL, nf, off);
+  if (lane == 0 && nf) atomicAdd(counters + kCntNonFinite, nf);
   uint32_t me = c.max_events;
   for (int off = 16; off > 0; off >>= 1) me = max(me, __shfl_down_sync(FULL, me, off));
   if (lane == 0 && me) atomicMax(counters + kCntMaxEvents, (unsigned long long)me);
 }
 
+// ---------------------------------------------------------------- the path loop
+// One warp's persistent loop over the paths of a work source W, which provides:
+//   take(s, need, lane)  new paths for the lanes in `need` (warp-collective);
+//   exhausted()          no new path is left (warp-uniform);
+//   scene(s), args(s)    the scene and options of a path (its job's, in a batch);
+//   finish(s, c)         film accumulation / replay check of a finished path;
+//   adj()                the adjoint's buffers.
+// Each iteration: (1) lanes without a path take new ones; (2) once at least shade_min
+// lanes wait at a real vertex (or no other lane can step) the warp shades them
+// together; (3) every other lane with a path advances it by one tentative collision.
+template <bool ADJ, bool LOCAL, bool GEN, class W>
+__device__ __forceinline__ void path_loop(W& src, int shade_min, LaneCounters& c) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  Lane s;
+  lane_init(s);
+  for (;;) {
+    const unsigned need = __ballot_sync(FULL, !s.active);
+    if (need && !src.exhausted()) src.take(s, need, lane);
+    const unsigned act = __ballot_sync(FULL, s.active);
+    if (act == 0u) {
+      if (src.exhausted()) break;
+      continue;
+    }
+    const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
+    if (wait_mask && (__popc(wait_mask) >= shade_min || wait_mask == act)) {
+      if (s.waiting) lane_shade<ADJ, GEN>(s, src.scene(s), src.args(s), src.adj(), c);
+    }
+    if (!s.active || s.waiting) continue;
+    if (lane_step<ADJ, LOCAL, GEN>(s, src.scene(s), src.args(s), src.adj(), c)) src.finish(s, c);
+  }
+}
+
 // ---------------------------------------------------------------- single-render kernel
+// Work source of one render: path indices [0, total) from the global cursor.
+template <bool ADJ>
+struct RenderSource {
+  const SceneDev& S;
+  const CameraDev& C;
+  const PathArgs& P;
+  const AdjOut& A;
+  float* image;
+  float* sqsum;
+  float* path_radiance;
+  unsigned long long* cursor;
+  WarpCursor wc;
+  __device__ __forceinline__ void take(Lane& s, unsigned need, int lane) {
+    const long long mine = warp_take(wc, !s.active, need, lane, cursor, P.total, kChunk);
+    if (!s.active && mine >= 0 && mine < P.total) lane_start<ADJ>(s, C, P, A, mine);
+  }
+  __device__ __forceinline__ bool exhausted() const { return wc.exhausted || wc.next >= P.total; }
+  __device__ __forceinline__ const SceneDev& scene(const Lane&) const { return S; }
+  __device__ __forceinline__ const PathArgs& args(const Lane&) const { return P; }
+  __device__ __forceinline__ const AdjOut& adj() const { return A; }
+  __device__ __forceinline__ void finish(Lane& s, LaneCounters& c) { lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c); }
+};
+
 // LOCAL: the scene uses local majorants (MajorantDev::hot > 0).  GEN: some object is a
 // height-field macrofacet or has an anisotropic or non-stationary kernel (the adjoint
 // supports the isotropic GPSS, stationary or with a correlation-scale grid).
 template <bool ADJ, bool LOCAL, bool GEN>
-__global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 5)
+__global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 8)
     k_path(const __grid_constant__ SceneDev S, const __grid_constant__ CameraDev C, const __grid_constant__ PathArgs P,
            float* __restrict__ image, float* __restrict__ sqsum, float* __restrict__ path_radiance,
-           float* __restrict__ path_T, unsigned long long* __restrict__ counters, const __grid_constant__ AdjOut A) {
-  const unsigned FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
-  WarpCursor wc{0, 0, false};
-  Lane s;
-  lane_init(s);
-  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, 0.0f};
-  for (;;) {
-    const unsigned need = __ballot_sync(FULL, !s.active);
-    if (need && !wc.exhausted) {
-      const long long mine = warp_take(wc, !s.active, need, lane, counters + kCntNum, P.total, kChunk);
-      if (!s.active && mine >= 0 && mine < P.total) lane_start<ADJ>(s, C, P, A, mine);
-    }
-    const unsigned act = __ballot_sync(FULL, s.active);
-    if (act == 0) {
-      if (wc.exhausted || wc.next >= P.total) break;
-      continue;
-    }
-    const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
-    if (wait_mask && (__popc(wait_mask) >= P.shade_min || wait_mask == act)) {
-      if (s.waiting) lane_shade<ADJ, GEN>(s, S, P, A, path_T, c);
-    }
-    if (!s.active || s.waiting) continue;
-    if (lane_step<ADJ, LOCAL, GEN>(s, S, P, A, path_T, c)) lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c);
-  }
-  flush_counters(c, counters, ADJ ? A.d_l : nullptr);
+           unsigned long long* __restrict__ counters, const __grid_constant__ AdjOut A) {
+  RenderSource<ADJ> src{S, C, P, A, image, sqsum, path_radiance, counters + kCntNum, WarpCursor{0, 0, false}};
+  LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, {0.0f, 0.0f, 0.0f, 0.0f}, 0};
+  path_loop<ADJ, LOCAL, GEN>(src, P.shade_min, c);
+  flush_counters(c, counters, ADJ ? A.d_l : nullptr, S.n_objs);
 }
 
 }  // namespace gpss

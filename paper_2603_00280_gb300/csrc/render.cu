@@ -15,7 +15,7 @@ int render_grid_size(int device, int block) {
 }
 
 cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
-                          float* sqsum, float* path_radiance, float* path_T, unsigned long long* counters, int grid,
+                          float* sqsum, float* path_radiance, unsigned long long* counters, int grid,
                           int block, int shade_min, cudaStream_t st) {
   PathArgs P;
   P.spp = o.spp;
@@ -30,13 +30,13 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   AdjOut A{};
   const bool local = S.mg.hot > 0.0f, gen = scene_general(S);
   if (local && gen)
-    k_path<false, true, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+    k_path<false, true, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
   else if (local)
-    k_path<false, true, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+    k_path<false, true, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
   else if (gen)
-    k_path<false, false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+    k_path<false, false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
   else
-    k_path<false, false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, path_T, counters, A);
+    k_path<false, false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("paths", ctypes.c_uint64), ("vertices", ctypes.c_uint64), ("null_collisions", ctypes.c_uint64),
                 ("shadow_steps", ctypes.c_uint64), ("majorant_cells", ctypes.c_uint64),
                 ("truncated", ctypes.c_uint64), ("aborted", ctypes.c_uint64),
-                ("max_path_events", ctypes.c_uint64), ("ms", ctypes.c_float)]
+                ("max_path_events", ctypes.c_uint64), ("ms", ctypes.c_float), ("nonfinite", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -44,58 +44,70 @@ def rel_err(a, b, floor=0.0):
     return np.abs(a - b) / np.maximum(np.abs(b), floor)
 
 
-# The GPU film accumulates per-pixel sums with FP32 atomics; its variance estimate
-# E[L^2] - mean^2 cancels for nearly deterministic pixels (e.g. sky seen through
-# jittered rays).  A floor of FILM_REL * |mean| on the GPU standard error covers
-# the FP32 accumulation error of sums of up to ~10^4 samples.
-FILM_REL = 2e-5
+# The GPU film accumulates per-pixel sums with FP32 atomics.  For a nearly
+# deterministic pixel (sky seen through jittered rays) every addition rounds the
+# same way, so the sum of n equal terms can drift by up to n half-ulps of the
+# running sum: a relative error of n 2^-25, which the sample variance (nearly 0
+# there) does not show.  The GPU standard error is floored at that bound (plus a
+# tiny constant for 0-valued pixels).
+def film_floor(mean, spp):
+    return np.abs(mean) * spp * 2.0 ** -25 + 1e-9
 
 
-def image_z(gpu_mean, gpu_sqsum, gpu_spp, orc_sum, orc_sumsq, orc_spp, orc_sample_var=None):
-    """Per-pixel z of the difference between two Monte Carlo images.  orc_sample_var:
-    the per-sample variance of the oracle's estimator measured by a larger run of the
-    same estimator (the GPU with the oracle's sampler); it raises the oracle's own
-    small-sample estimate where that missed the heavy tail."""
+def robust_var(v):
+    """Per-sample variance map (H, W, 3) of one side, made robust to its own small
+    samples: the larger of the pixel's estimate and the mean of its 3x3 neighbourhood
+    (edges clamped).  The variance varies slowly across an image except at
+    silhouettes, where a pixel's few samples may all miss (or all hit) the object and
+    its own estimate collapses; the neighbourhood there includes both."""
+    v = np.asarray(v, np.float64)
+    if v.ndim != 3 or v.shape[0] < 2 or v.shape[1] < 2:
+        return v
+    p = np.pad(v, ((1, 1), (1, 1), (0, 0)), mode="edge")
+    H, W = v.shape[:2]
+    nb = sum(p[i:i + H, j:j + W] for i in range(3) for j in range(3)) / 9.0
+    return np.maximum(v, nb)
+
+
+def image_z(gpu_mean, gpu_sqsum, gpu_spp, orc_sum, orc_sumsq, orc_spp):
+    """Per-pixel z of the difference between two independent Monte Carlo images, each
+    with the standard error of its own samples only (nothing is pooled between the
+    two sides): per-sample variances from each side's own sums of squares, made
+    robust by robust_var, over that side's sample count.  The oracle renders with its
+    exact visible-normal sampler where the object allows it (bounded path weights);
+    the GPU takes many more samples than the oracle."""
     gm = np.asarray(gpu_mean, np.float64)
-    gv = np.maximum(np.asarray(gpu_sqsum, np.float64) / gpu_spp - gm ** 2, 0.0) / gpu_spp
-    gv = np.maximum(gv, (FILM_REL * np.abs(gm)) ** 2)
-    om = orc_sum / orc_spp
-    ovar = np.maximum(orc_sumsq / orc_spp - om ** 2, 0.0)
-    if orc_sample_var is not None:
-        ovar = np.maximum(ovar, orc_sample_var)
-    # Where both sides sample the same per-pixel distribution (the same sampler), the
-    # path weights are heavy tailed, so the smaller sample's variance estimate is
-    # raised to the pooled estimate (dominated by the larger, GPU sample).
-    pooled = (gv * gpu_spp * gpu_spp + ovar * orc_spp) / (gpu_spp + orc_spp)
-    ov = np.maximum(ovar, pooled) / orc_spp
+    gv = robust_var(np.maximum(np.asarray(gpu_sqsum, np.float64) / gpu_spp - gm ** 2, 0.0)) / gpu_spp
+    gv = np.maximum(gv, film_floor(gm, gpu_spp) ** 2)
+    om = np.asarray(orc_sum, np.float64) / orc_spp
+    ov = robust_var(np.maximum(np.asarray(orc_sumsq, np.float64) / orc_spp - om ** 2, 0.0)) / orc_spp
     se = np.sqrt(gv + ov)
     z = np.where(se > 0, (gm - om) / np.where(se > 0, se, 1.0), np.where(np.abs(gm - om) > 1e-6, np.inf, 0.0))
     return z, gm, om, np.sqrt(gv), np.sqrt(ov)
 
 
-def check_image_parity(gm, gse, om, ose, frac4=0.01, block=4):
-    """Heavy-tail-robust parity criteria for two Monte Carlo images:
-    - at most `frac4` of the pixels with |z| > 4 (the mixture sampler's path
-      weights are heavy tailed, so per-pixel sample errors underestimate now and
-      then; |z| > 3 is reported, not asserted);
-    - block means over `block` x `block` pixels: at most 3% with |z| > 3;
-    - the image total within 4 standard errors."""
+def check_image_parity(gm, gse, om, ose, frac3=0.01):
+    """The image parity bar: at most 1% of the compared pixel-channels with |z| > 3
+    (0.27% expected; at least one such entry is allowed when fewer than 100 are
+    compared, where 1% is not a whole entry), every channel's image total within 3
+    standard errors, and no entry beyond |z| = 6.  Returns (ok, a one-line report
+    with the worst entries)."""
     se = np.sqrt(gse ** 2 + ose ** 2)
     z = np.where(se > 0, (gm - om) / np.where(se > 0, se, 1), 0.0)
-    out = {"frac_z3": float(np.mean(np.abs(z) > 3)), "frac_z4": float(np.mean(np.abs(z) > 4))}
-    H, W = gm.shape[:2]
-    hb, wb = H // block * block, W // block * block
-    if hb and wb:
-        def blk(a, sq=False):
-            a = a[:hb, :wb].reshape(hb // block, block, wb // block, block, -1)
-            return (a ** 2).sum(axis=(1, 3)) if sq else a.sum(axis=(1, 3))
-        bz = (blk(gm) - blk(om)) / np.sqrt(blk(gse, True) + blk(ose, True) + 1e-300)
-        out["block_frac_z3"] = float(np.mean(np.abs(bz) > 3))
-    else:
-        out["block_frac_z3"] = 0.0
-    out["total_z"] = float((gm.sum() - om.sum()) / np.sqrt(np.sum(gse ** 2) + np.sum(ose ** 2)))
-    ok = out["frac_z4"] <= frac4 and out["block_frac_z3"] <= 0.03 and abs(out["total_z"]) < 4
-    return ok, out
+    n = z.size
+    n3 = int(np.sum(np.abs(z) > 3))
+    allowed = max(1, int(frac3 * n))
+    ch = gm.reshape(-1, gm.shape[-1])
+    tz = (ch.sum(0) - om.reshape(ch.shape).sum(0)) / np.sqrt(
+        (gse.reshape(ch.shape) ** 2).sum(0) + (ose.reshape(ch.shape) ** 2).sum(0) + 1e-300)
+    worst = np.argsort(-np.abs(z).reshape(-1))[:6]
+    fl = lambda a: a.reshape(-1)
+    report = "n=%d |z|>3: %d (allowed %d) max|z|=%.2f total z=%s worst (idx, z, gpu, oracle, gse, ose): %s" % (
+        n, n3, allowed, float(np.abs(z).max()), np.round(tz, 2).tolist(),
+        [(int(i), round(float(fl(z)[i]), 2), float("%.4g" % fl(gm)[i]), float("%.4g" % fl(om)[i]),
+          float("%.3g" % fl(gse)[i]), float("%.3g" % fl(ose)[i])) for i in worst])
+    ok = n3 <= allowed and bool(np.all(np.abs(tz) < 3)) and float(np.abs(z).max()) < 6
+    return ok, report
 
 
 def two_spheres_rgb():
@@ -110,9 +122,3 @@ def two_spheres_rgb():
         alb = rng.uniform(0.3, 0.95, size=(3, n[2], n[1], n[0])).astype(np.float32)
         objs.append(W.make_object(W.sdf_sphere(p, c, r), v, alb, lo, hi, 0.05))
     return {"objects": objs, "light": W.sky_light()}
-
-
-def sample_var(mean, sqsum, spp):
-    """Per-sample variance of a GPU image from its sum of squares."""
-    m = np.asarray(mean, np.float64)
-    return np.maximum(np.asarray(sqsum, np.float64) / spp - m * m, 0.0)

@@ -220,11 +220,6 @@ def test_autograd_function_and_edge_cases():
         assert st["aborted"] == 0
         outs.append(dm.cpu().numpy())
     np.testing.assert_allclose(outs[0], outs[1], rtol=1e-4, atol=1e-6 * np.abs(outs[1]).max())
-    # multi-object scenes are not differentiable here
-    two = {"objects": [obj, obj], "light": sc["light"]}
-    with pytest.raises(gpss.GpssError) as e:
-        gpss.render_adjoint(gpss.Scene(two), wl["camera"], wl["opts"], torch.zeros((8, 8, 3), device="cuda"))
-    assert e.value.status == 5
 
 
 def test_full_size_differentiable_voxels_against_finite_differences():
@@ -270,3 +265,72 @@ def test_full_size_differentiable_voxels_against_finite_differences():
     f, fse = _mean_se(fd)
     assert abs(a) > 3 * ase and abs(f) > 3 * fse, (a, ase, f, fse)
     assert abs(a - f) < 4 * math.sqrt(ase ** 2 + fse ** 2) + 0.05 * abs(f), (a, ase, f, fse)
+
+
+def test_two_object_gradients_match_the_oracle_adjoint():
+    """Several objects (extinctions add, the scatterer chosen by extinction): the
+    adjoint's gradients of each object -- its summed mean, variance and albedo (per
+    channel) gradients and its length scale -- against the FP64 oracle's adjoint
+    (orc_render_grad) on two overlapping spheres with RGB albedo.  The gradient grids
+    of the objects lie one after another in object order."""
+    import torch
+    import oracle
+    from tests import gpu_common as C
+    sc = C.two_spheres_rgb()
+    cam = W.perspective_camera(10, 10, eye=(0.0, -1.6, 0.6))
+    opts = {"spp": 4096, "max_bounces": 4, "mix_R": 0.5}
+    g = np.zeros((10, 10, 3))
+    g[..., 0] = 1.0
+    g[..., 1] = 0.5
+    sizes = [o["mean"].size for o in sc["objects"]]
+    S = gpss.Scene(sc)
+    gt = torch.as_tensor(g, dtype=torch.float32).cuda()
+    rows, nonfinite, paths = [], 0, 0
+    for sd in range(16):
+        dm = torch.zeros(sum(sizes), device="cuda")
+        dv = torch.zeros(sum(sizes), device="cuda")
+        da = torch.zeros(3 * sum(sizes), device="cuda")
+        dl = torch.zeros(2, device="cuda")
+        st = gpss.render_adjoint(S, cam, dict(opts, seed=300 + sd), gt, dm, dv, da, dl)
+        assert st["aborted"] == 0
+        nonfinite += st["nonfinite"]
+        paths += st["paths"]
+        dm, dv, da, dl = (t.double().cpu().numpy() for t in (dm, dv, da, dl))
+        r = []
+        for k in range(2):
+            o0 = sum(sizes[:k])
+            r += [dm[o0:o0 + sizes[k]].sum(), dv[o0:o0 + sizes[k]].sum()]
+            a = da[3 * o0:3 * (o0 + sizes[k])].reshape(3, -1)
+            r += list(a.sum(axis=1)) + [dl[k]]
+        rows.append(r)
+    e = np.array(rows)
+    gm, gse = e.mean(0), e.std(0, ddof=1) / math.sqrt(len(e))
+    O = oracle.Scene(sc)
+    orows = []
+    # the oracle samples phase functions exactly (bounded path weights; the same expected
+    # gradient as the mixture the GPU runs); 16 batches
+    for sd in range(16):
+        res, ost = oracle.render_grad(O, cam, dict(opts, spp=32, seed=700 + sd, sampler="vndf"), g,
+                                      want=("mean", "var", "albedo", "l"))
+        assert ost["mismatch"] == 0
+        r = []
+        for k in range(2):
+            r += [res[k]["mean"].sum(), res[k]["var"].sum()] + list(res[k]["albedo"].sum(axis=1)) + [res[k]["l"]]
+        orows.append(r)
+    o = np.array(orows)
+    om, ose = o.mean(0), o.std(0, ddof=1) / math.sqrt(len(o))
+    names = ["%s%d" % (n, k) for k in range(2) for n in ("mean", "var", "albedo_r", "albedo_g", "albedo_b", "l")]
+    zero = (gse == 0) & (ose == 0)
+    # the loss weights no blue: both sides give exactly 0 for the blue albedo
+    assert np.all(np.abs(gm[zero]) == 0) and np.all(np.abs(om[zero]) == 0)
+    z = np.where(zero, 0.0, (gm - om) / np.sqrt(gse ** 2 + ose ** 2 + 1e-300))
+    info = "skipped %d of %d paths' contributions; " % (nonfinite, paths) + "; ".join(
+        "%s gpu %.5g +- %.2g oracle %.5g +- %.2g z %.2f" % (n, a, b, c, d, e)
+        for n, a, b, c, d, e in zip(names, gm, gse, om, ose, z))
+    assert nonfinite <= 1e-5 * paths, info
+    # z ~ Student's t with 15 degrees of freedom (the oracle's 16 batches)
+    assert np.abs(z).max() < 4, info
+    assert np.sum(np.abs(z) > 3) <= 1, info
+    # the albedo (4 per object... 2 nonzero channels) and l gradients are resolved; the summed
+    # mean and variance gradients cancel between the objects' near and far sides
+    assert np.sum(np.abs(om) > 3 * ose) >= 6, info

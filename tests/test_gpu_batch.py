@@ -166,3 +166,30 @@ def test_batch_rejects_bad_jobs():
     h = ctypes.c_void_p()
     assert L.gpss_batch_create(sh, cs, os_, n, 128, None, ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_batched_images_match_the_oracle():
+    """Three scenes of the batched recipe, one of each mean (a volume-like box,
+    sigma 0.10; a plane, sigma 0.036; a surface-like sphere, sigma 0.008), rendered
+    by one batched launch, each against the FP64 oracle (its exact visible-normal
+    sampler, every second pixel row): at most 1% of the pixel-channels beyond 3
+    standard errors, each image's total within 3."""
+    import oracle
+    js = [W.batched_scene(s, size_scale=0.125) for s in (1, 3, 4)]
+    for j in js:
+        j["opts"].update(spp=4096, max_bounces=8)
+    scenes = [gpss.Scene(j["scene"]) for j in js]
+    B = gpss.Batch(scenes, [j["camera"] for j in js], [j["opts"] for j in js], block_size=128)
+    imgs, sqs, st = B.render(want_sqsum=True)
+    assert st["aborted"] == 0
+    gm_all, gse_all, om_all, ose_all = [], [], [], []
+    for j, img, sq in zip(js, imgs, sqs):
+        cam = j["camera"]
+        rows = (0, cam["height"], 2)
+        s, s2, _ = oracle.render(oracle.Scene(j["scene"]), cam, dict(j["opts"], spp=64, seed=7, sampler="vndf"),
+                                 rows=rows)
+        sel = slice(*rows)
+        z, gm, om, gse, ose = C.image_z(img.cpu().numpy()[sel], sq.cpu().numpy()[sel], 4096, s[sel], s2[sel], 64)
+        ok, info = C.check_image_parity(gm, gse, om, ose)
+        assert ok, (j["name"], info)
+        assert om.max() > 0.0

@@ -172,11 +172,11 @@ def test_images_match_oracle(hf):
     for o in wl["scene"]["objects"]:
         o["ndf"] = kind
     G, O = gpss.Scene(wl["scene"]), oracle.Scene(wl["scene"])
-    spp = 2048
+    spp = 8192
     img, sq, st = gpss.render(G, wl["camera"], dict(wl["opts"], spp=spp, seed=3), want_sqsum=True)
     img, sq = img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64)
-    s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=64, seed=4))
-    z, gm, om, gse, ose = C.image_z(img, sq, spp, s, s2, 64)
+    s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=128, seed=4, sampler="vndf"))
+    z, gm, om, gse, ose = C.image_z(img, sq, spp, s, s2, 128)
     ok, info = C.check_image_parity(gm, gse, om, ose)
     assert ok, info
     assert st["aborted"] == 0

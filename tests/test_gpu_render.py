@@ -53,7 +53,7 @@ def test_white_furnace():
 def _parity(sc, cam, opts, orc_spp, gpu_spp, rows=None, cols=None, brick=0):
     img, sq, st = _gpu_render(sc, cam, dict(opts, spp=gpu_spp, seed=101), brick)
     O = oracle.Scene(sc)
-    s, s2, ost = oracle.render(O, cam, dict(opts, spp=orc_spp, seed=202), rows=rows, cols=cols)
+    s, s2, ost = oracle.render(O, cam, dict(opts, spp=orc_spp, seed=202, sampler="vndf"), rows=rows, cols=cols)
     H_, W_ = cam["height"], cam["width"]
     r = rows or (0, H_, 1)
     c = cols or (0, W_)
@@ -68,19 +68,19 @@ def _parity(sc, cam, opts, orc_spp, gpu_spp, rows=None, cols=None, brick=0):
 def test_tiny_slab_image_parity():
     """The tiny workload (64x64 orthographic view of the slab, 8 bounces) vs the oracle."""
     wl = W.tiny_slab()
-    _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=64, gpu_spp=1024, rows=(0, 64, 4))
+    _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=128, gpu_spp=8192, rows=(0, 64, 4))
 
 
 @pytest.mark.parametrize("brick", [1, 4])
 def test_heterogeneous_image_parity(brick):
     wl = W.heterogeneous(n=32, width=24, height=24, spp=32, max_bounces=16)
-    _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=64, gpu_spp=2048, brick=brick)
+    _parity(wl["scene"], wl["camera"], wl["opts"], orc_spp=128, gpu_spp=8192, brick=brick)
 
 
 def test_rgb_albedo_and_multiple_objects_parity():
     sc = C.two_spheres_rgb()
     cam = W.perspective_camera(20, 20, eye=(0.0, -1.6, 0.6))
-    _parity(sc, cam, {"spp": 16, "max_bounces": 8, "mix_R": 0.5}, orc_spp=48, gpu_spp=2048)
+    _parity(sc, cam, {"spp": 16, "max_bounces": 8, "mix_R": 0.5}, orc_spp=128, gpu_spp=8192)
 
 
 def test_sky_only_pixels_are_exact():
@@ -121,23 +121,37 @@ def test_same_seed_same_image_and_host_output():
     assert not np.allclose(a, c.cpu().numpy())
 
 
+def _full_size(wl, repeats):
+    """`repeats` full-size renders (the benchmark's launch) with consecutive seeds,
+    combined: mean image, summed squares and the total samples per pixel."""
+    S = gpss.Scene(wl["scene"])
+    H_, W_, spp = wl["camera"]["height"], wl["camera"]["width"], wl["opts"]["spp"]
+    m, q = np.zeros((H_, W_, 3)), np.zeros((H_, W_, 3))
+    for i in range(repeats):
+        img, sq, st = gpss.render(S, wl["camera"], dict(wl["opts"], seed=wl["opts"]["seed"] + 1000 * i), want_sqsum=True)
+        assert st["paths"] == H_ * W_ * spp and st["aborted"] == 0
+        m += img.cpu().numpy().astype(np.float64) / repeats
+        q += sq.cpu().numpy().astype(np.float64)
+    S.close()
+    assert np.all(np.isfinite(m))
+    return m, q, spp * repeats
+
+
 def test_full_size_workload_sampled_pixels():
-    """The benchmarked configuration (128^3 grid, 512x512, 64 spp, 32 bounces) in
-    the launch configuration the benchmark uses; a sample of pixels is checked
+    """The heterogeneous configuration (128^3 grid, 512x512, 64 spp, 32 bounces) in
+    the launch configuration the benchmark uses (16 renders with their own seeds, so
+    that the GPU side's standard errors are small); a sample of pixels is checked
     against the oracle one by one."""
     wl = W.heterogeneous()
-    S = gpss.Scene(wl["scene"])
-    img, sq, st = gpss.render(S, wl["camera"], wl["opts"], want_sqsum=True)
-    img, sq = img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64)
-    assert st["paths"] == 512 * 512 * 64 and st["aborted"] == 0
-    assert np.all(np.isfinite(img))
+    img, sq, gspp = _full_size(wl, 16)
     O = oracle.Scene(wl["scene"])
-    orc_spp = 32
-    rows, cols = (236, 276, 5), (246, 250)      # 8 x 4 pixels over the sphere's shell
-    s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=orc_spp, seed=5), rows=rows, cols=cols)
+    orc_spp = 64
+    rows, cols = (220, 284, 4), (240, 256)      # 16 x 16 pixels over the sphere's shell
+    s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=orc_spp, seed=5, sampler="vndf"), rows=rows,
+                             cols=cols)
     sel = (slice(*rows), slice(*cols))
-    z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], 64, s[sel], s2[sel], orc_spp)
-    ok, info = C.check_image_parity(gm, gse, om, ose, frac4=0.1, block=2)
+    z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], gspp, s[sel], s2[sel], orc_spp)
+    ok, info = C.check_image_parity(gm, gse, om, ose)
     assert ok, info
 
 
@@ -147,22 +161,19 @@ def test_full_size_surface_to_volume_sampled_pixels():
     256 spp, 64 bounces): every path completes, and sampled pixels over each object
     agree with the oracle."""
     wl = W.surface_to_volume()
-    S = gpss.Scene(wl["scene"])
-    img, sq, st = gpss.render(S, wl["camera"], wl["opts"], want_sqsum=True)
-    img, sq = img.cpu().numpy().astype(np.float64), sq.cpu().numpy().astype(np.float64)
-    assert st["paths"] == 1024 * 1024 * 256 and st["aborted"] == 0
-    assert np.all(np.isfinite(img))
-    S.close()
+    img, sq, gspp = _full_size(wl, 4)
     O = oracle.Scene(wl["scene"])
     gm_all, gse_all, om_all, ose_all = [], [], [], []
-    # torus (thin shell, slow in the oracle), box, sphere
-    for rows, cols, orc_spp in [((500, 502), (370, 372), 8), ((500, 504), (510, 514), 16), ((500, 504), (650, 654), 16)]:
-        s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=orc_spp, seed=9), rows=rows, cols=cols)
+    # torus (thin shell, slow in the oracle), box, sphere: 8 x 8 pixels each
+    for rows, cols, orc_spp in [((496, 504), (368, 376), 16), ((496, 504), (508, 516), 32),
+                                ((496, 504), (648, 656), 32)]:
+        s, s2, _ = oracle.render(O, wl["camera"], dict(wl["opts"], spp=orc_spp, seed=9, sampler="vndf"), rows=rows,
+                                 cols=cols)
         sel = (slice(*rows), slice(*cols))
-        z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], 256, s[sel], s2[sel], orc_spp)
+        z, gm, om, gse, ose = C.image_z(img[sel], sq[sel], gspp, s[sel], s2[sel], orc_spp)
         assert om.max() > 0.0  # the region sees the object
         for a, lst in ((gm, gm_all), (gse, gse_all), (om, om_all), (ose, ose_all)):
             lst.append(a.reshape(-1, 3))
     gm, gse, om, ose = (np.concatenate(l)[:, None, :] for l in (gm_all, gse_all, om_all, ose_all))
-    ok, info = C.check_image_parity(gm, gse, om, ose, frac4=0.1, block=1)
+    ok, info = C.check_image_parity(gm, gse, om, ose)
     assert ok, info

@@ -167,7 +167,7 @@ def test_images_and_tentative_collisions_against_constant_pieces(sphere):
     sc, G, _ = sphere
     cam = W.perspective_camera(24, 24)
     spp = 2048
-    opts = {"spp": spp, "max_bounces": 8}
+    opts = {"spp": spp, "max_bounces": 8, "sampler": "vndf"}  # bounded path weights on both sides
     G.set_surface_flight(True)
     img, sq, sa = gpss.render(G, cam, dict(opts, seed=21), want_sqsum=True)
     G.set_surface_flight(False)

@@ -110,12 +110,13 @@ def test_vndf_images_match_oracle_and_reduce_variance():
     wl = W.heterogeneous(n=32, width=20, height=20, spp=16, max_bounces=12)
     sc, cam = wl["scene"], wl["camera"]
     G, O = gpss.Scene(sc), oracle.Scene(sc)
-    spp = 2048
+    spp = 8192
     a, asq, sa = _render(G, cam, dict(wl["opts"], spp=spp, seed=41, sampler="vndf"))
-    s, s2, _ = oracle.render(O, cam, dict(wl["opts"], spp=48, seed=42))
-    # the oracle samples the mixture: its per-sample variance from the GPU mixture run
+    # the oracle's own exact sampler (an independent implementation: bisection of the
+    # visible slope's closed-form CDF in FP64)
+    s, s2, _ = oracle.render(O, cam, dict(wl["opts"], spp=128, seed=42, sampler="vndf"))
     b, bsq, sb = _render(G, cam, dict(wl["opts"], spp=spp, seed=43))
-    z, gm, om, gse, ose = C.image_z(a, asq, spp, s, s2, 48, orc_sample_var=C.sample_var(b, bsq, spp))
+    z, gm, om, gse, ose = C.image_z(a, asq, spp, s, s2, 128)
     ok, info = C.check_image_parity(gm, gse, om, ose)
     assert ok, info
     va = np.maximum(asq / spp - a * a, 0)
