@@ -181,8 +181,9 @@ struct Rng {
 };
 
 // ---------------------------------------------------------------- special functions
-// lambda(u) = phi(u)/Phi(u) = sqrt(2/pi) / erfcx(-u/sqrt2)   (inverse Mills ratio)
-__device__ __forceinline__ float inv_mills(float u) { return kSqrt2OverPi / erfcxf(-u * kInvSqrt2); }
+// lambda(u) = phi(u)/Phi(u) = sqrt(2/pi) / erfcx(-u/sqrt2)   (inverse Mills ratio).  The
+// division is the fast one (2 ulp; it returns 0 where erfcx overflows, lambda's limit).
+__device__ __forceinline__ float inv_mills(float u) { return __fdividef(kSqrt2OverPi, erfcxf(-u * kInvSqrt2)); }
 
 // e^{-a^2} without the rounding error of a*a: a^2 = hi + lo exactly (lo from an FMA,
 // the error-free product of Dekker / Ogita-Rump-Oishi), e^{-a^2} = e^{-hi} (1 - lo) to
@@ -343,11 +344,14 @@ struct Local {
   float rho;     // lambda(mu/sigma)/sigma
 };
 
+// One reciprocal square root serves sigma, mu/sigma and rho (a few ulp each: far below the
+// 1e-5 bar, and lambda's sensitivity to u is |u + lambda|, so also at |u| ~ 10).
 __device__ __forceinline__ Local local_of(const ObjectDev& o, const Field& f) {
   Local l;
-  l.sigma = sqrtf(f.var);
+  const float inv_sig = rsqrtf(f.var);
+  l.sigma = f.var * inv_sig;
   l.alpha = l.sigma * f.as;
-  l.rho = inv_mills(f.mu / l.sigma) / l.sigma;
+  l.rho = inv_mills(f.mu * inv_sig) * inv_sig;
   return l;
 }
 
@@ -462,7 +466,7 @@ __device__ __forceinline__ bool is_aniso(const Field& f) { return f.kb != 1.0f |
 __device__ __forceinline__ float projected_area(V3 d, const Field& f, float alpha) {
   if (f.ndf != kNdfGpss) return hf_projected_area(f.ndf, d, hf_normal(f.g), alpha);
   if (is_aniso(f)) return area_aniso(d, f, alpha);
-  return alpha * psi(dot(d, f.g) / alpha);
+  return alpha * psi(__fdividef(dot(d, f.g), alpha));
 }
 
 // sigma_t of one object at x for direction d (0 outside its box); fills f/l.
