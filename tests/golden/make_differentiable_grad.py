@@ -4,7 +4,9 @@ per-voxel test (tests/test_gpu_adjoint_voxels.py).
 
 Configuration: the start field of the differentiable workload (64^3 mean,
 variance and albedo grids, l = 0.012; 256x256 perspective camera, procedural sky,
-32 bounces, the paper's sampling mixture R = 0.5).  Loss: the sum of all three
+32 bounces).  The oracle samples phase functions exactly (its visible-normal
+sampler: the same expected gradient as the paper's mixture, which the GPU side
+runs, with bounded path weights, so batch standard errors are reliable).  Loss: the sum of all three
 channels over a 16x16 window of the image (d_image = 1 there, 0 elsewhere).
 Voxels: 32 nodes (seed 3) drawn from the shell nodes (|mu| < 3 sigma, reading Q18)
 that project into the window's interior and that the camera sees (oracle
@@ -97,7 +99,7 @@ def main():
     t0 = time.time()
     rows, paths = [], 0
     for b in range(a.batches):
-        (r,), st = oracle.render_grad(S, cam, dict(opts, spp=a.spp, seed=1 + b), g, nodes=[nodes],
+        (r,), st = oracle.render_grad(S, cam, dict(opts, spp=a.spp, seed=1 + b, sampler="vndf"), g, nodes=[nodes],
                                       want=("mean", "var", "albedo"), **win)
         assert st["mismatch"] == 0
         paths += st["paths"]
@@ -107,8 +109,8 @@ def main():
     m, se = e.mean(0), e.std(0, ddof=1) / math.sqrt(len(e))
     lrows = []
     for b in range(a.l_batches):
-        (r,), st = oracle.render_grad(S, cam, dict(opts, spp=a.l_spp, seed=1001 + b), g, nodes=[nodes[:1]],
-                                      want=("l",), **win)
+        (r,), st = oracle.render_grad(S, cam, dict(opts, spp=a.l_spp, seed=1001 + b, sampler="vndf"), g,
+                                      nodes=[nodes[:1]], want=("l",), **win)
         paths += st["paths"]
         lrows.append(r["l"])
         print("l batch %d/%d  %.0f s" % (b + 1, a.l_batches, time.time() - t0), flush=True)
@@ -116,7 +118,8 @@ def main():
     k = len(nodes)
     out = {
         "generated_by": "tests/golden/make_differentiable_grad.py (FP64 oracle, orc_render_grad)",
-        "workload": "differentiable_64 start field (64^3; 256x256 perspective, sky, 32 bounces, mixture R=0.5)",
+        "workload": "differentiable_64 start field (64^3; 256x256 perspective, sky, 32 bounces); oracle sampler: "
+                    "exact visible normals",
         "loss": "sum of all channels of the image over the window (d_image = 1 there, 0 elsewhere)",
         "window": list(WINDOW),
         "voxel_rule": "32 nodes (seed 3) among shell nodes |mu| < 3 sigma projecting into the window interior "
