@@ -40,6 +40,40 @@ __global__ void k_split_grad(const float2* __restrict__ mv, float* __restrict__ 
   }
 }
 
+// The adjoint instance of the path kernel for the scene (its traversal, as the forward
+// render's, so the replay takes the same tentative collisions; the general one where an
+// object has a correlation-scale grid, the only general feature the adjoint accepts) on
+// a grid of the SMs times its resident blocks.  A.record = 1 runs it as the recording
+// forward pass (film image/sqsum, per-path radiance path_radiance).
+cudaError_t launch_adjoint_kernel(const SceneDev& S, const CameraDev& C, const PathArgs& P, float* image, float* sqsum,
+                                  float* path_radiance, unsigned long long* counters, const AdjOut& A, int device,
+                                  cudaStream_t cs) {
+  const int trav = trav_of(S);
+  const bool gen = scene_general(S);
+  const void* fns[2][4] = {{(const void*)k_path<true, kTravGrid, false>, (const void*)k_path<true, kTravLocal, false>,
+                            (const void*)k_path<true, kTravSplit, false>, (const void*)k_path<true, kTravSplitLocal, false>},
+                           {(const void*)k_path<true, kTravGrid, true>, (const void*)k_path<true, kTravLocal, true>,
+                            (const void*)k_path<true, kTravSplit, true>, (const void*)k_path<true, kTravSplitLocal, true>}};
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[gen ? 1 : 0][trav], kPathBlock, 0);
+  const int g = sms * (per_sm > 0 ? per_sm : 1);
+  float *im = image, *sq = sqsum, *pr = path_radiance;
+  unsigned long long* ct = counters;
+  if (gen) {
+    if (trav == kTravSplitLocal) k_path<true, kTravSplitLocal, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else if (trav == kTravSplit) k_path<true, kTravSplit, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else if (trav == kTravLocal) k_path<true, kTravLocal, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else k_path<true, kTravGrid, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+  } else {
+    if (trav == kTravSplitLocal) k_path<true, kTravSplitLocal, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else if (trav == kTravSplit) k_path<true, kTravSplit, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else if (trav == kTravLocal) k_path<true, kTravLocal, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else k_path<true, kTravGrid, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace gpss
 
 using namespace gpss;
@@ -119,7 +153,7 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   P.inv_spp = 1.0f / (float)opts->spp;
   P.shade_min = s->shade_min;
   P.exact_vndf = (opts->flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
-  AdjOut A;
+  AdjOut A{};
   A.d_image = d_image;
   A.L_path = s->path_radiance;
   // gradient grids of the objects one after another (object order); albedo: each
@@ -149,25 +183,7 @@ extern "C" gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam,
   A.d_alb = d_albedo;
   A.d_l = d_length_scale;
   A.d_cs = d_correlation_scale;
-  int sms = 0, per_sm = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  const SceneDev S = scene_dev(s);
-  // instances: local majorants or not; the general one where the object has a
-  // correlation-scale grid (the only general feature the adjoint accepts)
-  const bool local = S.mg.hot > 0.0f, gen = scene_general(S);
-  const void* fn = local ? (gen ? (const void*)k_path<true, true, true> : (const void*)k_path<true, true, false>)
-                         : (gen ? (const void*)k_path<true, false, true> : (const void*)k_path<true, false, false>);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPathBlock, 0);
-  const int agrid = sms * (per_sm > 0 ? per_sm : 1);
-  float* const nf = nullptr;
-  if (local && gen)
-    k_path<true, true, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
-  else if (local)
-    k_path<true, true, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
-  else if (gen)
-    k_path<true, false, true><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
-  else
-    k_path<true, false, false><<<agrid, kPathBlock, 0, cs>>>(S, C, P, nf, nf, nf, s->counters, A);
+  e = launch_adjoint_kernel(scene_dev(s), C, P, nullptr, nullptr, nullptr, s->counters, A, s->device, cs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   if (A.d_mv) {

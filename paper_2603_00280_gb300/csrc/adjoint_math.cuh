@@ -43,18 +43,20 @@ struct DSig {
   V3 dg;
 };
 
+// st is evaluated by the forward's own expressions (local_of, projected_area), so that
+// the adjoint's tentative-collision decisions replay the forward's bit for bit; the
+// partials reuse sigma, alpha and rho from it.
 __device__ __forceinline__ DSig dsigma_t(const ObjectDev& o, const Field& f, V3 d) {
-  const float sig = sqrtf(f.var);
-  const float alpha = sig * f.as;  // sqrt2 sigma/(s(x) l)
+  const Local l = local_of(o, f);
+  const float sig = l.sigma, alpha = l.alpha, rho = l.rho;  // alpha = sqrt2 sigma/(s(x) l)
   const float u = f.mu / sig;
-  const float lam = inv_mills(u);
+  const float lam = rho * sig;
   const float lamp = -lam * (u + lam);
-  const float rho = lam / sig;
   float ps, ec_over, ea_over;
   psi_ratios(dot(d, f.g) / alpha, ps, ec_over, ea_over);
   const float S = alpha * ps;
   DSig r;
-  r.st = rho * S;
+  r.st = rho * projected_area(d, f, alpha);
   r.dmu = S * lamp / f.var;
   // sigma(d) = alpha psi(d.grad mu/alpha): the alpha cancels, d sigma(d)/d grad mu = psi'(a) d
   // = -erfc(a)/2 d, with erfc(a) = ec_over psi

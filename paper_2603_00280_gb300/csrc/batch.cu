@@ -3,9 +3,9 @@
 //
 // Work distribution.  The paths of all jobs (scene, camera, options) form one
 // index space: job j owns [begin_j, begin_j + npix_j * spp_j), and inside a job a
-// path's index is gpss_render's (sample * npix + pixel).  Resident warps take
-// chunks of consecutive indices from one atomic cursor (warp_take), so a chunk is
-// a tile of (job, sample, pixel range) and crosses a job boundary at most once.
+// path's index is gpss_render's (path_of: pixel tiles, samples within a tile).  Resident warps take
+// chunks of consecutive indices from one atomic cursor (warp_take), so a chunk mostly
+// lies in one job.
 // A lane looks its job up when a new path's index leaves its current job's range
 // (binary search over the begin offsets) and reads the job's scene, camera and
 // options by reference from the device table: lanes of one warp mostly share a
@@ -83,23 +83,24 @@ struct BatchSource {
   }
   __device__ __forceinline__ bool exhausted() const { return wc.exhausted || wc.next >= total; }
   __device__ __forceinline__ const SceneDev& scene(const Lane& s) const { return jobs[s.job].S; }
+  __device__ __forceinline__ const MajorantDev* grids(const Lane& s) const { return jobs[s.job].S.og; }
   __device__ __forceinline__ const PathArgs& args(const Lane& s) const { return jobs[s.job].P; }
   __device__ __forceinline__ const AdjOut& adj() const { return A; }
   __device__ __forceinline__ void finish(Lane& s, LaneCounters& c) {
     const JobDev& J = jobs[s.job];
-    lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, c);
+    lane_finish<false>(s, J.P, J.image, J.sqsum, nullptr, false, c);
   }
 };
 
 // The persistent kernel over all jobs: k_path's loop over the batch's work source.  Register cap 96 for every block size, so that 640 lanes per
 // SM stay resident.
-template <int BLOCK, bool LOCAL, bool GEN>
+template <int BLOCK, int TRAV, bool GEN>
 __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const long long* __restrict__ begins,
                                         int n_jobs, long long total, int chunk, int shade_min,
                                         unsigned long long* __restrict__ counters) {
   BatchSource src{jobs, begins, n_jobs, total, chunk, counters + kCntNum, AdjOut{}, WarpCursor{0, 0, false}};
   LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, {0.0f, 0.0f, 0.0f, 0.0f}, 0};
-  path_loop<false, LOCAL, GEN>(src, shade_min, c);
+  path_loop<false, TRAV, GEN>(src, shade_min, c);
   flush_counters(c, counters, nullptr, 0);
 }
 
@@ -115,48 +116,62 @@ __global__ void k_zero_films(const JobDev* __restrict__ jobs) {
   }
 }
 
-template <int BLOCK, bool LOCAL, bool GEN>
+template <int BLOCK, int TRAV, bool GEN>
 static int batch_grid(int device) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK, LOCAL, GEN>, BLOCK, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK, TRAV, GEN>, BLOCK, 0);
   return sms * std::max(per_sm, 1);
 }
 
-template <bool LOCAL, bool GEN>
+template <int TRAV, bool GEN>
 static int grid_for_t(int block, int device) {
   switch (block) {
-    case 64: return batch_grid<64, LOCAL, GEN>(device);
-    case 256: return batch_grid<256, LOCAL, GEN>(device);
-    default: return batch_grid<128, LOCAL, GEN>(device);
+    case 64: return batch_grid<64, TRAV, GEN>(device);
+    case 256: return batch_grid<256, TRAV, GEN>(device);
+    default: return batch_grid<128, TRAV, GEN>(device);
   }
 }
 
-static int grid_for(int block, bool local, bool gen, int device) {
-  if (local) return gen ? grid_for_t<true, true>(block, device) : grid_for_t<true, false>(block, device);
-  return gen ? grid_for_t<false, true>(block, device) : grid_for_t<false, false>(block, device);
+// The batch instances: the grid walk, local majorants, and per-object intervals with
+// local majorants (which serves every scene).
+template <bool GEN>
+static int grid_for_g(int block, int trav, int device) {
+  if (trav & kTravSplit) return grid_for_t<kTravSplitLocal, GEN>(block, device);
+  if (trav == kTravLocal) return grid_for_t<kTravLocal, GEN>(block, device);
+  return grid_for_t<kTravGrid, GEN>(block, device);
 }
 
-template <bool LOCAL, bool GEN>
+static int grid_for(int block, int trav, bool gen, int device) {
+  return gen ? grid_for_g<true>(block, trav, device) : grid_for_g<false>(block, trav, device);
+}
+
+template <int TRAV, bool GEN>
 static void launch_batch_t(int block, int grid, const JobDev* jobs, const long long* begins, int n, long long total,
                            int chunk, int shade_min, unsigned long long* counters, cudaStream_t st) {
   switch (block) {
-    case 64: k_batch<64, LOCAL, GEN><<<grid, 64, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-    case 256: k_batch<256, LOCAL, GEN><<<grid, 256, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
-    default: k_batch<128, LOCAL, GEN><<<grid, 128, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    case 64: k_batch<64, TRAV, GEN><<<grid, 64, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    case 256: k_batch<256, TRAV, GEN><<<grid, 256, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
+    default: k_batch<128, TRAV, GEN><<<grid, 128, 0, st>>>(jobs, begins, n, total, chunk, shade_min, counters); break;
   }
 }
 
-static cudaError_t launch_batch(int block, bool local, bool gen, int grid, const JobDev* jobs, const long long* begins,
+template <bool GEN>
+static void launch_batch_g(int block, int trav, int grid, const JobDev* jobs, const long long* begins, int n,
+                           long long total, int chunk, int shade_min, unsigned long long* counters, cudaStream_t st) {
+  if (trav & kTravSplit)
+    launch_batch_t<kTravSplitLocal, GEN>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+  else if (trav == kTravLocal)
+    launch_batch_t<kTravLocal, GEN>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+  else
+    launch_batch_t<kTravGrid, GEN>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+}
+
+static cudaError_t launch_batch(int block, int trav, bool gen, int grid, const JobDev* jobs, const long long* begins,
                                 int n, long long total, int chunk, int shade_min, unsigned long long* counters,
                                 cudaStream_t st) {
-  if (local) {
-    if (gen) launch_batch_t<true, true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
-    else launch_batch_t<true, false>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
-  } else {
-    if (gen) launch_batch_t<false, true>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
-    else launch_batch_t<false, false>(block, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
-  }
+  if (gen) launch_batch_g<true>(block, trav, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
+  else launch_batch_g<false>(block, trav, grid, jobs, begins, n, total, chunk, shade_min, counters, st);
   return cudaGetLastError();
 }
 
@@ -183,7 +198,7 @@ struct gpss_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool table_valid = false;
-  bool local = false;              // some job's scene uses local majorants
+  int trav = kTravGrid;            // the union of the jobs' traversal kinds (trav_of bits)
   bool gen = false;                // some job's scene needs the general kernel instances
   int block = 128, shade_min = kBatchDefaultShade, chunk = kBatchDefaultChunk, grid = 0;
 };
@@ -222,12 +237,12 @@ static void fill_table(const gpss_batch_s* b, JobDev* out, float* const* images,
 static float time_shape(gpss_batch b, int block, int shade_min, int chunk, const JobDev* jobs, const long long* begins,
                         long long total, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, bool warm,
                         cudaError_t* err) {
-  const int grid = grid_for(block, b->local, b->gen, b->device);
+  const int grid = grid_for(block, b->trav, b->gen, b->device);
   float ms = 0.0f;
   for (int rep = warm ? 0 : 1; rep < 2; ++rep) {
     cudaMemsetAsync(b->counters, 0, 16 * sizeof(unsigned long long), st);
     cudaEventRecord(e0, st);
-    if ((*err = launch_batch(block, b->local, b->gen, grid, jobs, begins, b->n, total, chunk, shade_min, b->counters, st)) != cudaSuccess)
+    if ((*err = launch_batch(block, b->trav, b->gen, grid, jobs, begins, b->n, total, chunk, shade_min, b->counters, st)) != cudaSuccess)
       return -1.0f;
     cudaEventRecord(e1, st);
     if ((*err = cudaEventSynchronize(e1)) != cudaSuccess) return -1.0f;
@@ -333,7 +348,7 @@ static gpss_status capture_graph(gpss_batch b) {
     return cuda_fail(e, "begin capture");
   cudaMemsetAsync(b->counters, 0, 16 * sizeof(unsigned long long), b->capture);
   k_zero_films<<<dim3(64, b->n), 256, 0, b->capture>>>(b->table_dev);
-  cudaError_t le = launch_batch(b->block, b->local, b->gen, b->grid, b->table_dev, b->begins_dev, b->n, b->total, b->chunk,
+  cudaError_t le = launch_batch(b->block, b->trav, b->gen, b->grid, b->table_dev, b->begins_dev, b->n, b->total, b->chunk,
                                 b->shade_min, b->counters, b->capture);
   e = cudaStreamEndCapture(b->capture, &b->graph);
   if (le != cudaSuccess) return cuda_fail(le, "batch launch (capture)");
@@ -378,7 +393,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
       return GPSS_ERR_INVALID_ARG;
     }
     if (!camera_dev(&cams[i], &b->cams[i])) { free_batch(b); return GPSS_ERR_INVALID_ARG; }
-    if (scene_dev(scenes[i]).mg.hot > 0.0f) b->local = true;
+    b->trav |= trav_of(scene_dev(scenes[i]));
     if (scene_general(scene_dev(scenes[i]))) b->gen = true;
     PathArgs& P = b->args[i];
     P.spp = opts[i].spp;
@@ -416,7 +431,7 @@ extern "C" gpss_status gpss_batch_create(const gpss_scene* scenes, const gpss_ca
   } else {
     b->block = block_size;
   }
-  b->grid = grid_for(b->block, b->local, b->gen, dev);
+  b->grid = grid_for(b->block, b->trav, b->gen, dev);
   if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) { st = cuda_fail(e, "batch setup"); free_batch(b); return st; }
   if ((st = capture_graph(b)) != GPSS_OK) { free_batch(b); return st; }
   *out = b;

@@ -178,6 +178,8 @@ static void free_scene(gpss_scene s) {
     cudaFree(s->obj[k].albedo);
     cudaFree(s->obj[k].cscale);
     cudaFree(s->obj[k].tangent);
+    cudaFree(s->obj[k].omaj);
+    cudaFree(s->obj[k].oskip);
   }
   cudaFree(s->maj);
   cudaFree(s->skip);
@@ -220,8 +222,38 @@ static gpss_status setup_majorant(gpss_scene s) {
   if (e != cudaSuccess) return cuda_fail(e, "majorant allocation");
   s->mg.maj = s->maj;
   if ((e = cudaMalloc(&s->skip, ncell * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "skip grid allocation");
-  if ((e = cudaMalloc(&s->skip_tmp, 3 * ncell * sizeof(float))) != cudaSuccess) return cuda_fail(e, "skip scratch allocation");
   s->mg.skip = s->skip;
+  size_t tmp_cells = ncell;
+  if (s->n_objs > 1) {
+    // each object's own grid: its box at its node spacing (x the brick that keeps it
+    // below 64 Mi cells)
+    for (int k = 0; k < s->n_objs; ++k) {
+      ObjectHost& o = s->obj[k];
+      MajorantDev& g = o.og;
+      g = MajorantDev{};
+      for (int b = 1;; b *= 2) {
+        double cells = 1.0;
+        for (int a = 0; a < 3; ++a) {
+          const float cell = (o.bmax[a] - o.bmin[a]) / (float)(o.n[a] - 1) * b;
+          g.gmin[a] = o.bmin[a];
+          g.cell[a] = cell;
+          g.inv_cell[a] = 1.0f / cell;
+          g.dims[a] = std::max(1, (int)std::ceil((o.bmax[a] - o.bmin[a]) / cell - 1e-4f));
+          cells *= g.dims[a];
+        }
+        if (cells <= 1.0 * (1 << 26) || b >= 64) break;
+      }
+      const size_t oc = (size_t)g.dims[0] * g.dims[1] * g.dims[2];
+      if ((e = cudaMalloc(&o.omaj, oc * sizeof(float))) != cudaSuccess ||
+          (e = cudaMalloc(&o.oskip, oc * sizeof(float2))) != cudaSuccess)
+        return cuda_fail(e, "object majorant allocation");
+      g.maj = o.omaj;
+      g.skip = o.oskip;
+      tmp_cells = std::max(tmp_cells, oc);
+    }
+  }
+  if ((e = cudaMalloc(&s->skip_tmp, 3 * tmp_cells * sizeof(float))) != cudaSuccess)
+    return cuda_fail(e, "skip scratch allocation");
   return GPSS_OK;
 }
 
@@ -346,6 +378,13 @@ extern "C" gpss_status gpss_scene_set_surface_flight(gpss_scene s, int enable) {
   if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
   if (enable != 0 && enable != 1) { set_error("enable must be 0 or 1"); return GPSS_ERR_INVALID_ARG; }
   s->lin_flight = enable != 0;
+  return GPSS_OK;
+}
+
+extern "C" gpss_status gpss_scene_set_object_grids(gpss_scene s, int enable) {
+  if (!s) { set_error("null scene"); return GPSS_ERR_INVALID_ARG; }
+  if (enable != 0 && enable != 1) { set_error("enable must be 0 or 1"); return GPSS_ERR_INVALID_ARG; }
+  s->object_grids = enable != 0;
   return GPSS_OK;
 }
 

@@ -240,7 +240,7 @@ __global__ void k_eval_tr(const SceneDev S, int n, const float* org, const float
 }
 
 // Ratio tracking with the renderer's majorant traversal and extinction.
-__global__ void k_estimate_tr(const SceneDev S, int n, const float* org, const float* dir, const float* tmax,
+__global__ void k_estimate_tr(const __grid_constant__ SceneDev S, int n, const float* org, const float* dir, const float* tmax,
                               int samples, uint64_t seed, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -252,9 +252,11 @@ __global__ void k_estimate_tr(const SceneDev S, int n, const float* org, const f
     rng.init(seed, (uint32_t)i, (uint32_t)s);
     rng.start(0, kPurposeNee);
     Walk w;
+    int gid;
     float T = 1.0f;
-    if (walk_begin(S.mg, o, d, tmax[i], w)) {
-      for (float tau = -__logf(rng.next()); walk_advance(S.mg, S.obj[0], o, d, w, tau, cells) == kWalkHit;
+    if (trace_begin<true>(S, S.og, o, d, tmax[i], w, gid)) {
+      for (float tau = -__logf(rng.next());
+           trace_advance<true, true, true>(S, S.og, o, d, tmax[i], w, gid, tau, cells) == kWalkHit;
            tau = -__logf(rng.next())) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);
@@ -267,7 +269,7 @@ __global__ void k_estimate_tr(const SceneDev S, int n, const float* org, const f
 }
 
 // Delta-tracking free-flight distance (the renderer's flight loop without scattering).
-__global__ void k_free_flight(const SceneDev S, int n, const float* org, const float* dir, int samples,
+__global__ void k_free_flight(const __grid_constant__ SceneDev S, int n, const float* org, const float* dir, int samples,
                               uint64_t seed, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -278,9 +280,11 @@ __global__ void k_free_flight(const SceneDev S, int n, const float* org, const f
     rng.init(seed, (uint32_t)i, (uint32_t)s);
     rng.start(0, kPurposeFlight);
     Walk w;
+    int gid;
     float t_hit = INFINITY;
-    if (walk_begin(S.mg, o, d, INFINITY, w)) {
-      for (float tau = -__logf(rng.next()); walk_advance(S.mg, S.obj[0], o, d, w, tau, cells) == kWalkHit;
+    if (trace_begin<true>(S, S.og, o, d, INFINITY, w, gid)) {
+      for (float tau = -__logf(rng.next());
+           trace_advance<true, true, true>(S, S.og, o, d, INFINITY, w, gid, tau, cells) == kWalkHit;
            tau = -__logf(rng.next())) {
         const V3 x = fma3(w.t, d, o);
         const float st = scene_sigma_t(S, x, d);

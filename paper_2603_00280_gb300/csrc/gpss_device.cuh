@@ -98,7 +98,11 @@ struct LightDev {
 struct SceneDev {
   int n_objs;
   ObjectDev obj[kMaxObjects];
-  MajorantDev mg;
+  MajorantDev mg;          // over the union of the boxes (majorants of all objects added)
+  // Per-object traversal (split = 1, scenes of several objects): og[k] is object k's own
+  // majorant grid over its box, at its node spacing, with its local majorants.
+  int split;
+  MajorantDev og[kMaxObjects];
   LightDev light;
 };
 
@@ -604,7 +608,8 @@ __device__ __forceinline__ void beckmann_frame(V3 d, V3 g, float alpha, V3& z, f
 // of its visible-normal density.
 __device__ __forceinline__ float beckmann_vis_den(V3 wi, V3 z, float a) {
   const float ci = fmaxf(dot(wi, z), 0.0f);
-  const float si = sqrtf(fmaxf(0.0f, 1.0f - ci * ci));
+  const V3 wxz = cross(wi, z);
+  const float si = sqrtf(dot(wxz, wxz));  // no cancellation near the axis
   if (si <= 0.0f) return ci;
   const float ac = ci / (a * si);
   return 0.5f * ci * (1.0f + erff(ac)) + a * si * expf(-ac * ac) * (0.5f * kInvSqrtPi);
@@ -634,7 +639,11 @@ __device__ __forceinline__ V3 beckmann_sample_vis(V3 wi, V3 z, float a, float u1
   onb(z, t1, t2);
   V3 ws = normalize(v3(a * dot(wi, t1), a * dot(wi, t2), dot(wi, z)));
   const float ct = ws.z;
-  const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+  // sin from the tangential components: sqrt(1 - ct^2) cancels near the axis (ct rounded
+  // to 1 - 2^-24 gives 3.5e-4 for a true 1e-7), and the slope rotation below would then
+  // shrink every slope toward 0 -- a rough proposal about -d (a zero mean gradient) met
+  // this on a share of its samples and rendered 30% bright
+  const float st = sqrtf(ws.x * ws.x + ws.y * ws.y);
   float cphi = 1.0f, sphi = 0.0f;
   if (st > 1e-7f) {
     cphi = ws.x / st;
@@ -788,7 +797,21 @@ __device__ __forceinline__ bool phase_sample_mix(const Mix& mx, float sd, V3 d, 
   const float pdf_m = hf ? hf_pdf_m(d, m, f, alpha, sd) : mix_pdf_m(mx, d, m);
   if (!(pdf_m > 0.0f)) return false;
   w_over_F = ndf_field(m, f, alpha) * fabsf(dm) / (sd * pdf_m);
-  pdf = pdf_m / (4.0f * fabsf(dm));
+  // The pdf for the MIS weight of this direction is evaluated from d2 as the NEE side
+  // evaluates it (half vector normalize(d2 - d)), so that the two weights of every
+  // direction add to 1.  For m near grazing, d2 is close to d and the half vector
+  // recomputed from d2 is not m (cancellation): the sample's own pdf_m then differs
+  // from the NEE side's value, and mixing the two biased the estimate (a zero-gradient
+  // fog, whose Beckmann proposal is very rough, rendered 30% bright).  The weight
+  // w_over_F keeps the sample's own pdf_m, the density it was drawn from.
+  pdf = 0.0f;
+  V3 h = d2 - d;
+  const float hl2 = dot(h, h);
+  if (hl2 > 0.0f) {
+    h = rsqrtf(hl2) * h;
+    const float dh = dot(d, h);
+    if (dh < 0.0f) pdf = (hf ? hf_pdf_m(d, h, f, alpha, sd) : mix_pdf_m(mx, d, h)) / (4.0f * fabsf(dh));
+  }
   return isfinite(w_over_F);
 }
 
@@ -1311,9 +1334,11 @@ __device__ __forceinline__ int cell_index(float p, float gmin, float inv_cell, i
   return min(max((int)floorf((p - gmin) * inv_cell), 0), dims - 1);
 }
 
-__device__ __forceinline__ bool walk_begin(const MajorantDev& g, V3 o, V3 d, float tmax, Walk& w) {
+// Starts a walk of grid g along the ray over [tmin, tmax] clipped to the grid's box;
+// false when that is empty.
+__device__ __forceinline__ bool walk_begin(const MajorantDev& g, V3 o, V3 d, float tmin, float tmax, Walk& w) {
   const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
-  float t0 = 0.0f, t1 = tmax;
+  float t0 = tmin, t1 = tmax;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float gmax = g.gmin[a] + g.cell[a] * g.dims[a];
@@ -1419,6 +1444,113 @@ __device__ __forceinline__ int walk_advance(const MajorantDev& g, const ObjectDe
         w.cy = cell_index(fmaf(w.t, d.y, o.y), g.gmin[1], g.inv_cell[1], g.dims[1]);
       }
     }
+  }
+  return kWalkExit;
+}
+
+// ---------------------------------------------------------------- traversal of a scene
+// A scene of several objects (SceneDev::split) is walked interval by interval: the
+// faces of the objects' boxes cut the ray; an interval inside exactly one box walks that
+// object's own grid (og: its node spacing, its local majorants), an interval inside
+// several boxes walks the union grid (their majorants added), and intervals in no box
+// are skipped.  The optical-depth budget tau carries from one interval to the next, so
+// the tentative collisions are those of one delta-tracking walk against a piecewise
+// majorant (unbiased, as with any majorant).  The union grid alone has the resolution of
+// the finest grid over the whole union box, which coarsens it (brick doubling below
+// 64 Mi cells) where the objects' own spacings differ.  Other scenes walk the union grid
+// (a single object's own).
+
+// [a, b]: the ray's parameter range inside the object's box (b < a when it misses).
+__device__ __forceinline__ void box_span(const ObjectDev& ob, V3 o, V3 d, float& a, float& b) {
+  const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  a = -INFINITY;
+  b = INFINITY;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (dd[k] == 0.0f) {
+      if (oo[k] < ob.bmin[k] || oo[k] > ob.bmax[k]) b = -INFINITY;
+    } else {
+      const float inv = 1.0f / dd[k];
+      float t0 = (ob.bmin[k] - oo[k]) * inv, t1 = (ob.bmax[k] - oo[k]) * inv;
+      if (t0 > t1) {
+        const float tmp = t0;
+        t0 = t1;
+        t1 = tmp;
+      }
+      a = fmaxf(a, t0);
+      b = fminf(b, t1);
+    }
+  }
+}
+
+// The first non-empty traversal interval at or after t (below tmax): walk w started on
+// its grid, gid = the object whose box alone covers it, or -1 (several: the union
+// grid).  False when no box lies ahead.  og: the objects' grids (S.og, or a copy of it
+// in shared memory, which the walk reads with a per-lane index at every step).
+__device__ __forceinline__ bool trace_interval(const SceneDev& S, const MajorantDev* og, V3 o, V3 d, float t, float tmax,
+                                               Walk& w, int& gid) {
+  for (int it = 0; it <= 2 * kMaxObjects; ++it) {  // each pass moves t past one box face
+    float t_next = tmax;
+    int n_in = 0, who = 0;
+    for (int k = 0; k < S.n_objs; ++k) {
+      float a, b;
+      box_span(S.obj[k], o, d, a, b);
+      if (!(b > a) || b <= t) continue;
+      if (a <= t) {
+        ++n_in;
+        who = k;
+        t_next = fminf(t_next, b);
+      } else {
+        t_next = fminf(t_next, a);
+      }
+    }
+    if (!(t < t_next)) return false;
+    if (n_in > 0) {
+      gid = n_in == 1 ? who : -1;
+      if (walk_begin(gid < 0 ? S.mg : og[gid], o, d, t, t_next, w)) return true;
+    }
+    t = t_next;
+  }
+  return false;
+}
+
+// Traversal kinds of the path kernels (template parameter TRAV), as bits: kTravLocal
+// compiles local majorants in (a thin object), kTravSplit the per-object intervals
+// (several objects).  A kernel of kind k serves every scene whose kind is a subset of k.
+enum : int { kTravGrid = 0, kTravLocal = 1, kTravSplit = 2, kTravSplitLocal = 3 };
+
+__host__ __device__ inline int trav_of(const SceneDev& S) {
+  int k = kTravGrid;
+  if (S.split) {
+    k |= kTravSplit;
+    for (int i = 0; i < S.n_objs; ++i)
+      if (S.og[i].hot > 0.0f) k |= kTravLocal;
+  } else if (S.mg.hot > 0.0f) {
+    k |= kTravLocal;
+  }
+  return k;
+}
+
+// Starts the traversal of the ray over [0, tmax].
+template <bool SPLIT>
+__device__ __forceinline__ bool trace_begin(const SceneDev& S, const MajorantDev* og, V3 o, V3 d, float tmax, Walk& w,
+                                            int& gid) {
+  gid = -1;
+  if (SPLIT && S.split) return trace_interval(S, og, o, d, 0.0f, tmax, w, gid);
+  return walk_begin(S.mg, o, d, 0.0f, tmax, w);
+}
+
+// Advances the traversal to the next tentative collision (kWalkHit: w.t and w.sbar set)
+// or to the end of the ray (kWalkExit), consuming tau.  SPLIT compiles the per-object
+// intervals in (with LOCAL: objects' grids may have local majorants).
+template <bool LOCAL, bool SPLIT, bool GEN>
+__device__ __forceinline__ int trace_advance(const SceneDev& S, const MajorantDev* og, V3 o, V3 d, float tmax, Walk& w,
+                                             int& gid, float& tau, uint32_t& steps) {
+  for (int it = 0; it <= 2 * kMaxObjects + 1; ++it) {
+    const bool own = SPLIT && gid >= 0;
+    if (walk_advance<LOCAL, GEN>(own ? og[gid] : S.mg, S.obj[own ? gid : 0], o, d, w, tau, steps) == kWalkHit)
+      return kWalkHit;
+    if (!SPLIT || !S.split || !trace_interval(S, og, o, d, w.t_end, tmax, w, gid)) return kWalkExit;
   }
   return kWalkExit;
 }

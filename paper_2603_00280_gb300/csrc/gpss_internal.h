@@ -39,6 +39,11 @@ struct ObjectHost {
   float length_scale_b = 0.0f, length_scale_n = 0.0f;  // resolved (l_t where unset)
   float* cscale = nullptr;   // device correlation-scale factors (nodes), or null
   float* tangent = nullptr;  // device tangent field (3 planes of nodes), or null
+  bool thin = false;         // sigma_min below the grid spacing (local majorants pay)
+  // the object's own majorant grid (scenes of several objects): geometry, majorants, skip
+  MajorantDev og{};
+  float* omaj = nullptr;
+  float2* oskip = nullptr;
   bool anisotropic() const {
     return length_scale_b != length_scale || length_scale_n != length_scale || tangent != nullptr;
   }
@@ -56,13 +61,14 @@ struct gpss_scene_s {
   gpss::MajorantDev mg{};
   float* maj = nullptr;            // device majorant grid (fine level)
   float2* skip = nullptr;          // device skip grid (M_r, r) per majorant cell
-  float* skip_tmp = nullptr;       // 3 x cells scratch for the skip build
+  float* skip_tmp = nullptr;       // 3 x cells scratch for the skip build (largest grid)
   int skip_levels = 5;             // radii 1, 2, ..., 2^(levels-1)
   float kappa = 0.5f;              // expected majorant depth allowed per skip
   int shade_min = 24;              // lanes a warp gathers before shading real vertices
   float hot = 4.0f;                // local-majorant threshold (0 = off; single-object scenes)
   bool lin_flight = false;         // surface-limit analytic flight in local pieces (opt-in)
   bool thin = false;               // some object's sigma_min < its grid spacing (local majorants pay)
+  bool object_grids = false;       // several objects: per-object traversal on their own grids (opt-in)
   int brick = 1;                   // majorant cell = brick x finest field cell
   // scratch owned by the scene
   unsigned long long* counters = nullptr;   // kCntNum u64 + work cursor
@@ -100,9 +106,16 @@ bool camera_dev(const gpss_camera* c, CameraDev* out);
 
 // kernels (launch wrappers)
 uint64_t path_fingerprint(const gpss_camera* cam, const gpss_render_opts* o, uint64_t scene_version);
+// Forward render; with path_radiance (the per-path radiance an adjoint replays) it runs
+// the adjoint's kernel in its recording mode instead of the forward kernel.
 cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_render_opts& o, float* image,
                           float* sqsum, float* path_radiance, unsigned long long* counters, int grid,
                           int block, int shade_min, cudaStream_t st);
+struct PathArgs;
+struct AdjOut;
+cudaError_t launch_adjoint_kernel(const SceneDev& S, const CameraDev& C, const PathArgs& P, float* image, float* sqsum,
+                                  float* path_radiance, unsigned long long* counters, const AdjOut& A, int device,
+                                  cudaStream_t cs);
 int render_block_size();
 int render_grid_size(int device, int block);
 

@@ -1,8 +1,10 @@
-// path_kernel.cuh -- the persistent path kernel k_path<ADJ, LOCAL, GEN>:
+// path_kernel.cuh -- the persistent path kernel k_path<ADJ, TRAV, GEN>:
 //   ADJ = false  forward render (film accumulation);
 //   ADJ = true   path-replay adjoint: the same paths, traced from the same random
 //                numbers by the same code, with gradient scattering added;
-//   LOCAL        local majorants compiled in (scenes with thin objects);
+//   TRAV         the traversal compiled in (trav_of): the union majorant grid alone,
+//                with local majorants (a thin single object), or per-object intervals
+//                (several objects; gpss_device.cuh, trace_advance);
 //   GEN          height-field objects and anisotropic / non-stationary kernels
 //                compiled in (otherwise every object is an isotropic stationary GPSS
 //                and the kind and kernel dispatch folds away).
@@ -84,6 +86,11 @@ struct AdjOut {
   float* d_cs;            // d correlation-scale factor per node, or null
   long long node_off[kMaxObjects];  // object k's first node in d_mv and d_cs (objects in order)
   long long alb_off[kMaxObjects];   // object k's first albedo value in d_alb (channels x nodes each)
+  // record = 1: the forward pass whose per-path radiance the adjoint replays, run by the
+  // adjoint's own kernel with no gradient (d_image unused): film and per-path radiance
+  // as a forward render.  The replay then executes the same machine code with the same
+  // random numbers, so its decisions match the recorded ones bit for bit.
+  int record;
 };
 
 // Per-lane work counters, reduced per warp at the end of the kernel.
@@ -262,6 +269,8 @@ __device__ __forceinline__ float adj_vertex(const ObjectDev& ob, int k, V3 x, V3
 // ---------------------------------------------------------------- per-lane path state
 struct Lane {
   bool active, waiting, begin, cont, walk_ok;
+  int gid;     // the grid of the traversal interval (trace_advance)
+  bool vgrad;  // adjoint: waiting for the vertex gradient (shadow pre-pass done), not for shading
   long long pidx;
   uint32_t pixel;
   int job;
@@ -280,25 +289,67 @@ struct Lane {
 };
 
 __device__ __forceinline__ void lane_init(Lane& s) {
-  s.active = s.waiting = s.begin = s.cont = s.walk_ok = false;
+  s.active = s.waiting = s.begin = s.cont = s.walk_ok = s.vgrad = false;
+  s.gid = -1;
   s.pidx = 0;
   s.pixel = 0;
   s.job = 0;
 }
 
-// Starts path `pidx` (= sample * npix + pixel) of a render; returns false when the
+// The order of a render's paths.  The image is cut into kTile x kTile pixel tiles, taken
+// in row-major order, and all samples of one tile come before the next tile (samples
+// outer, pixels inner); the pixels outside the full tiles (a right and a bottom strip,
+// when a side is not a multiple of kTile) follow, samples outer.  The resident lanes
+// then hold the paths of a few neighbouring tiles, whose camera rays and first vertices
+// read the same field cells (L2 reuse on grids larger than L2).  A path keeps its
+// (pixel, sample), hence its random numbers: the order changes only the order of the
+// film's float sums.
+constexpr int kTile = 16;
+
+__device__ __forceinline__ void path_of(long long pidx, int width, int height, int spp, uint32_t& pixel, int& sample) {
+  const int tx = width / kTile, ty = height / kTile;
+  const long long per_tile = (long long)kTile * kTile * spp;
+  const long long full = per_tile * tx * ty;
+  if (pidx < full) {
+    const long long tile = pidx / per_tile;
+    const long long r = pidx - tile * per_tile;
+    sample = (int)(r / (kTile * kTile));
+    const int q = (int)(r - (long long)sample * (kTile * kTile));
+    const int py = (int)(tile / tx) * kTile + q / kTile, px = (int)(tile % tx) * kTile + q % kTile;
+    pixel = (uint32_t)py * (uint32_t)width + (uint32_t)px;
+    return;
+  }
+  const long long rest = (long long)width * height - (long long)tx * ty * (kTile * kTile);  // > 0 here
+  const long long r = pidx - full;
+  sample = (int)(r / rest);
+  int k = (int)(r - (long long)sample * rest);
+  const int rw = width - tx * kTile, rh = ty * kTile;  // the right strip is rw x rh pixels
+  if (k < rw * rh) {
+    pixel = (uint32_t)(k / rw) * (uint32_t)width + (uint32_t)(tx * kTile + k % rw);
+    return;
+  }
+  k -= rw * rh;
+  pixel = (uint32_t)(rh + k / width) * (uint32_t)width + (uint32_t)(k % width);
+}
+
+// Starts path `pidx` (in the order of path_of) of a render; returns false when the
 // adjoint has nothing to do for it (no gradient flows through its pixel).
 template <bool ADJ>
 __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const PathArgs& P, const AdjOut& A,
                                            long long pidx) {
   s.pidx = pidx;
-  const int sample = (int)(pidx / P.npix);
-  s.pixel = (uint32_t)(pidx - (long long)sample * P.npix);
+  int sample;
+  path_of(pidx, C.width, C.height, P.spp, s.pixel, sample);
   if constexpr (ADJ) {
-    s.gpix = v3(A.d_image[3 * s.pixel] * P.inv_spp, A.d_image[3 * s.pixel + 1] * P.inv_spp,
-                A.d_image[3 * s.pixel + 2] * P.inv_spp);
-    s.Ltot = v3(A.L_path[3 * pidx], A.L_path[3 * pidx + 1], A.L_path[3 * pidx + 2]);
-    if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) return false;
+    if (A.record) {
+      s.gpix = v3(0.0f, 0.0f, 0.0f);
+      s.Ltot = v3(0.0f, 0.0f, 0.0f);
+    } else {
+      s.gpix = v3(A.d_image[3 * s.pixel] * P.inv_spp, A.d_image[3 * s.pixel + 1] * P.inv_spp,
+                  A.d_image[3 * s.pixel + 2] * P.inv_spp);
+      s.Ltot = v3(A.L_path[3 * pidx], A.L_path[3 * pidx + 1], A.L_path[3 * pidx + 2]);
+      if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) return false;
+    }
   }
   s.rng.init(P.seed, s.pixel, (uint32_t)sample);
   s.rng.start(0, kPurposeCamera);
@@ -313,6 +364,7 @@ __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const Pa
   s.rng.start(0, kPurposeFlight);
   s.begin = true;
   s.waiting = false;
+  s.vgrad = false;
   s.active = true;
   return true;
 }
@@ -324,8 +376,12 @@ template <bool GEN>
 __device__ __forceinline__ void adj_vertex_done(Lane& s, const SceneDev& S, const AdjOut& A, V3 wl, float Tfin,
                                                 LaneCounters& c) {
   const V3 x = s.o;
-  const V3 F = fetch_albedo(S.obj[s.kobj], x);
   const V3 Ck = v3(s.pend.x * Tfin, s.pend.y * Tfin, s.pend.z * Tfin);
+  if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) {  // recording: no gradient
+    s.L = s.L + Ck;
+    return;
+  }
+  const V3 F = fetch_albedo(S.obj[s.kobj], x);
   const V3 after = s.Ltot - s.L - Ck;
   const float Wnee = dot(s.gpix, Ck);
   const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
@@ -348,10 +404,48 @@ __device__ __forceinline__ bool lane_continue(Lane& s) {
   return false;
 }
 
+// Ends the path at the lane's next step: with walk_ok = false and beta = 0 the step
+// treats it as an escaped flight that adds nothing.
+__device__ __forceinline__ void lane_end_at_next_step(Lane& s) {
+  s.mode = kFlight;
+  s.walk_ok = false;
+  s.begin = false;
+  s.beta = v3(0.0f, 0.0f, 0.0f);
+}
+
+// Adjoint, with the warp's shading (the vertex gradient is long, divergent code: taken
+// in the traversal loop it would run for one lane at a time): the gradient of the vertex
+// whose shadow pre-pass found T_fin, then the gradient pass of the same shadow ray (its
+// random numbers replayed from the start of the NEE stream) if it carries any.
+template <bool GEN>
+__device__ __forceinline__ void lane_vertex_grad(Lane& s, const SceneDev& S, const AdjOut& A, LaneCounters& c) {
+  s.waiting = false;
+  s.vgrad = false;
+  adj_vertex_done<GEN>(s, S, A, s.d, s.Tfin, c);
+  if (s.Tfin > 0.0f && dot(s.gpix, s.pend) != 0.0f) {
+    s.mode = kShadow;
+    s.T = 1.0f;
+    s.begin = true;
+    s.rng.start((uint32_t)(s.bounce - 1), kPurposeNee);
+    if (S.light.kind != kLightDirectional) {
+      s.rng.next();
+      s.rng.next();
+    }
+    return;
+  }
+  if (lane_continue(s)) lane_end_at_next_step(s);
+}
+
 // Shading of a real vertex: phase sampling, next-event estimation setup.
 template <bool ADJ, bool GEN>
 __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                            LaneCounters& c) {
+  if constexpr (ADJ) {
+    if (s.vgrad) {
+      lane_vertex_grad<GEN>(s, S, A, c);
+      return;
+    }
+  }
   const bool env = S.light.kind != kLightDirectional;
   s.waiting = false;
   const V3 x = fma3(s.w.t, s.d, s.o);
@@ -424,12 +518,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   if (s.cont) {
     lane_continue(s);
   } else {
-    // no shadow ray and no continuation: with walk_ok = false and beta = 0 the
-    // step treats the lane as an escaped flight that adds nothing
-    s.mode = kFlight;
-    s.walk_ok = false;
-    s.begin = false;
-    s.beta = v3(0.0f, 0.0f, 0.0f);
+    lane_end_at_next_step(s);  // no shadow ray and no continuation
   }
 }
 
@@ -438,18 +527,19 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
 // that only computes the ray's final transmittance T_fin, then -- when the vertex's
 // NEE contribution pend T_fin carries gradient -- the gradient pass (kShadow) whose
 // tentative collisions scatter -d sigma_t/(majorant - sigma_t) with weight <g, pend> T_fin.
-template <bool ADJ, bool LOCAL, bool GEN>
-__device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
-                                          LaneCounters& c) {
+template <bool ADJ, int TRAV, bool GEN>
+__device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const MajorantDev* og, const PathArgs& P,
+                                          const AdjOut& A, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
+  constexpr bool LOCAL = (TRAV & kTravLocal) != 0, SPLIT = (TRAV & kTravSplit) != 0;
   if (s.begin) {
-    s.walk_ok = walk_begin(S.mg, s.o, s.d, INFINITY, s.w);
+    s.walk_ok = trace_begin<SPLIT>(S, og, s.o, s.d, INFINITY, s.w, s.gid);
     s.begin = false;
   }
   bool hit = false;
   if (s.walk_ok) {
     float tau = -__logf(s.rng.next());
-    hit = walk_advance<LOCAL, GEN>(S.mg, S.obj[0], s.o, s.d, s.w, tau, c.cells) == kWalkHit;
+    hit = trace_advance<LOCAL, SPLIT, GEN>(S, og, s.o, s.d, INFINITY, s.w, s.gid, tau, c.cells) == kWalkHit;
   }
   if (hit) {
     ++s.events;
@@ -458,15 +548,16 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
       ++c.shadow;
       if (!ratio_step(s.T, sigma_t_at<GEN>(S, x, s.d), s.w.sbar, s.rng)) s.walk_ok = false;
     } else if (ADJ && S.n_objs == 1) {
-      // extinction and its partials from one evaluation (the decision uses the same value)
+      // the extinction by the forward's expression (the recording pass and the replay run
+      // this same code), its partials only where a gradient is scattered
       float st = 0.0f, cs = 1.0f, k_adj = 0.0f;
       bool real = false;
-      DSig ds;
+      Field f;
       const bool inobj = inside(S.obj[0], x);
       if (inobj) {
-        const Field f = fetch_k<GEN>(S.obj[0], x);
-        ds = dsigma_t(S.obj[0], f, s.d);
-        st = ds.st;
+        f = fetch_k<GEN>(S.obj[0], x);
+        const Local l = local_of(S.obj[0], f);
+        st = l.rho * projected_area(s.d, f, l.alpha);
         cs = f.cs;
       }
       if (s.mode == kFlight) {
@@ -485,8 +576,10 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
         if (Wn != 0.0f) k_adj = -Wn / (s.w.sbar - st);
         if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;
       }
-      if (inobj && k_adj != 0.0f)
+      if (inobj && k_adj != 0.0f) {
+        const DSig ds = dsigma_t(S.obj[0], f, s.d);
         c.acc_l[0] += adj_scatter_event<GEN>(S.obj[0], 0, x, real ? dlog_of(ds) : ds, k_adj, cs, A, c.nonfinite);
+      }
     } else {
       const float st = sigma_t_at<GEN>(S, x, s.d);
       float k_adj = 0.0f;  // adjoint (several objects): weight of every object's d sigma_t here
@@ -532,22 +625,12 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
   }
   if constexpr (ADJ) {
     if (s.mode == kShadowPre) {
-      // T_fin known: the vertex's gradient; then the gradient pass of the same shadow ray
-      // (its random numbers replayed from the start of the NEE stream) if it carries any
-      const float Tfin = s.T;
-      adj_vertex_done<GEN>(s, S, A, s.d, Tfin, c);
-      if (Tfin > 0.0f && dot(s.gpix, s.pend) != 0.0f) {
-        s.Tfin = Tfin;
-        s.mode = kShadow;
-        s.T = 1.0f;
-        s.begin = true;
-        s.rng.start((uint32_t)(s.bounce - 1), kPurposeNee);
-        if (env) {
-          s.rng.next();
-          s.rng.next();
-        }
-        return false;
-      }
+      // T_fin known: the lane waits for the warp's shading, which takes the vertex's
+      // gradient and starts the gradient pass (lane_vertex_grad)
+      s.Tfin = s.T;
+      s.vgrad = true;
+      s.waiting = true;
+      return false;
     }
   } else {
     s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
@@ -559,8 +642,8 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Path
 template <bool ADJ>
 __device__ __forceinline__ void lane_finish(Lane& s, const PathArgs& P, float* __restrict__ image,
                                             float* __restrict__ sqsum, float* __restrict__ path_radiance,
-                                            LaneCounters& c) {
-  if constexpr (!ADJ) {
+                                            bool record, LaneCounters& c) {
+  if (!ADJ || record) {
     float* px = image + 3 * (size_t)s.pixel;
     atomicAdd(px + 0, s.L.x * P.inv_spp);
     atomicAdd(px + 1, s.L.y * P.inv_spp);
@@ -647,12 +730,13 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
 //   take(s, need, lane)  new paths for the lanes in `need` (warp-collective);
 //   exhausted()          no new path is left (warp-uniform);
 //   scene(s), args(s)    the scene and options of a path (its job's, in a batch);
+//   grids(s)             the objects' own majorant grids of that scene (per-object traversal);
 //   finish(s, c)         film accumulation / replay check of a finished path;
 //   adj()                the adjoint's buffers.
 // Each iteration: (1) lanes without a path take new ones; (2) once at least shade_min
 // lanes wait at a real vertex (or no other lane can step) the warp shades them
 // together; (3) every other lane with a path advances it by one tentative collision.
-template <bool ADJ, bool LOCAL, bool GEN, class W>
+template <bool ADJ, int TRAV, bool GEN, class W>
 __device__ __forceinline__ void path_loop(W& src, int shade_min, LaneCounters& c) {
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
@@ -671,7 +755,7 @@ __device__ __forceinline__ void path_loop(W& src, int shade_min, LaneCounters& c
       if (s.waiting) lane_shade<ADJ, GEN>(s, src.scene(s), src.args(s), src.adj(), c);
     }
     if (!s.active || s.waiting) continue;
-    if (lane_step<ADJ, LOCAL, GEN>(s, src.scene(s), src.args(s), src.adj(), c)) src.finish(s, c);
+    if (lane_step<ADJ, TRAV, GEN>(s, src.scene(s), src.grids(s), src.args(s), src.adj(), c)) src.finish(s, c);
   }
 }
 
@@ -687,6 +771,7 @@ struct RenderSource {
   float* sqsum;
   float* path_radiance;
   unsigned long long* cursor;
+  const MajorantDev* og;  // the objects' grids, copied to shared memory
   WarpCursor wc;
   __device__ __forceinline__ void take(Lane& s, unsigned need, int lane) {
     const long long mine = warp_take(wc, !s.active, need, lane, cursor, P.total, kChunk);
@@ -694,22 +779,32 @@ struct RenderSource {
   }
   __device__ __forceinline__ bool exhausted() const { return wc.exhausted || wc.next >= P.total; }
   __device__ __forceinline__ const SceneDev& scene(const Lane&) const { return S; }
+  __device__ __forceinline__ const MajorantDev* grids(const Lane&) const { return og; }
   __device__ __forceinline__ const PathArgs& args(const Lane&) const { return P; }
   __device__ __forceinline__ const AdjOut& adj() const { return A; }
-  __device__ __forceinline__ void finish(Lane& s, LaneCounters& c) { lane_finish<ADJ>(s, P, image, sqsum, path_radiance, c); }
+  __device__ __forceinline__ void finish(Lane& s, LaneCounters& c) {
+    lane_finish<ADJ>(s, P, image, sqsum, path_radiance, A.record != 0, c);
+  }
 };
 
-// LOCAL: the scene uses local majorants (MajorantDev::hot > 0).  GEN: some object is a
+// TRAV: the scene's traversal (trav_of).  GEN: some object is a
 // height-field macrofacet or has an anisotropic or non-stationary kernel (the adjoint
 // supports the isotropic GPSS, stationary or with a correlation-scale grid).
-template <bool ADJ, bool LOCAL, bool GEN>
+template <bool ADJ, int TRAV, bool GEN>
 __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 8)
     k_path(const __grid_constant__ SceneDev S, const __grid_constant__ CameraDev C, const __grid_constant__ PathArgs P,
            float* __restrict__ image, float* __restrict__ sqsum, float* __restrict__ path_radiance,
            unsigned long long* __restrict__ counters, const __grid_constant__ AdjOut A) {
-  RenderSource<ADJ> src{S, C, P, A, image, sqsum, path_radiance, counters + kCntNum, WarpCursor{0, 0, false}};
+  // the objects' grids in shared memory: the per-object walk reads them with a per-lane
+  // object index at every step (a parameter-space read would be an indexed constant load)
+  __shared__ MajorantDev s_og[kMaxObjects];
+  if constexpr ((TRAV & kTravSplit) != 0) {
+    if (threadIdx.x < kMaxObjects) s_og[threadIdx.x] = S.og[threadIdx.x];
+    __syncthreads();
+  }
+  RenderSource<ADJ> src{S, C, P, A, image, sqsum, path_radiance, counters + kCntNum, s_og, WarpCursor{0, 0, false}};
   LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, {0.0f, 0.0f, 0.0f, 0.0f}, 0};
-  path_loop<ADJ, LOCAL, GEN>(src, P.shade_min, c);
+  path_loop<ADJ, TRAV, GEN>(src, P.shade_min, c);
   flush_counters(c, counters, ADJ ? A.d_l : nullptr, S.n_objs);
 }
 

@@ -9,7 +9,7 @@ int render_block_size() { return kPathBlock; }
 int render_grid_size(int device, int block) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<false, false, false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_path<false, kTravGrid, false>, block, 0);
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
 }
@@ -28,15 +28,33 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
   P.shade_min = shade_min;
   P.exact_vndf = (o.flags & GPSS_FLAG_EXACT_VNDF) ? 1 : 0;
   AdjOut A{};
-  const bool local = S.mg.hot > 0.0f, gen = scene_general(S);
-  if (local && gen)
-    k_path<false, true, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
-  else if (local)
-    k_path<false, true, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
-  else if (gen)
-    k_path<false, false, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
-  else
-    k_path<false, false, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+  if (path_radiance) {
+    // kept for an adjoint: recorded by the adjoint's own kernel (bit-identical replay)
+    A.record = 1;
+    int device = 0;
+    cudaGetDevice(&device);
+    return launch_adjoint_kernel(S, C, P, image, sqsum, path_radiance, counters, A, device, st);
+  }
+  const int trav = trav_of(S);
+  if (scene_general(S)) {
+    if (trav == kTravSplitLocal)
+      k_path<false, kTravSplitLocal, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else if (trav == kTravSplit)
+      k_path<false, kTravSplit, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else if (trav == kTravLocal)
+      k_path<false, kTravLocal, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else
+      k_path<false, kTravGrid, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+  } else {
+    if (trav == kTravSplitLocal)
+      k_path<false, kTravSplitLocal, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else if (trav == kTravSplit)
+      k_path<false, kTravSplit, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else if (trav == kTravLocal)
+      k_path<false, kTravLocal, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else
+      k_path<false, kTravGrid, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+  }
   return cudaGetLastError();
 }
 

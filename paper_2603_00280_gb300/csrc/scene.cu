@@ -201,32 +201,41 @@ gpss_status scene_upload(gpss_scene s, const gpss_object_desc* objs, int n, cuda
     o.sigma_min = std::sqrt(vmin);
     float h = INFINITY;
     for (int a = 0; a < 3; ++a) h = std::fmin(h, (o.bmax[a] - o.bmin[a]) / (float)(o.n[a] - 1));
-    if (h > o.sigma_min) s->thin = true;
+    o.thin = h > o.sigma_min;
+    if (o.thin) s->thin = true;
   }
   return GPSS_OK;
 }
 
-gpss_status build_skip(gpss_scene s, cudaStream_t st) {
-  const int nx = s->mg.dims[0], ny = s->mg.dims[1], nz = s->mg.dims[2];
+// Skip grid of one majorant grid g (majorants maj, result skip) with the scene's levels
+// and kappa; s->skip_tmp holds 3 x the cells of the largest grid.
+static void build_skip_grid(gpss_scene s, const MajorantDev& g, const float* maj, float2* skip, cudaStream_t st) {
+  const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
   const long long n = (long long)nx * ny * nz;
   const int nb = blocks_for((size_t)n, 256);
-  k_skip_init<<<nb, 256, 0, st>>>(s->maj, s->skip, n);
+  k_skip_init<<<nb, 256, 0, st>>>(maj, skip, n);
   if (s->skip_levels > 0) {
     float* P = s->skip_tmp;
     float* Q = P + n;
     float* R = Q + n;
-    const float hmin = fminf(fminf(s->mg.cell[0], s->mg.cell[1]), s->mg.cell[2]);
+    const float hmin = fminf(fminf(g.cell[0], g.cell[1]), g.cell[2]);
     const float limit = s->kappa / hmin;  // M_r * r * h_min <= kappa
     for (int lev = 0; lev < s->skip_levels; ++lev) {
       const int r = 1 << lev;
       const int off = lev == 0 ? 1 : r >> 1;
-      const float* src = lev == 0 ? s->maj : P;
+      const float* src = lev == 0 ? maj : P;
       k_max_axis<<<nb, 256, 0, st>>>(src, Q, nx, ny, nz, 0, off, lev == 0);
       k_max_axis<<<nb, 256, 0, st>>>(Q, R, nx, ny, nz, 1, off, lev == 0);
       k_max_axis<<<nb, 256, 0, st>>>(R, P, nx, ny, nz, 2, off, lev == 0);
-      k_skip_select<<<nb, 256, 0, st>>>(P, s->skip, n, r, limit);
+      k_skip_select<<<nb, 256, 0, st>>>(P, skip, n, r, limit);
     }
   }
+}
+
+gpss_status build_skip(gpss_scene s, cudaStream_t st) {
+  build_skip_grid(s, s->mg, s->maj, s->skip, st);
+  if (s->n_objs > 1)
+    for (int k = 0; k < s->n_objs; ++k) build_skip_grid(s, s->obj[k].og, s->obj[k].omaj, s->obj[k].oskip, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "skip grid kernels");
   return GPSS_OK;
@@ -262,6 +271,13 @@ SceneDev scene_dev(const gpss_scene_s* s) {
   d.mg.skip = s->skip;
   d.mg.hot = (s->n_objs == 1 && s->thin) ? s->hot : 0.0f;
   d.mg.lin = s->lin_flight ? 1 : 0;
+  d.split = (s->n_objs > 1 && s->object_grids) ? 1 : 0;
+  if (s->n_objs > 1)
+    for (int k = 0; k < s->n_objs; ++k) {
+      d.og[k] = s->obj[k].og;
+      d.og[k].hot = s->obj[k].thin ? s->hot : 0.0f;
+      d.og[k].lin = s->lin_flight ? 1 : 0;
+    }
   d.light = s->light;
   return d;
 }
@@ -270,6 +286,16 @@ gpss_status build_majorant(gpss_scene s, cudaStream_t st) {
   const SceneDev S = scene_dev(s);
   const long long ncell = (long long)s->mg.dims[0] * s->mg.dims[1] * s->mg.dims[2];
   k_majorant<<<blocks_for((size_t)ncell, 128), 128, 0, st>>>(S, s->mg, s->maj);
+  if (s->n_objs > 1)
+    for (int k = 0; k < s->n_objs; ++k) {
+      // object k alone over its own grid
+      SceneDev Sk = S;
+      Sk.n_objs = 1;
+      Sk.obj[0] = S.obj[k];
+      const MajorantDev& g = s->obj[k].og;
+      const long long oc = (long long)g.dims[0] * g.dims[1] * g.dims[2];
+      k_majorant<<<blocks_for((size_t)oc, 128), 128, 0, st>>>(Sk, g, s->obj[k].omaj);
+    }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "majorant kernel");
   return build_skip(s, st);

@@ -79,6 +79,7 @@ _SIGS = {
     "gpss_scene_set_traversal": [_VP, _I, _F, _VP],
     "gpss_scene_set_schedule": [_VP, _I],
     "gpss_scene_set_local_majorant": [_VP, _F],
+    "gpss_scene_set_object_grids": [_VP, _I],
     "gpss_scene_set_surface_flight": [_VP, _I],
     "gpss_scene_majorant": [_VP, ctypes.POINTER(_I), _VP, _VP],
     "gpss_render": [_VP, ctypes.POINTER(Camera), ctypes.POINTER(RenderOpts), _VP, _VP, ctypes.POINTER(Stats), _VP],
@@ -265,6 +266,9 @@ class Scene:
 
     def set_schedule(self, shade_min: int = 24):
         _call("gpss_scene_set_schedule", self.handle, int(shade_min))
+
+    def set_object_grids(self, enable: bool = True):
+        _call("gpss_scene_set_object_grids", self.handle, 1 if enable else 0)
 
     def set_local_majorant(self, hot: float = 4.0):
         _call("gpss_scene_set_local_majorant", self.handle, float(hot))

@@ -144,7 +144,10 @@ def test_phase_eval_parity(which, request):
 
 def test_phase_sampler_weights_and_histogram(hetero):
     """GPU samples: the returned weight and pdf equal the oracle's p/pdf at the
-    GPU's own sampled direction, and the sample histogram follows the pdf."""
+    GPU's own sampled direction, and the sample histogram follows the pdf.  The
+    returned pdf is the mixture pdf evaluated from the sampled direction (the value the
+    renderer's MIS weights use, as on the NEE side): 0 where the half vector re-derived
+    from an FP32 direction almost equal to d no longer faces -d."""
     sc, G, O = hetero
     x0 = C.dyadic_points(1, 21, -0.3, 0.3)[0]
     d0 = C.unit_dirs(1, 22)[0]
@@ -154,11 +157,11 @@ def test_phase_sampler_weights_and_histogram(hetero):
     ds = np.tile(d0, (n, 1))
     d2, w, pdf = gpss.sample_phase(G, 0, xs, ds, u)
     d2, w, pdf = d2.cpu().numpy(), w.cpu().numpy(), pdf.cpu().numpy()
-    assert np.all(pdf > 0)
+    assert np.all(pdf >= 0) and np.mean(pdf > 0) > 0.999
     # away from grazing half-vectors, where re-deriving m from the FP32-rounded d2 cancels
     mh = d2 - d0
     mh /= np.linalg.norm(mh, axis=1, keepdims=True)
-    keep = np.nonzero(np.abs(mh @ d0) > 0.05)[0][:300]
+    keep = np.nonzero((np.abs(mh @ d0) > 0.05) & (pdf > 0))[0][:300]
     op, opdf = oracle.phase_eval(O, 0, xs[keep].astype(np.float64), ds[keep].astype(np.float64),
                                  d2[keep].astype(np.float64))
     np.testing.assert_allclose(pdf[keep], opdf, rtol=2e-4)
