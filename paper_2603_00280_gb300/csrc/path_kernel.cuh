@@ -550,7 +550,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
     } else if (ADJ && S.n_objs == 1) {
       // the extinction by the forward's expression (the recording pass and the replay run
       // this same code), its partials only where a gradient is scattered
-      float st = 0.0f, cs = 1.0f, k_adj = 0.0f;
+      float st = 0.0f, k_adj = 0.0f;
       bool real = false;
       Field f;
       const bool inobj = inside(S.obj[0], x);
@@ -558,7 +558,6 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
         f = fetch_k<GEN>(S.obj[0], x);
         const Local l = local_of(S.obj[0], f);
         st = l.rho * projected_area(s.d, f, l.alpha);
-        cs = f.cs;
       }
       if (s.mode == kFlight) {
         real = s.rng.next() * s.w.sbar < st;
@@ -578,7 +577,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
       }
       if (inobj && k_adj != 0.0f) {
         const DSig ds = dsigma_t(S.obj[0], f, s.d);
-        c.acc_l[0] += adj_scatter_event<GEN>(S.obj[0], 0, x, real ? dlog_of(ds) : ds, k_adj, cs, A, c.nonfinite);
+        c.acc_l[0] += adj_scatter_event<GEN>(S.obj[0], 0, x, real ? dlog_of(ds) : ds, k_adj, f.cs, A, c.nonfinite);
       }
     } else {
       const float st = sigma_t_at<GEN>(S, x, s.d);
@@ -626,8 +625,14 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
   if constexpr (ADJ) {
     if (s.mode == kShadowPre) {
       // T_fin known: the lane waits for the warp's shading, which takes the vertex's
-      // gradient and starts the gradient pass (lane_vertex_grad)
+      // gradient and starts the gradient pass (lane_vertex_grad); a recording path (no
+      // gradient) has neither and goes on at once (scheduling only: the path's arithmetic
+      // and random numbers are the same either way)
       s.Tfin = s.T;
+      if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) {
+        s.L = s.L + v3(s.pend.x * s.Tfin, s.pend.y * s.Tfin, s.pend.z * s.Tfin);
+        return lane_continue(s);
+      }
       s.vgrad = true;
       s.waiting = true;
       return false;
