@@ -281,10 +281,13 @@ gpss_status gpss_render_adjoint(gpss_scene s, const gpss_camera* cam, const gpss
  * scene in gpss_render's order: 16x16-pixel tiles, all samples of a tile
  * together) that the resident threads consume in chunks through one atomic
  * cursor; each path carries the index of its scene in a device table of (scene,
- * camera, options, film pointers).  Scene i's paths and random numbers are exactly
- * those of gpss_render(scenes[i], cams[i], opts[i]): the images agree with separate
- * renders up to the order of the film's float additions.  No counterpart in the
- * paper (an execution-model feature).
+ * camera, options, film pointers).  Scene i's path indices and random numbers are
+ * those of gpss_render(scenes[i], cams[i], opts[i]), so the batch estimates each
+ * image with the separate render's per-pixel error; the two kernels are separate
+ * compilations and may round a rare decision differently (approximate FP32
+ * division), so the images agree up to the film's summation order except in a few
+ * pixels.  Repeated batch launches agree exactly.  No counterpart in the paper (an
+ * execution-model feature).
  *
  *   scenes, cams, opts: n entries each (copied; the scenes must stay alive and
  *     unchanged in layout while the batch exists, and live on the current device;

@@ -98,9 +98,10 @@ template <int BLOCK, int TRAV, bool GEN>
 __global__ void __maxnreg__(96) k_batch(const JobDev* __restrict__ jobs, const long long* __restrict__ begins,
                                         int n_jobs, long long total, int chunk, int shade_min,
                                         unsigned long long* __restrict__ counters) {
+  __shared__ LaneCold s_cold[BLOCK];
   BatchSource src{jobs, begins, n_jobs, total, chunk, counters + kCntNum, AdjOut{}, WarpCursor{0, 0, false}};
   LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, {0.0f, 0.0f, 0.0f, 0.0f}, 0};
-  path_loop<false, TRAV, GEN>(src, shade_min, c);
+  path_loop<false, TRAV, GEN>(src, shade_min, s_cold, c);
   flush_counters(c, counters, nullptr, 0);
 }
 

@@ -267,17 +267,33 @@ __device__ __forceinline__ float adj_vertex(const ObjectDev& ob, int k, V3 x, V3
 }
 
 // ---------------------------------------------------------------- per-lane path state
+// The part of a lane's state that the traversal loop does not touch -- throughput,
+// radiance, the pending NEE contribution, the next direction, weight and pdf, the bounce,
+// pixel and path index: read and written at vertices and at the ends of rays only.  In the
+// forward kernels it lives in shared memory (one record per thread, 21 words: an odd
+// stride, so a warp's accesses to one field hit 32 different banks) instead of registers,
+// which at the 64-register cap spilled it to local memory, whose reloads missed L1 under
+// the field gathers' traffic (5% less frame time).  The adjoint kernel, at 128 registers
+// without spills, keeps it in registers (in shared memory it ran 4% slower).
+struct LaneCold {
+  V3 beta, L, pend, d_next, beta_next;
+  float prev_pdf, pdf_next;
+  int bounce;
+  uint32_t pixel;
+  uint32_t pidx_lo, pidx_hi;
+};
+static_assert(sizeof(LaneCold) == 21 * 4, "LaneCold: 21 words (odd stride)");
+
 struct Lane {
   bool active, waiting, begin, cont, walk_ok;
   int gid;     // the grid of the traversal interval (trace_advance)
   bool vgrad;  // adjoint: waiting for the vertex gradient (shadow pre-pass done), not for shading
-  long long pidx;
-  uint32_t pixel;
+  LaneCold* c;  // the lane's record in shared memory
   int job;
   Rng rng;
-  V3 o, d, beta, L, pend, d_next, beta_next;
-  float prev_pdf, T, pdf_next;
-  int bounce, mode;
+  V3 o, d;
+  float T;
+  int mode;
   uint32_t events;
   Walk w;
   // adjoint state: the path's forward radiance, dLoss/dpixel / spp, the current
@@ -291,8 +307,8 @@ struct Lane {
 __device__ __forceinline__ void lane_init(Lane& s) {
   s.active = s.waiting = s.begin = s.cont = s.walk_ok = s.vgrad = false;
   s.gid = -1;
-  s.pidx = 0;
-  s.pixel = 0;
+  s.c->pidx_lo = s.c->pidx_hi = 0u;
+  s.c->pixel = 0;
   s.job = 0;
 }
 
@@ -337,28 +353,29 @@ __device__ __forceinline__ void path_of(long long pidx, int width, int height, i
 template <bool ADJ>
 __device__ __forceinline__ bool lane_start(Lane& s, const CameraDev& C, const PathArgs& P, const AdjOut& A,
                                            long long pidx) {
-  s.pidx = pidx;
+  s.c->pidx_lo = (uint32_t)pidx;
+  s.c->pidx_hi = (uint32_t)((unsigned long long)pidx >> 32);
   int sample;
-  path_of(pidx, C.width, C.height, P.spp, s.pixel, sample);
+  path_of(pidx, C.width, C.height, P.spp, s.c->pixel, sample);
   if constexpr (ADJ) {
     if (A.record) {
       s.gpix = v3(0.0f, 0.0f, 0.0f);
       s.Ltot = v3(0.0f, 0.0f, 0.0f);
     } else {
-      s.gpix = v3(A.d_image[3 * s.pixel] * P.inv_spp, A.d_image[3 * s.pixel + 1] * P.inv_spp,
-                  A.d_image[3 * s.pixel + 2] * P.inv_spp);
+      s.gpix = v3(A.d_image[3 * s.c->pixel] * P.inv_spp, A.d_image[3 * s.c->pixel + 1] * P.inv_spp,
+                  A.d_image[3 * s.c->pixel + 2] * P.inv_spp);
       s.Ltot = v3(A.L_path[3 * pidx], A.L_path[3 * pidx + 1], A.L_path[3 * pidx + 2]);
       if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) return false;
     }
   }
-  s.rng.init(P.seed, s.pixel, (uint32_t)sample);
+  s.rng.init(P.seed, s.c->pixel, (uint32_t)sample);
   s.rng.start(0, kPurposeCamera);
   const float jx = s.rng.next(), jy = s.rng.next();
-  camera_ray(C, (int)(s.pixel % (uint32_t)C.width), (int)(s.pixel / (uint32_t)C.width), jx, jy, s.o, s.d);
-  s.beta = v3(1.0f, 1.0f, 1.0f);
-  s.L = v3(0.0f, 0.0f, 0.0f);
-  s.prev_pdf = -1.0f;
-  s.bounce = 0;
+  camera_ray(C, (int)(s.c->pixel % (uint32_t)C.width), (int)(s.c->pixel / (uint32_t)C.width), jx, jy, s.o, s.d);
+  s.c->beta = v3(1.0f, 1.0f, 1.0f);
+  s.c->L = v3(0.0f, 0.0f, 0.0f);
+  s.c->prev_pdf = -1.0f;
+  s.c->bounce = 0;
   s.mode = kFlight;
   s.events = 0;
   s.rng.start(0, kPurposeFlight);
@@ -376,30 +393,30 @@ template <bool GEN>
 __device__ __forceinline__ void adj_vertex_done(Lane& s, const SceneDev& S, const AdjOut& A, V3 wl, float Tfin,
                                                 LaneCounters& c) {
   const V3 x = s.o;
-  const V3 Ck = v3(s.pend.x * Tfin, s.pend.y * Tfin, s.pend.z * Tfin);
+  const V3 Ck = v3(s.c->pend.x * Tfin, s.c->pend.y * Tfin, s.c->pend.z * Tfin);
   if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) {  // recording: no gradient
-    s.L = s.L + Ck;
+    s.c->L = s.c->L + Ck;
     return;
   }
   const V3 F = fetch_albedo(S.obj[s.kobj], x);
-  const V3 after = s.Ltot - s.L - Ck;
+  const V3 after = s.Ltot - s.c->L - Ck;
   const float Wnee = dot(s.gpix, Ck);
   const float Wph = s.cont ? dot(s.gpix, after) : 0.0f;
   const V3 ac = v3(F.x > 0.0f ? s.gpix.x * (Ck.x + (s.cont ? after.x : 0.0f)) / F.x : 0.0f,
                    F.y > 0.0f ? s.gpix.y * (Ck.y + (s.cont ? after.y : 0.0f)) / F.y : 0.0f,
                    F.z > 0.0f ? s.gpix.z * (Ck.z + (s.cont ? after.z : 0.0f)) / F.z : 0.0f);
-  c.acc_l[s.kobj] += adj_vertex<GEN>(S.obj[s.kobj], s.kobj, x, s.d_in, wl, s.d_next, Wnee, Wph, ac, A, c.nonfinite);
-  s.L = s.L + Ck;
+  c.acc_l[s.kobj] += adj_vertex<GEN>(S.obj[s.kobj], s.kobj, x, s.d_in, wl, s.c->d_next, Wnee, Wph, ac, A, c.nonfinite);
+  s.c->L = s.c->L + Ck;
 }
 
 // After the shadow ray (or in place of it): the next flight, or the end of the path.
 __device__ __forceinline__ bool lane_continue(Lane& s) {
   if (!s.cont) return true;
   s.mode = kFlight;
-  s.d = s.d_next;
-  s.beta = s.beta_next;
-  s.prev_pdf = s.pdf_next;
-  s.rng.start((uint32_t)s.bounce, kPurposeFlight);
+  s.d = s.c->d_next;
+  s.c->beta = s.c->beta_next;
+  s.c->prev_pdf = s.c->pdf_next;
+  s.rng.start((uint32_t)s.c->bounce, kPurposeFlight);
   s.begin = true;
   return false;
 }
@@ -410,7 +427,7 @@ __device__ __forceinline__ void lane_end_at_next_step(Lane& s) {
   s.mode = kFlight;
   s.walk_ok = false;
   s.begin = false;
-  s.beta = v3(0.0f, 0.0f, 0.0f);
+  s.c->beta = v3(0.0f, 0.0f, 0.0f);
 }
 
 // Adjoint, with the warp's shading (the vertex gradient is long, divergent code: taken
@@ -422,11 +439,11 @@ __device__ __forceinline__ void lane_vertex_grad(Lane& s, const SceneDev& S, con
   s.waiting = false;
   s.vgrad = false;
   adj_vertex_done<GEN>(s, S, A, s.d, s.Tfin, c);
-  if (s.Tfin > 0.0f && dot(s.gpix, s.pend) != 0.0f) {
+  if (s.Tfin > 0.0f && dot(s.gpix, s.c->pend) != 0.0f) {
     s.mode = kShadow;
     s.T = 1.0f;
     s.begin = true;
-    s.rng.start((uint32_t)(s.bounce - 1), kPurposeNee);
+    s.rng.start((uint32_t)(s.c->bounce - 1), kPurposeNee);
     if (S.light.kind != kLightDirectional) {
       s.rng.next();
       s.rng.next();
@@ -457,7 +474,7 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     // several objects: the real collision's factor is the chosen object's sigma_t,k (the
     // choice probability sigma_t,k/sigma_t is held fixed), known only now
     if (S.n_objs > 1) {
-      const float W = dot(s.gpix, s.Ltot - s.L);
+      const float W = dot(s.gpix, s.Ltot - s.c->L);
       if (W != 0.0f) {
         const DSig ds = dsigma_t(S.obj[k], f, s.d);
         if (ds.st > 0.0f) c.acc_l[k] += adj_scatter_event<GEN>(S.obj[k], k, x, dlog_of(ds), W, f.cs, A, c.nonfinite);
@@ -467,17 +484,17 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
     s.kobj = k;
   }
   s.o = x;
-  s.cont = s.bounce + 1 < P.max_bounces;
+  s.cont = s.c->bounce + 1 < P.max_bounces;
   float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
   if (s.cont) {
-    s.rng.start((uint32_t)s.bounce, kPurposePhase);
+    s.rng.start((uint32_t)s.c->bounce, kPurposePhase);
     u0 = s.rng.next();
     u1 = s.rng.next();
     u2 = s.rng.next();
   } else {
     ++c.trunc;
   }
-  s.rng.start((uint32_t)s.bounce, kPurposeNee);
+  s.rng.start((uint32_t)s.c->bounce, kPurposeNee);
   V3 wl, Le;
   if (!env) {
     wl = v3(S.light.dir[0], S.light.dir[1], S.light.dir[2]);
@@ -494,9 +511,9 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   if (s.cont) {
     const PhaseSample& ps = vs.next;
     if (ps.ok) {
-      s.d_next = ps.d2;
-      s.beta_next = v3(s.beta.x * F.x * ps.w_over_F, s.beta.y * F.y * ps.w_over_F, s.beta.z * F.z * ps.w_over_F);
-      s.pdf_next = ps.pdf;
+      s.c->d_next = ps.d2;
+      s.c->beta_next = v3(s.c->beta.x * F.x * ps.w_over_F, s.c->beta.y * F.y * ps.w_over_F, s.c->beta.z * F.z * ps.w_over_F);
+      s.c->pdf_next = ps.pdf;
     } else {
       s.cont = false;
     }
@@ -504,8 +521,8 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   const PhaseEval& pe = vs.nee;
   const float lw = env ? power_heuristic(kInv4Pi, pe.pdf) * (4.0f * kPi) : 1.0f;
   const float scale = pe.p_over_F * lw;
-  s.pend = v3(s.beta.x * F.x * scale * Le.x, s.beta.y * F.y * scale * Le.y, s.beta.z * F.z * scale * Le.z);
-  ++s.bounce;
+  s.c->pend = v3(s.c->beta.x * F.x * scale * Le.x, s.c->beta.y * F.y * scale * Le.y, s.c->beta.z * F.z * scale * Le.z);
+  ++s.c->bounce;
   if (scale > 0.0f) {
     // the shadow ray; the adjoint first replays it for its final transmittance (pre-pass)
     s.mode = ADJ ? kShadowPre : kShadow;
@@ -561,7 +578,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
       }
       if (s.mode == kFlight) {
         real = s.rng.next() * s.w.sbar < st;
-        const float W = dot(s.gpix, s.Ltot - s.L);
+        const float W = dot(s.gpix, s.Ltot - s.c->L);
         if (W != 0.0f) k_adj = real ? W : -W / (s.w.sbar - st);  // real: times d ln sigma_t
         if (real) {
           ++c.vert;
@@ -571,7 +588,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
         }
       } else {
         ++c.shadow;
-        const float Wn = dot(s.gpix, s.pend) * s.Tfin;
+        const float Wn = dot(s.gpix, s.c->pend) * s.Tfin;
         if (Wn != 0.0f) k_adj = -Wn / (s.w.sbar - st);
         if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;
       }
@@ -586,7 +603,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
         const bool real = s.rng.next() * s.w.sbar < st;
         if constexpr (ADJ) {
           // a real collision's gradient waits for the object choice at shading
-          const float W = dot(s.gpix, s.Ltot - s.L);
+          const float W = dot(s.gpix, s.Ltot - s.c->L);
           if (!real && W != 0.0f) k_adj = -W / (s.w.sbar - st);
         }
         if (real) {
@@ -598,7 +615,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
       } else {
         ++c.shadow;
         if constexpr (ADJ) {
-          const float Wn = dot(s.gpix, s.pend) * s.Tfin;
+          const float Wn = dot(s.gpix, s.c->pend) * s.Tfin;
           if (Wn != 0.0f) k_adj = -Wn / (s.w.sbar - st);
         }
         if (!ratio_step(s.T, st, s.w.sbar, s.rng)) s.walk_ok = false;  // T = 0: the shadow ray ends here
@@ -617,8 +634,8 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
   if (s.mode == kFlight) {
     if (env) {
       const V3 Le = env_radiance(S.light, s.d);
-      const float wm = s.prev_pdf < 0.0f ? 1.0f : power_heuristic(s.prev_pdf, kInv4Pi);
-      s.L = v3(fmaf(s.beta.x * Le.x, wm, s.L.x), fmaf(s.beta.y * Le.y, wm, s.L.y), fmaf(s.beta.z * Le.z, wm, s.L.z));
+      const float wm = s.c->prev_pdf < 0.0f ? 1.0f : power_heuristic(s.c->prev_pdf, kInv4Pi);
+      s.c->L = v3(fmaf(s.c->beta.x * Le.x, wm, s.c->L.x), fmaf(s.c->beta.y * Le.y, wm, s.c->L.y), fmaf(s.c->beta.z * Le.z, wm, s.c->L.z));
     }
     return true;
   }
@@ -630,7 +647,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
       // and random numbers are the same either way)
       s.Tfin = s.T;
       if (s.gpix.x == 0.0f && s.gpix.y == 0.0f && s.gpix.z == 0.0f) {
-        s.L = s.L + v3(s.pend.x * s.Tfin, s.pend.y * s.Tfin, s.pend.z * s.Tfin);
+        s.c->L = s.c->L + v3(s.c->pend.x * s.Tfin, s.c->pend.y * s.Tfin, s.c->pend.z * s.Tfin);
         return lane_continue(s);
       }
       s.vgrad = true;
@@ -638,7 +655,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
       return false;
     }
   } else {
-    s.L = v3(fmaf(s.pend.x, s.T, s.L.x), fmaf(s.pend.y, s.T, s.L.y), fmaf(s.pend.z, s.T, s.L.z));
+    s.c->L = v3(fmaf(s.c->pend.x, s.T, s.c->L.x), fmaf(s.c->pend.y, s.T, s.c->L.y), fmaf(s.c->pend.z, s.T, s.c->L.z));
   }
   return lane_continue(s);
 }
@@ -649,25 +666,26 @@ __device__ __forceinline__ void lane_finish(Lane& s, const PathArgs& P, float* _
                                             float* __restrict__ sqsum, float* __restrict__ path_radiance,
                                             bool record, LaneCounters& c) {
   if (!ADJ || record) {
-    float* px = image + 3 * (size_t)s.pixel;
-    atomicAdd(px + 0, s.L.x * P.inv_spp);
-    atomicAdd(px + 1, s.L.y * P.inv_spp);
-    atomicAdd(px + 2, s.L.z * P.inv_spp);
+    float* px = image + 3 * (size_t)s.c->pixel;
+    atomicAdd(px + 0, s.c->L.x * P.inv_spp);
+    atomicAdd(px + 1, s.c->L.y * P.inv_spp);
+    atomicAdd(px + 2, s.c->L.z * P.inv_spp);
     if (sqsum) {
-      float* q = sqsum + 3 * (size_t)s.pixel;
-      atomicAdd(q + 0, s.L.x * s.L.x);
-      atomicAdd(q + 1, s.L.y * s.L.y);
-      atomicAdd(q + 2, s.L.z * s.L.z);
+      float* q = sqsum + 3 * (size_t)s.c->pixel;
+      atomicAdd(q + 0, s.c->L.x * s.c->L.x);
+      atomicAdd(q + 1, s.c->L.y * s.c->L.y);
+      atomicAdd(q + 2, s.c->L.z * s.c->L.z);
     }
     if (path_radiance) {
-      float* pr = path_radiance + 3 * s.pidx;
-      pr[0] = s.L.x;
-      pr[1] = s.L.y;
-      pr[2] = s.L.z;
+      const long long pidx = (long long)(((unsigned long long)s.c->pidx_hi << 32) | s.c->pidx_lo);
+      float* pr = path_radiance + 3 * pidx;
+      pr[0] = s.c->L.x;
+      pr[1] = s.c->L.y;
+      pr[2] = s.c->L.z;
     }
   } else {
     // the replay must reproduce the forward path; count any that does not
-    const V3 e = s.L - s.Ltot;
+    const V3 e = s.c->L - s.Ltot;
     const float tol = 1e-3f * (fabsf(s.Ltot.x) + fabsf(s.Ltot.y) + fabsf(s.Ltot.z)) + 1e-6f;
     if (fabsf(e.x) + fabsf(e.y) + fabsf(e.z) > tol) ++c.abort;
   }
@@ -742,10 +760,16 @@ __device__ __forceinline__ void flush_counters(const LaneCounters& c, unsigned l
 // lanes wait at a real vertex (or no other lane can step) the warp shades them
 // together; (3) every other lane with a path advances it by one tentative collision.
 template <bool ADJ, int TRAV, bool GEN, class W>
-__device__ __forceinline__ void path_loop(W& src, int shade_min, LaneCounters& c) {
+__device__ __forceinline__ void path_loop(W& src, int shade_min, LaneCold* cold, LaneCounters& c) {
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
   Lane s;
+  LaneCold own;  // the adjoint kernel (128 registers, no spills) keeps the record in registers
+  if constexpr (ADJ) {
+    s.c = &own;
+  } else {
+    s.c = cold + threadIdx.x;
+  }
   lane_init(s);
   for (;;) {
     const unsigned need = __ballot_sync(FULL, !s.active);
@@ -807,9 +831,10 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 8)
     if (threadIdx.x < kMaxObjects) s_og[threadIdx.x] = S.og[threadIdx.x];
     __syncthreads();
   }
+  __shared__ LaneCold s_cold[kPathBlock];
   RenderSource<ADJ> src{S, C, P, A, image, sqsum, path_radiance, counters + kCntNum, s_og, WarpCursor{0, 0, false}};
   LaneCounters c{0, 0, 0, 0, 0, 0, 0, 0, {0.0f, 0.0f, 0.0f, 0.0f}, 0};
-  path_loop<ADJ, TRAV, GEN>(src, P.shade_min, c);
+  path_loop<ADJ, TRAV, GEN>(src, P.shade_min, s_cold, c);
   flush_counters(c, counters, ADJ ? A.d_l : nullptr, S.n_objs);
 }
 
