@@ -48,26 +48,32 @@ __global__ void k_split_grad(const float2* __restrict__ mv, float* __restrict__ 
 cudaError_t launch_adjoint_kernel(const SceneDev& S, const CameraDev& C, const PathArgs& P, float* image, float* sqsum,
                                   float* path_radiance, unsigned long long* counters, const AdjOut& A, int device,
                                   cudaStream_t cs) {
-  const int trav = trav_of(S);
+  int trav = trav_of(S);
+  if (trav != kTravGrid && trav != kTravLocal && trav != kTravMulti && trav != kTravSplit) trav = kTravSplitLocal;
   const bool gen = scene_general(S);
-  const void* fns[2][4] = {{(const void*)k_path<true, kTravGrid, false>, (const void*)k_path<true, kTravLocal, false>,
-                            (const void*)k_path<true, kTravSplit, false>, (const void*)k_path<true, kTravSplitLocal, false>},
+  const int slot = trav == kTravGrid ? 0 : trav == kTravLocal ? 1 : trav == kTravMulti ? 2 : trav == kTravSplit ? 3 : 4;
+  const void* fns[2][5] = {{(const void*)k_path<true, kTravGrid, false>, (const void*)k_path<true, kTravLocal, false>,
+                            (const void*)k_path<true, kTravMulti, false>, (const void*)k_path<true, kTravSplit, false>,
+                            (const void*)k_path<true, kTravSplitLocal, false>},
                            {(const void*)k_path<true, kTravGrid, true>, (const void*)k_path<true, kTravLocal, true>,
-                            (const void*)k_path<true, kTravSplit, true>, (const void*)k_path<true, kTravSplitLocal, true>}};
+                            (const void*)k_path<true, kTravMulti, true>, (const void*)k_path<true, kTravSplit, true>,
+                            (const void*)k_path<true, kTravSplitLocal, true>}};
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[gen ? 1 : 0][trav], kPathBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[gen ? 1 : 0][slot], kPathBlock, 0);
   const int g = sms * (per_sm > 0 ? per_sm : 1);
   float *im = image, *sq = sqsum, *pr = path_radiance;
   unsigned long long* ct = counters;
   if (gen) {
     if (trav == kTravSplitLocal) k_path<true, kTravSplitLocal, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
     else if (trav == kTravSplit) k_path<true, kTravSplit, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else if (trav == kTravMulti) k_path<true, kTravMulti, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
     else if (trav == kTravLocal) k_path<true, kTravLocal, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
     else k_path<true, kTravGrid, true><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
   } else {
     if (trav == kTravSplitLocal) k_path<true, kTravSplitLocal, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
     else if (trav == kTravSplit) k_path<true, kTravSplit, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
+    else if (trav == kTravMulti) k_path<true, kTravMulti, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
     else if (trav == kTravLocal) k_path<true, kTravLocal, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
     else k_path<true, kTravGrid, false><<<g, kPathBlock, 0, cs>>>(S, C, P, im, sq, pr, ct, A);
   }

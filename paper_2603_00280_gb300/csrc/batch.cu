@@ -135,10 +135,10 @@ static int grid_for_t(int block, int device) {
 }
 
 // The batch instances: the grid walk, local majorants, and per-object intervals with
-// local majorants (which serves every scene).
+// local majorants and several objects (which serves every scene).
 template <bool GEN>
 static int grid_for_g(int block, int trav, int device) {
-  if (trav & kTravSplit) return grid_for_t<kTravSplitLocal, GEN>(block, device);
+  if (trav & kTravSplit) return grid_for_t<kTravSplitLocal, GEN>(block, device);  // split or several objects
   if (trav == kTravLocal) return grid_for_t<kTravLocal, GEN>(block, device);
   return grid_for_t<kTravGrid, GEN>(block, device);
 }

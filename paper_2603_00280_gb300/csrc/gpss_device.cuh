@@ -1514,13 +1514,19 @@ __device__ __forceinline__ bool trace_interval(const SceneDev& S, const Majorant
   return false;
 }
 
-// Traversal kinds of the path kernels (template parameter TRAV), as bits: kTravLocal
-// compiles local majorants in (a thin object), kTravSplit the per-object intervals
-// (several objects).  A kernel of kind k serves every scene whose kind is a subset of k.
-enum : int { kTravGrid = 0, kTravLocal = 1, kTravSplit = 2, kTravSplitLocal = 3 };
+// Kinds of the path kernels (template parameter TRAV), as bits: kTravLocal compiles local
+// majorants in (a thin object), kTravSplitBit the per-object intervals, kTravMulti the code
+// of scenes of several objects (extinctions added, the scattering object chosen; without it
+// a kernel holds the single-object paths only, which keeps the adjoint's code smaller).  A
+// kernel of kind k serves every scene whose kind is a subset of k.
+enum : int {
+  kTravLocal = 1, kTravSplitBit = 2, kTravMulti = 4,
+  kTravGrid = 0, kTravSplit = kTravSplitBit | kTravMulti, kTravSplitLocal = kTravSplit | kTravLocal
+};
 
 __host__ __device__ inline int trav_of(const SceneDev& S) {
   int k = kTravGrid;
+  if (S.n_objs > 1) k |= kTravMulti;
   if (S.split) {
     k |= kTravSplit;
     for (int i = 0; i < S.n_objs; ++i)

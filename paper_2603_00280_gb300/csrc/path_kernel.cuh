@@ -125,10 +125,11 @@ __device__ __forceinline__ Field fetch_k(const ObjectDev& o, V3 x) {
 }
 
 
-// Total extinction at x (single object fast path; several objects add).
-template <bool GEN>
+// Total extinction at x (single object fast path; several objects add; MULTI = false:
+// the kernel serves single-object scenes only).
+template <bool GEN, bool MULTI>
 __device__ __forceinline__ float sigma_t_at(const SceneDev& S, V3 x, V3 d) {
-  if (S.n_objs == 1) {
+  if (!MULTI || S.n_objs == 1) {
     if (!inside(S.obj[0], x)) return 0.0f;
     const Field f = fetch_k<GEN>(S.obj[0], x);
     const Local l = local_of(S.obj[0], f);
@@ -454,7 +455,7 @@ __device__ __forceinline__ void lane_vertex_grad(Lane& s, const SceneDev& S, con
 }
 
 // Shading of a real vertex: phase sampling, next-event estimation setup.
-template <bool ADJ, bool GEN>
+template <bool ADJ, bool GEN, bool MULTI>
 __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const PathArgs& P, const AdjOut& A,
                                            LaneCounters& c) {
   if constexpr (ADJ) {
@@ -466,14 +467,15 @@ __device__ __forceinline__ void lane_shade(Lane& s, const SceneDev& S, const Pat
   const bool env = S.light.kind != kLightDirectional;
   s.waiting = false;
   const V3 x = fma3(s.w.t, s.d, s.o);
-  const int k = S.n_objs > 1 ? choose_object<GEN>(S, x, s.d, s.rng.next()) : 0;
+  const bool multi = MULTI && S.n_objs > 1;
+  const int k = multi ? choose_object<GEN>(S, x, s.d, s.rng.next()) : 0;
   const Field f = fetch_k<GEN>(S.obj[k], x);
   const float alpha = sqrtf(f.var) * f.as;  // the density rho is not needed for shading
   const V3 F = fetch_albedo(S.obj[k], x);
   if constexpr (ADJ) {
     // several objects: the real collision's factor is the chosen object's sigma_t,k (the
     // choice probability sigma_t,k/sigma_t is held fixed), known only now
-    if (S.n_objs > 1) {
+    if (multi) {
       const float W = dot(s.gpix, s.Ltot - s.c->L);
       if (W != 0.0f) {
         const DSig ds = dsigma_t(S.obj[k], f, s.d);
@@ -548,7 +550,8 @@ template <bool ADJ, int TRAV, bool GEN>
 __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const MajorantDev* og, const PathArgs& P,
                                           const AdjOut& A, LaneCounters& c) {
   const bool env = S.light.kind != kLightDirectional;
-  constexpr bool LOCAL = (TRAV & kTravLocal) != 0, SPLIT = (TRAV & kTravSplit) != 0;
+  constexpr bool LOCAL = (TRAV & kTravLocal) != 0, SPLIT = (TRAV & kTravSplitBit) != 0,
+                 MULTI = (TRAV & kTravMulti) != 0;
   if (s.begin) {
     s.walk_ok = trace_begin<SPLIT>(S, og, s.o, s.d, INFINITY, s.w, s.gid);
     s.begin = false;
@@ -563,8 +566,8 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
     const V3 x = fma3(s.w.t, s.d, s.o);
     if (ADJ && s.mode == kShadowPre) {
       ++c.shadow;
-      if (!ratio_step(s.T, sigma_t_at<GEN>(S, x, s.d), s.w.sbar, s.rng)) s.walk_ok = false;
-    } else if (ADJ && S.n_objs == 1) {
+      if (!ratio_step(s.T, sigma_t_at<GEN, MULTI>(S, x, s.d), s.w.sbar, s.rng)) s.walk_ok = false;
+    } else if (ADJ && (!MULTI || S.n_objs == 1)) {
       // the extinction by the forward's expression (the recording pass and the replay run
       // this same code), its partials only where a gradient is scattered
       float st = 0.0f, k_adj = 0.0f;
@@ -597,7 +600,7 @@ __device__ __forceinline__ bool lane_step(Lane& s, const SceneDev& S, const Majo
         c.acc_l[0] += adj_scatter_event<GEN>(S.obj[0], 0, x, real ? dlog_of(ds) : ds, k_adj, f.cs, A, c.nonfinite);
       }
     } else {
-      const float st = sigma_t_at<GEN>(S, x, s.d);
+      const float st = sigma_t_at<GEN, MULTI>(S, x, s.d);
       float k_adj = 0.0f;  // adjoint (several objects): weight of every object's d sigma_t here
       if (s.mode == kFlight) {
         const bool real = s.rng.next() * s.w.sbar < st;
@@ -781,7 +784,7 @@ __device__ __forceinline__ void path_loop(W& src, int shade_min, LaneCold* cold,
     }
     const unsigned wait_mask = __ballot_sync(FULL, s.waiting);
     if (wait_mask && (__popc(wait_mask) >= shade_min || wait_mask == act)) {
-      if (s.waiting) lane_shade<ADJ, GEN>(s, src.scene(s), src.args(s), src.adj(), c);
+      if (s.waiting) lane_shade<ADJ, GEN, (TRAV & kTravMulti) != 0>(s, src.scene(s), src.args(s), src.adj(), c);
     }
     if (!s.active || s.waiting) continue;
     if (lane_step<ADJ, TRAV, GEN>(s, src.scene(s), src.grids(s), src.args(s), src.adj(), c)) src.finish(s, c);
@@ -827,7 +830,7 @@ __global__ void __launch_bounds__(kPathBlock, ADJ ? 4 : 8)
   // the objects' grids in shared memory: the per-object walk reads them with a per-lane
   // object index at every step (a parameter-space read would be an indexed constant load)
   __shared__ MajorantDev s_og[kMaxObjects];
-  if constexpr ((TRAV & kTravSplit) != 0) {
+  if constexpr ((TRAV & kTravSplitBit) != 0) {
     if (threadIdx.x < kMaxObjects) s_og[threadIdx.x] = S.og[threadIdx.x];
     __syncthreads();
   }

@@ -35,12 +35,15 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
     cudaGetDevice(&device);
     return launch_adjoint_kernel(S, C, P, image, sqsum, path_radiance, counters, A, device, st);
   }
-  const int trav = trav_of(S);
+  int trav = trav_of(S);
+  if (trav != kTravGrid && trav != kTravLocal && trav != kTravMulti && trav != kTravSplit) trav = kTravSplitLocal;
   if (scene_general(S)) {
     if (trav == kTravSplitLocal)
       k_path<false, kTravSplitLocal, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
     else if (trav == kTravSplit)
       k_path<false, kTravSplit, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else if (trav == kTravMulti)
+      k_path<false, kTravMulti, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
     else if (trav == kTravLocal)
       k_path<false, kTravLocal, true><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
     else
@@ -50,6 +53,8 @@ cudaError_t launch_render(const SceneDev& S, const CameraDev& C, const gpss_rend
       k_path<false, kTravSplitLocal, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
     else if (trav == kTravSplit)
       k_path<false, kTravSplit, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
+    else if (trav == kTravMulti)
+      k_path<false, kTravMulti, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
     else if (trav == kTravLocal)
       k_path<false, kTravLocal, false><<<grid, block, 0, st>>>(S, C, P, image, sqsum, path_radiance, counters, A);
     else
