@@ -103,6 +103,7 @@ def test_calls_reject_null_and_invalid_arguments():
     assert L.gpss_scene_destroy(None) == 1
     assert L.gpss_scene_set_surface_flight(None, 1) == 1
     assert L.gpss_scene_set_local_majorant(None, 4.0) == 1
+    assert L.gpss_scene_set_object_grids(None, 1) == 1
     assert L.gpss_eval_local_piece(None, 1, buf, buf, buf, buf, buf, buf, buf, buf, buf, buf, None) == 1
     assert L.gpss_render_adjoint(None, ctypes.byref(cam), ctypes.byref(opts), buf, None, None, None, None, None,
                                  None, None) == 1
