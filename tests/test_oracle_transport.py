@@ -1,7 +1,8 @@
 """Pins of the oracle's transmittance and path tracer against closed forms:
 constant-mean and plane-mean transmittance (Eq. sm2tr with Eq.
 generalized_sigma_t), exact single scattering, a white furnace, and finite
-differences with common random numbers against an exact derivative."""
+differences with common random numbers against an exact derivative; and, on a tiny
+input, against a brute-force delta/ratio tracker with one global majorant."""
 import math
 
 import numpy as np
@@ -186,3 +187,108 @@ def test_exact_sampler_and_mixture_render_the_same_image():
     (a, sa, va), (b, sb, vb) = out["mixture"], out["vndf"]
     assert abs(a - b) < 4 * math.sqrt(sa * sa + sb * sb), (a, sa, b, sb)
     assert vb < 0.5 * va
+
+
+def _box_span(o, d, lo, hi):
+    """[t0, t1] of the ray o + t d inside the box [lo, hi] (t1 < t0 when it misses)."""
+    t0, t1 = 0.0, math.inf
+    for a in range(3):
+        if d[a] == 0.0:
+            if not (lo[a] <= o[a] <= hi[a]):
+                return 1.0, 0.0
+            continue
+        ta, tb = (lo[a] - o[a]) / d[a], (hi[a] - o[a]) / d[a]
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    return t0, t1
+
+
+def test_regular_tracking_agrees_with_naive_delta_tracking():
+    """Brute force on a tiny input (a 3x3x3-node grid, 4x4 pixels): the oracle's path
+    tracer (regular tracking: optical depth by quadrature, free-flight distance by root
+    finding, transmittance by quadrature) against a textbook one written here from the
+    oracle's point evaluations only -- delta tracking and ratio tracking against a single
+    global majorant, the exact visible-normal sampler, next-event estimation toward a
+    directional light at every vertex.  Both estimate the same image; they share no
+    tracking code."""
+    rng = np.random.default_rng(7)
+    lo, hi = np.array([-0.25, -0.25, -0.25]), np.array([0.25, 0.25, 0.25])
+    p = W.node_coords(lo, hi, (3, 3, 3))
+    mean = (W.sdf_sphere(p, (0.0, 0.0, 0.0), 0.15) + rng.uniform(-0.03, 0.03, p.shape[:3])).astype(np.float32)
+    var = rng.uniform(0.02 ** 2, 0.05 ** 2, p.shape[:3]).astype(np.float32)
+    l = 0.05
+    sc = {"objects": [W.make_object(mean, var, 0.8, lo, hi, l)],
+          "light": W.directional_light((0.3, -0.4, 1.0), 1.0)}
+    O = oracle.Scene(sc)
+    # global majorant: rho <= lambda(u_min)/sigma_lo with u_min the smallest mu/sigma the
+    # trilinear fields reach; sigma(d) = E[max(0, -d.g)] <= |grad mu|_max + (sigma_hi/l)/sqrt(2 pi)
+    m = mean.astype(np.float64)
+    s_lo, s_hi = math.sqrt(float(var.min())), math.sqrt(float(var.max()))
+    u_min = m.min() / (s_lo if m.min() < 0 else s_hi)
+    rho_max = oracle.inv_mills(u_min) / s_lo
+    h = (hi - lo) / 2.0
+    gmax = math.sqrt(sum((np.abs(np.diff(m, axis=2 - a)).max() / h[a]) ** 2 for a in range(3)))
+    sbar = 1.05 * rho_max * (gmax + (s_hi / l) / math.sqrt(2 * math.pi))
+    wl = np.array(sc["light"]["dir"])
+    cam = {"type": "ortho", "eye": (0.0, -1.0, 0.35), "look_at": (0.0, 0.0, 0.0), "up": (0.0, 0.0, 1.0),
+           "fov_y_deg": 40.0, "ortho_w": 0.45, "ortho_h": 0.45, "width": 4, "height": 4}
+    bounces = 3
+
+    def sig(x, d):
+        return float(oracle.sigma_t(O, x, d)[0])
+
+    def ratio_tracking(x, d):
+        _, t1 = _box_span(x, d, lo, hi)
+        T, t = 1.0, 0.0
+        while True:
+            t += -math.log(1.0 - rng.random()) / sbar
+            if t >= t1:
+                return T
+            s = sig(x + t * d, d)
+            assert s <= sbar
+            T *= 1.0 - s / sbar
+
+    def path(px, py):
+        o, d = oracle.camera_ray(cam, px, py, rng.random(), rng.random())
+        beta, L = 1.0, 0.0
+        for _ in range(bounces):
+            t0, t1 = _box_span(o, d, lo, hi)
+            if t1 <= t0:
+                return L
+            t, hit = t0, False
+            while True:
+                t += -math.log(1.0 - rng.random()) / sbar
+                if t >= t1:
+                    break
+                x = o + t * d
+                s = sig(x, d)
+                assert s <= sbar
+                if rng.random() * sbar < s:
+                    hit = True
+                    break
+            if not hit:
+                return L
+            pv, _ = oracle.phase_eval(O, 0, x, d, wl)
+            L += beta * pv[0, 0] * ratio_tracking(x, wl)
+            d2, w, _, ok = oracle.phase_sample_exact(O, 0, x, d, rng.random((1, 3)))
+            if not ok[0]:
+                return L
+            beta *= w[0, 0]
+            o, d = x, d2[0]
+        return L
+
+    n_naive = 160
+    naive = np.array([[[path(px, py) for _ in range(n_naive)] for px in range(4)] for py in range(4)])
+    nm, nse = naive.mean(2), naive.std(2, ddof=1) / math.sqrt(n_naive)
+    spp = 4096
+    s, s2, _ = oracle.render(O, cam, {"spp": spp, "max_bounces": bounces, "seed": 5, "sampler": "vndf"})
+    om = s[..., 0] / spp
+    ostd = np.sqrt(np.maximum(s2[..., 0] / spp - om * om, 0))
+    ose = ostd / math.sqrt(spp)
+    # a pixel whose few contributing paths the 160 naive samples miss shows a zero sample
+    # variance: its standard error is floored at the oracle's per-path spread
+    nse = np.maximum(nse, ostd / math.sqrt(n_naive))
+    z = (nm - om) / np.sqrt(nse ** 2 + ose ** 2 + 1e-30)
+    assert (om > 0).sum() >= 8, om
+    assert np.abs(z).max() < 4, (z, nm, om)
+    tot = (nm.sum() - om.sum()) / math.sqrt((nse ** 2).sum() + (ose ** 2).sum())
+    assert abs(tot) < 3, (tot, nm.sum(), om.sum())
