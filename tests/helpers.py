@@ -188,3 +188,20 @@ def slab_single_scatter_objects(d, wl, objects, irradiance=1.0, ztop=0.125, zbot
 
 def zscores(mean_a, se_a, mean_b, se_b=0.0):
     return (np.asarray(mean_a) - np.asarray(mean_b)) / np.sqrt(np.asarray(se_a) ** 2 + np.asarray(se_b) ** 2)
+
+
+def tiny_brute_force_scene():
+    """A 3x3x3-node heterogeneous GPSS (noisy sphere mean, random variance) lit by a
+    directional light, and a 4x4 orthographic camera: the brute-force input on which the
+    oracle's regular tracking is checked against a naive delta tracker, and the GPU
+    against the oracle."""
+    rng = np.random.default_rng(7)
+    lo, hi = np.array([-0.25, -0.25, -0.25]), np.array([0.25, 0.25, 0.25])
+    p = W.node_coords(lo, hi, (3, 3, 3))
+    mean = (W.sdf_sphere(p, (0.0, 0.0, 0.0), 0.15) + rng.uniform(-0.03, 0.03, p.shape[:3])).astype(np.float32)
+    var = rng.uniform(0.02 ** 2, 0.05 ** 2, p.shape[:3]).astype(np.float32)
+    sc = {"objects": [W.make_object(mean, var, 0.8, lo, hi, 0.05)],
+          "light": W.directional_light((0.3, -0.4, 1.0), 1.0)}
+    cam = {"type": "ortho", "eye": (0.0, -1.0, 0.35), "look_at": (0.0, 0.0, 0.0), "up": (0.0, 0.0, 1.0),
+           "fov_y_deg": 40.0, "ortho_w": 0.45, "ortho_h": 0.45, "width": 4, "height": 4}
+    return sc, cam, lo, hi

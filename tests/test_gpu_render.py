@@ -97,6 +97,14 @@ def test_zero_gradient_fog_parity(sampler):
     assert st["vertices"] > 0
 
 
+def test_tiny_brute_force_input_parity():
+    """The brute-force input on which the oracle's regular tracking is checked against a
+    naive delta tracker (3x3x3 nodes, 4x4 pixels, 3 bounces, directional light): the GPU
+    against the oracle."""
+    sc, cam, _, _ = H.tiny_brute_force_scene()
+    _parity(sc, cam, {"max_bounces": 3, "mix_R": 0.5}, orc_spp=4096, gpu_spp=65536)
+
+
 def test_sky_only_pixels_are_exact():
     """Rays that miss every object return the sky radiance exactly."""
     sc = C.dyadic_hetero(4)

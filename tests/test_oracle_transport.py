@@ -210,14 +210,10 @@ def test_regular_tracking_agrees_with_naive_delta_tracking():
     global majorant, the exact visible-normal sampler, next-event estimation toward a
     directional light at every vertex.  Both estimate the same image; they share no
     tracking code."""
-    rng = np.random.default_rng(7)
-    lo, hi = np.array([-0.25, -0.25, -0.25]), np.array([0.25, 0.25, 0.25])
-    p = W.node_coords(lo, hi, (3, 3, 3))
-    mean = (W.sdf_sphere(p, (0.0, 0.0, 0.0), 0.15) + rng.uniform(-0.03, 0.03, p.shape[:3])).astype(np.float32)
-    var = rng.uniform(0.02 ** 2, 0.05 ** 2, p.shape[:3]).astype(np.float32)
-    l = 0.05
-    sc = {"objects": [W.make_object(mean, var, 0.8, lo, hi, l)],
-          "light": W.directional_light((0.3, -0.4, 1.0), 1.0)}
+    sc, cam, lo, hi = H.tiny_brute_force_scene()
+    rng = np.random.default_rng(11)
+    obj = sc["objects"][0]
+    mean, var, l = obj["mean"], obj["var"], obj["length_scale"]
     O = oracle.Scene(sc)
     # global majorant: rho <= lambda(u_min)/sigma_lo with u_min the smallest mu/sigma the
     # trilinear fields reach; sigma(d) = E[max(0, -d.g)] <= |grad mu|_max + (sigma_hi/l)/sqrt(2 pi)
@@ -229,8 +225,6 @@ def test_regular_tracking_agrees_with_naive_delta_tracking():
     gmax = math.sqrt(sum((np.abs(np.diff(m, axis=2 - a)).max() / h[a]) ** 2 for a in range(3)))
     sbar = 1.05 * rho_max * (gmax + (s_hi / l) / math.sqrt(2 * math.pi))
     wl = np.array(sc["light"]["dir"])
-    cam = {"type": "ortho", "eye": (0.0, -1.0, 0.35), "look_at": (0.0, 0.0, 0.0), "up": (0.0, 0.0, 1.0),
-           "fov_y_deg": 40.0, "ortho_w": 0.45, "ortho_h": 0.45, "width": 4, "height": 4}
     bounces = 3
 
     def sig(x, d):
