@@ -223,7 +223,9 @@ gpss_status gpss_scene_majorant(gpss_scene s, int dims[3], float* values, gpss_s
  * image/sqsum may be device or host memory (host: rendered into a scene-owned
  * film, then copied back).  stats (host, nullable): filled after the stream is
  * synchronised.  With GPSS_FLAG_KEEP_PATH_RADIANCE the scene keeps each path's
- * radiance for gpss_render_adjoint with the same camera and options.  Path (pixel p,
+ * radiance for gpss_render_adjoint with the same camera and options; that render runs
+ * in the adjoint's own kernel (same estimator, about 1.3x the plain render's time), so
+ * that the adjoint's replay repeats its decisions bit for bit.  Path (pixel p,
  * sample j) draws its random numbers from Philox counters keyed by (p, j); the
  * resident threads take paths in 16x16-pixel tiles, all samples of a tile together,
  * which changes only the order of the film's float additions. */
