@@ -286,3 +286,48 @@ def test_regular_tracking_agrees_with_naive_delta_tracking():
     assert np.abs(z).max() < 4, (z, nm, om)
     tot = (nm.sum() - om.sum()) / math.sqrt((nse ** 2).sum() + (ose ** 2).sum())
     assert abs(tot) < 3, (tot, nm.sum(), om.sum())
+
+
+def test_zero_gradient_fog_single_scattering_closed_form():
+    """A constant mean (grad mu = 0): the slopes are isotropic, so sigma(d) = alpha psi(0)
+    = alpha/(2 sqrt pi) for every d, sigma_t = rho sigma(d) is constant in the box, and the
+    phase function is F/(4 pi) (Eq. gdf_to_ndf with a zero mean gradient).  Single
+    scattering toward a directional light is then the 1-D integral
+    L = int exp(-sigma_t t) sigma_t F/(4 pi) E exp(-sigma_t s(t)) dt, s(t) the light path to
+    the box face.  The oracle's extinction at such a point (every direction) and its
+    rendered pixel (next-event estimation with the phase function at a zero gradient)
+    against that."""
+    from scipy.integrate import quad
+    lo, hi = np.array([-0.125, -0.125, -0.125]), np.array([0.125, 0.125, 0.125])
+    p = W.node_coords(lo, hi, (5, 5, 5))
+    mu0, var0, l, F = 0.0625, 0.0078125, 0.0625, 0.75  # exact in the grids' float32
+    sc = {"objects": [W.make_object(np.full(p.shape[:3], mu0), var0, F, lo, hi, l)],
+          "light": W.directional_light((0.2, -0.3, 1.0), 1.0)}
+    O = oracle.Scene(sc)
+    sig = math.sqrt(var0)
+    alpha = math.sqrt(2.0) * sig / l
+    rho = oracle.inv_mills(mu0 / sig) / sig
+    st = rho * alpha / (2.0 * math.sqrt(math.pi))
+    rng = np.random.default_rng(3)
+    for _ in range(8):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        assert oracle.sigma_t(O, [0.01, -0.02, 0.03], d)[0] == pytest.approx(st, rel=1e-12)
+    wl = np.array(sc["light"]["dir"])
+    cam = {"type": "ortho", "eye": (0.0, -1.0, 0.0), "look_at": (0.0, 0.0, 0.0), "up": (0.0, 0.0, 1.0),
+           "fov_y_deg": 40.0, "ortho_w": 0.02, "ortho_h": 0.02, "width": 1, "height": 1}
+    o = np.array([0.0, -1.0, 0.0])
+    d = np.array([0.0, 1.0, 0.0])
+    t0, t1 = _box_span(o, d, lo, hi)
+
+    def f(t):
+        x = o + t * d
+        _, s1 = _box_span(x, wl, lo, hi)
+        return math.exp(-st * (t - t0)) * st * F / (4.0 * math.pi) * math.exp(-st * s1)
+
+    ref = quad(f, t0, t1, epsabs=0, epsrel=1e-12)[0]
+    spp = 65536
+    s, s2, _ = oracle.render(O, cam, {"spp": spp, "max_bounces": 1, "seed": 3})
+    m = s[0, 0, 0] / spp
+    se = math.sqrt(max(s2[0, 0, 0] / spp - m * m, 0.0) / spp)
+    assert abs(m - ref) < 4 * se + 1e-4 * ref, (m, ref, se)
