@@ -194,3 +194,43 @@ def test_exact_visible_normal_sampler(case, side):
         return pv[:, 0] / f["albedo"][0]
 
     assert _hist_chi2(S, x, d, d2, pdf_fn) > 1e-4
+
+
+@pytest.mark.parametrize("sampler", ["mixture", "exact"])
+def test_samplers_at_a_zero_mean_gradient(sampler):
+    """A constant mean (grad mu = 0): the phase function is isotropic, F/(4 pi), so
+    weighted samples must be spread uniformly in cos(d, d2) and in azimuth about d, with
+    mean weight F.  (The mixture's Beckmann proposal is then the roughest, about -d.)"""
+    lo, hi = (-0.125, -0.125, -0.125), (0.125, 0.125, 0.125)
+    p = W.node_coords(lo, hi, (5, 5, 5))
+    F = 0.75
+    O = oracle.Scene({"objects": [W.make_object(np.full(p.shape[:3], 0.0625), 0.0078125, F, lo, hi, 0.0625)]})
+    x = np.array([0.01, -0.02, 0.03])
+    d = np.array([0.3, 0.5, -0.8])
+    d /= np.linalg.norm(d)
+    n = 40000
+    u = np.random.default_rng(5).random((n, 3))
+    xs, ds = np.tile(x, (n, 1)), np.tile(d, (n, 1))
+    if sampler == "exact":
+        d2, w, pdf, ok = oracle.phase_sample_exact(O, 0, xs, ds, u)
+    else:
+        d2, w, pdf, ok = oracle.phase_sample(O, 0, xs, ds, u)
+    assert ok.mean() > 0.999
+    w = w[:, 0] * ok
+    assert abs(w.mean() - F) < 5 * w.std() / math.sqrt(n) + 1e-12, (w.mean(), F)
+    c = d2 @ d
+    fx, fy, _ = H.frame(d)
+    ph = np.mod(np.arctan2(d2 @ fy, d2 @ fx), 2 * math.pi)
+    # weighted counts in (cos, azimuth) cells against F/(4 pi) x the cell's solid angle
+    nb = 6
+    ci = np.clip(((c + 1) / 2 * nb).astype(int), 0, nb - 1)
+    pj = np.clip((ph / (2 * math.pi) * nb).astype(int), 0, nb - 1)
+    cells = np.zeros((nb, nb))
+    np.add.at(cells, (ci, pj), w)
+    expect = F * n / (nb * nb)
+    se = np.sqrt(np.zeros_like(cells) + (w ** 2).mean() * n / (nb * nb))  # Poisson-like cell counts
+    z = (cells - expect) / se
+    assert np.abs(z).max() < 4.5, z
+    # the pdf is the density of the returned directions: the exact sampler's is p/F = 1/(4 pi)
+    if sampler == "exact":
+        assert np.allclose(pdf[ok], 1.0 / (4 * math.pi), rtol=1e-9)
